@@ -1,0 +1,400 @@
+"""Benchmark of the SPA sweep on GB300 (one JSON line on stdout).
+
+A step is one whole SPA sweep (every row of the hot path: init, T x [reweight,
+log-sum-exp/ESS, resampling, proposal scales, M x (propose, likelihood, accept),
+summaries]) over one synthetic hit region, with the inputs resident in HBM. The
+metric is particle-log-likelihood throughput: algorithmic multiply-adds N*n*p per
+likelihood evaluation (the split-BF16 doubling is not counted) over the sweep's
+T*M + 1 evaluations, divided by the sweep wall time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload hit-region]
+                  [--precision split_bf16|fp32] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload. Under torchrun each rank runs its own sweep
+(independent replicas: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def workload_desc(w):
+    return (f"{w['name']}: n={w['n']} p={w['p']} N={w['N']} T={w['T']} M={w['M']} "
+            f"{w['move'].upper()} nu={w['nu']:g}")
+
+
+def algorithmic_gmac(w):
+    return w["N"] * w["n"] * w["p"] * (w["T"] * w["M"] + 1) / 1e9
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_sha() -> str:
+    path = os.path.join(ROOT, "paper_1106_0322_gb300", "csrc", "k_loglik_tc.cu")
+    h = hashlib.sha256()
+    for f in (path, os.path.join(ROOT, "paper_1106_0322_gb300", "csrc", "spa_device.cuh")):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def profile_traffic(workload: str):
+    """DRAM bytes per launch of the likelihood kernel from the committed ncu summary, if it
+    was captured from the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "roofline_counters.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload)
+    if not e or e.get("kernel_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_sample(w, region, sched, seconds_target=15.0, seed=1):
+    """Time the FP64 oracle on a bounded prefix of the sweep (init + the first steps)."""
+    import oracle
+
+    threads = oracle.max_threads()
+    # calibrate on one step, then take as many steps as fit in ~seconds_target
+    t0 = time.perf_counter()
+    oracle.run(region.G, region.y, w["nu"], sched[:1], w["N"], w["M"], seed=seed)
+    one = time.perf_counter() - t0
+    steps = max(1, min(w["T"], int(seconds_target / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(region.G, region.y, w["nu"], sched[:steps], w["N"], w["M"], seed=seed)
+    dt = time.perf_counter() - t0
+    gmac = w["N"] * w["n"] * w["p"] * (steps * w["M"] + 1) / 1e9
+    return {"value": gmac / dt, "unit": "GMAC/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {steps} of {w['T']} scale steps (init + {steps * w['M']} moves) of the same "
+                      f"workload, full N, {dt:.1f} s on {threads} threads"}
+
+
+def reference_arm(args, w):
+    """--impl reference: the FP64 oracle timed on the host cores, bounded samples."""
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1106_0322_gb300 import synth
+
+    oracle.build()
+    region = synth.workload_region(w["name"])
+    sched = synth.geometric_schedule(w["T"])
+    t0 = time.perf_counter()
+    oracle.run(region.G, region.y, w["nu"], sched[:1], w["N"], w["M"], seed=1)
+    one = time.perf_counter() - t0
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    steps_per = max(1, min(w["T"], int(budget / max(one, 1e-3))))
+    gmac = w["N"] * w["n"] * w["p"] * (steps_per * w["M"] + 1) / 1e9
+    for k in range(args.warmup):
+        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], w["N"], w["M"], seed=100 + k)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], w["N"], w["M"], seed=200 + k)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = gmac * args.steps / tot
+    threads = oracle.max_threads()
+    sample = (f"each step: first {steps_per} of {w['T']} scale steps (init + {steps_per * w['M']} moves) of the "
+              f"workload at full N, FP64, {threads} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GMAC/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(w), "sample": sample, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "GMAC/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+METRIC = "SPA sweep particle-loglik throughput (algorithmic GMAC/s = N*n*p*(T*M+1) / sweep wall time)"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="hit-region")
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+
+    from paper_1106_0322_gb300 import synth
+
+    w = dict(synth.WORKLOADS[args.workload])
+    w["name"] = args.workload
+    if args.impl == "reference":
+        return reference_arm(args, w)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1106_0322_gb300 as spa
+
+    region = synth.workload_region(args.workload)
+    sched_h = synth.geometric_schedule(w["T"])
+    sched_d = torch.tensor(sched_h, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream)
+    reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
+    T, p = w["T"], w["p"]
+    out_d = {
+        "mean": torch.empty((T, p), dtype=torch.float64, device=dev),
+        "quantile": torch.empty((T, p, 3), dtype=torch.float64, device=dev),
+        "conc": torch.empty((T, p, 2), dtype=torch.float64, device=dev),
+        "ess": torch.empty(T, dtype=torch.float64, device=dev),
+        "log_z_inc": torch.empty(T, dtype=torch.float64, device=dev),
+        "accept_rate": torch.empty(T, dtype=torch.float64, device=dev),
+        "resampled": torch.empty(T, dtype=torch.uint8, device=dev),
+    }
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    seed_base = 1000 * (rank + 1)
+
+    def one_sweep(k):
+        reg.run_device(sched_d, w["N"], w["M"], seed_base + k, out_d)
+
+    for k in range(args.warmup):
+        one_sweep(k)
+    reg.sync()
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- timed region
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    total_ms = 0.0
+    for k in range(args.steps):
+        flush.zero_()  # L2 flushed between timed sweeps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_sweep(args.warmup + k)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    reg.sync()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    launches = reg.last_launch_count() * args.steps
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    gmac = algorithmic_gmac(w)
+    value = world * gmac * args.steps / (total_ms / 1e3)
+    assert np.all(np.isfinite(out_d["mean"].cpu().numpy()))
+
+    # ----------------------------------- dominant kernel: the likelihood GEMM + epilogue
+    reps = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reg.loglik_repeat(w["N"], 5, stream.cuda_stream)
+    e0.record(stream)
+    reg.loglik_repeat(w["N"], reps, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    reg.sync()
+    kern_ms = e0.elapsed_time(e1) / reps
+    peaks, peak_src = measured_peaks()
+    flop = 2.0 * w["N"] * w["n"] * w["p"]
+    achieved = flop / (kern_ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained" if args.precision == "split_bf16" else "bf16_tflops")
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": profile_traffic(args.workload),
+                "kernel": "k_loglik_tc" if args.precision == "split_bf16" else "k_eta_tile",
+                "launch_ms": kern_ms, "peak_source": f"{peak_src}: bf16 sustained (kernel inside a long step)",
+                "algorithmic_flop_per_launch": flop}
+
+    # --------------------------------- plain FP32 comparator sweep on the same workload
+    plain = None
+    if args.precision == "split_bf16" and rank == 0:
+        reg32 = spa.Region(region.G, region.y, w["nu"],
+                           config=spa.make_config(move=w["move"], precision="fp32", stream=stream.cuda_stream))
+        reg32.run_device(sched_d, w["N"], w["M"], 7, out_d)
+        reg32.sync()
+        flush.zero_()
+        e0.record(stream)
+        reg32.run_device(sched_d, w["N"], w["M"], 8, out_d)
+        e1.record(stream)
+        e1.synchronize()
+        reg32.sync()
+        pms = e0.elapsed_time(e1)
+        plain = {"ms_per_step": pms, "value": gmac / (pms / 1e3), "unit": "GMAC/s",
+                 "speedup_of_split_bf16": pms / ms_per_step}
+        reg32.close()
+
+    # ------------------------------------------ end to end through the C ABI, host buffers
+    e2e = None
+    if not args.no_e2e:
+        G_pin = torch.from_numpy(region.G).pin_memory()
+        y_pin = torch.from_numpy(region.y).pin_memory()
+        ereg = spa.Region(region.G, region.y, w["nu"], config=spa.make_config(move=w["move"], precision=args.precision))
+        ereg.run(sched_h, w["N"], w["M"], 1)  # builds the graph once, as a long-lived context does
+        t_e2e = 0.0
+        ksteps = max(2, min(args.steps, 5))
+        for k in range(ksteps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ereg.set_data(G_pin.numpy(), y_pin.numpy())
+            res = ereg.run(sched_h, w["N"], w["M"], 50 + k)
+            t_e2e += time.perf_counter() - t0
+        bi = region.G.nbytes + region.y.nbytes + sched_h.nbytes + 8
+        bo = sum(v.nbytes for v in res.values())
+        e2e = {"value": gmac * ksteps / t_e2e, "unit": "GMAC/s", "h2d_bytes_per_step": int(bi),
+               "d2h_bytes_per_step": int(bo), "ms_per_step": 1e3 * t_e2e / ksteps,
+               "path": "spa_set_data (pinned host G, y) + spa_run (host schedule -> host results)"}
+        ereg.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w, region, sched_h)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "GMAC/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "bf16" if args.precision == "split_bf16" else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(w), "precision": args.precision,
+                       "l2": "flushed (512 MB write) between timed sweeps",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "accumulate": "fp32 (tcgen05 TMEM)" if args.precision == "split_bf16" else "fp32 FFMA",
+                       "weights": "fp64"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "plain_fp32": plain,
+        }
+        print(json.dumps(line), flush=True)
+    reg.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

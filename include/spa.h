@@ -1,0 +1,225 @@
+/*
+ * spa.h -- C ABI of the GB300 sparsity-path-analysis (SPA) library.
+ *
+ * The library runs the sequential Monte Carlo sweep over the scale c of a
+ * generalised-t prior on logistic-regression coefficients (Lee, Caron, Doucet &
+ * Holmes, arXiv:1106.0322, Sections 2-5) on one NVIDIA GB300 (sm_103a). Every step
+ * of the sweep runs in the library's own CUDA kernels: the genotype store, the
+ * split-BF16 tcgen05 likelihood GEMM with a fused softplus epilogue (or a plain
+ * FP32 SIMT comparator), the prior incremental weight, the FP64 log-sum-exp / ESS,
+ * systematic resampling, the random-walk / MALA moves and the per-scale summaries.
+ *
+ * Conventions for every function:
+ *   - Return value: SPA_OK (0) or one of the SPA_E* codes below. No exception, no
+ *     abort and no exit crosses this boundary; spa_last_error() gives a message.
+ *   - Pointers are HOST pointers unless the name ends in _device, where they are
+ *     device pointers of the current CUDA device.
+ *   - Inputs are read during the call and never retained; the library copies what it
+ *     keeps. Outputs are caller-allocated buffers of the documented size.
+ *   - Matrices are row-major. Genotypes G are n x p (individual-major); particle
+ *     matrices B are N x p (particle-major).
+ *   - A context is not thread-safe: use one context per host thread. Distinct
+ *     contexts may be used concurrently.
+ *   - The library owns all device memory it allocates and frees it in spa_destroy.
+ */
+#ifndef SPA_H
+#define SPA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status codes */
+#define SPA_OK 0
+#define SPA_EINVAL 1      /* invalid argument: sizes < 1, nu <= 0 or NaN, genotype not in
+                             {0,1,2}, phenotype not in {0,1}, a monomorphic marker (sd 0),
+                             a non-positive or non-finite scale, NULL pointer */
+#define SPA_ENOMEM 2      /* device or host allocation failed */
+#define SPA_ECUDA 3       /* a CUDA runtime call failed (message in spa_last_error) */
+#define SPA_ETIMEOUT 4    /* a bounded device-side wait gave up (the kernel returned early) */
+#define SPA_ENUMERIC 5    /* NaN/Inf in a log-likelihood or a log-weight, or ESS < 1 */
+#define SPA_EUNSUPPORTED 6 /* configuration not supported (e.g. no sm_100-family GPU) */
+
+/* ------------------------------------------------------------------ configuration */
+#define SPA_MOVE_RW 0       /* joint random-walk Metropolis-Hastings */
+#define SPA_MOVE_MALA 1     /* Metropolis-adjusted Langevin, driven by the adjoint kernel */
+
+#define SPA_PREC_SPLIT_BF16 0 /* tcgen05: X exact in BF16, beta = hi + lo BF16, FP32 accumulate */
+#define SPA_PREC_FP32 1       /* plain FP32 SIMT (FFMA) comparator path */
+
+#define SPA_INIT_PRIOR_IS 0       /* prior draws at c_1 weighted by the likelihood */
+#define SPA_INIT_RESAMPLE_MOVE 1  /* the same, then resampled and burn_in_steps x M moves */
+
+#define SPA_MAX_QUANTILES 8
+#define SPA_MAX_DELTAS 8
+
+typedef struct spa_config {
+    int32_t move_kind;       /* SPA_MOVE_RW (default) or SPA_MOVE_MALA */
+    int32_t precision;       /* SPA_PREC_SPLIT_BF16 (default) or SPA_PREC_FP32 */
+    int32_t init_mode;       /* SPA_INIT_PRIOR_IS (default) or SPA_INIT_RESAMPLE_MOVE */
+    int32_t burn_in_steps;   /* blocks of M moves at c_1 for SPA_INIT_RESAMPLE_MOVE (default 0) */
+    int32_t n_quantiles;     /* number of weighted quantile levels (default 3) */
+    double quantiles[SPA_MAX_QUANTILES]; /* levels in (0,1) (default 0.05, 0.5, 0.95) */
+    int32_t n_deltas;        /* number of concentration thresholds (default 2) */
+    double deltas[SPA_MAX_DELTAS];       /* Delta > 0 of V = 1 - Pr(|beta_j| < Delta) (0.05, 0.1) */
+    double ess_frac;         /* resample when ESS < ess_frac * N (default 0.75, Section 4) */
+    double rw_scale;         /* RW: sigma_j = rw_scale/sqrt(p) * max(sd_W(beta_j), sd_floor*c) (2.38) */
+    double mala_h;           /* MALA: initial lambda in h = lambda * p^(-1/6) (1.65) */
+    double sd_floor;         /* floor of the proposal scale relative to c (default 1e-3) */
+    void* stream;            /* cudaStream_t to run on; NULL: the context's own stream */
+} spa_config;
+
+/* Per-scale outputs of a sweep, caller-allocated (any pointer may be NULL to skip it).
+ * t indexes the schedule, j the marker, q the quantile level, d the threshold. */
+typedef struct spa_result {
+    double* mean;         /* [T*p]    weighted posterior mean of beta_j at c_t          */
+    double* quantile;     /* [T*p*Q]  weighted quantiles (index (t*p + j)*Q + q)        */
+    double* conc;         /* [T*p*D]  concentration 1 - Pr(|beta_j| < Delta_d)          */
+    double* ess;          /* [T]      effective sample size after reweighting           */
+    double* log_z_inc;    /* [T]      log Z_t/Z_{t-1}; entry 0 is log Z_1 (prior IS)    */
+    double* accept_rate;  /* [T]      fraction of accepted proposals in step t's moves  */
+    uint8_t* resampled;   /* [T]      1 if the particles were resampled at step t       */
+} spa_result;
+
+typedef struct spa_ctx spa_ctx;
+
+/* Fills *cfg with the defaults listed above. */
+void spa_config_default(spa_config* cfg);
+
+/* --------------------------------------------------------------------- lifecycle */
+
+/* Create a context for one hit region (Section 3 data, Section 2 model).
+ *   G   n*p genotypes in {0,1,2}, row-major (individual i, marker j)
+ *   y   n phenotypes in {0,1} (case = 1)
+ *   nu  Gt degrees of freedom a > 0 (eq. gent_prior, q = 1); +INFINITY selects the
+ *       double-exponential prior (the a -> infinity limit, Section 5.4)
+ * Copies G and y to the device, standardises the columns (Section 3: mean 0, unit
+ * population sd) and builds the exact BF16 GEMM operand. Errors: SPA_EINVAL for bad
+ * sizes or values (including a monomorphic column), SPA_ENOMEM, SPA_ECUDA,
+ * SPA_EUNSUPPORTED if the current device is not compute capability 10.x. */
+int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double nu, spa_ctx** out);
+
+/* Replace the genotypes and phenotypes of an existing context (same n, p). */
+int spa_set_data(spa_ctx* ctx, const int8_t* G, const uint8_t* y);
+
+/* Set / read the configuration. spa_set_config validates it (SPA_EINVAL). */
+int spa_set_config(spa_ctx* ctx, const spa_config* cfg);
+int spa_get_config(const spa_ctx* ctx, spa_config* cfg);
+
+/* Free every device and host resource of the context. NULL is ignored. */
+void spa_destroy(spa_ctx* ctx);
+
+/* Message for the last failing call on this context, or, for ctx == NULL, the last
+ * failure of a context-free call on this host thread. Never NULL. */
+const char* spa_last_error(const spa_ctx* ctx);
+
+/* --------------------------------------------------------------------- the sweep */
+
+/* Run the SMC sampler over the prior scale (Section 4) with targets
+ * pi_t(beta) = p(beta | X, y, a, c_t), t = 0..T-1:
+ *   t = 0   N draws from Gt(a, c_0), weighted by the likelihood (log Z_1 estimate);
+ *   t >= 1  reweight by gamma_t/gamma_{t-1} (the prior ratio, Section 4 with the
+ *           reversal backward kernel), log Z_t/Z_{t-1} = log sum_i W_{t-1} w_t;
+ *   every t resample (systematic) if ESS < ess_frac*N, then moves_per_step MCMC
+ *           moves invariant for pi_t (resample before move, Section 4), then the
+ *           per-scale summaries of Section 5 into *out (host buffers).
+ *   scale_schedule  T values c_t > 0 (any order; the paper sweeps b_t = a c_t down)
+ *   N               particles (1 .. 2^22); moves_per_step >= 0; seed keys Philox.
+ * Blocks until the results are on the host. SPA_ENUMERIC if a log-likelihood or a
+ * weight became non-finite, SPA_ETIMEOUT if a device wait gave up. */
+int spa_run(spa_ctx* ctx, const double* scale_schedule, int64_t T, int64_t N,
+            int32_t moves_per_step, uint64_t seed, spa_result* out);
+
+/* As spa_run, but the schedule and every spa_result array are DEVICE pointers and the
+ * call only enqueues the sweep on the configured stream (no host synchronisation).
+ * Device-side errors are reported by the next spa_sync(). */
+int spa_run_device(spa_ctx* ctx, const double* scale_schedule_device, int64_t T, int64_t N,
+                   int32_t moves_per_step, uint64_t seed, spa_result* out_device);
+
+/* Wait for work enqueued on the context's stream and report device-side errors. */
+int spa_sync(spa_ctx* ctx);
+
+/* Batched sweeps over R independent regions (each context its own data, nu and
+ * config), all enqueued before any is waited for. */
+typedef struct spa_batch_args {
+    const double* const* schedules;  /* R host pointers, schedule of region r      */
+    const int64_t* T;                /* [R] schedule lengths                        */
+    const int64_t* N;                /* [R] particle counts                         */
+    const int32_t* moves_per_step;   /* [R]                                         */
+    const uint64_t* seeds;           /* [R]                                         */
+} spa_batch_args;
+int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_result* outs);
+
+/* Number of kernels the last spa_run / spa_run_device of this context launched. */
+int64_t spa_last_launch_count(const spa_ctx* ctx);
+
+/* Enqueue `reps` launches of the context's likelihood kernel (split-BF16 tcgen05 or
+ * FP32 SIMT, per the configuration) on `stream` over the particles last packed for
+ * N (by spa_run / spa_loglik with the same N), in the launch configuration the sweep
+ * uses. No host synchronisation; for timing the kernel with events on `stream`.
+ * SPA_EINVAL if no workspace of N particles exists. */
+int spa_loglik_repeat(spa_ctx* ctx, int64_t N, int32_t reps, void* stream);
+
+/* ------------------------------------------------------- per-step entry points */
+
+/* Log-likelihood l(beta) = sum_i [y_i eta_i - log(1 + exp(eta_i))], eta = X beta
+ * (Section 2, standardised X of Section 3) for N particles B (N*p floats), with the
+ * context's precision: split-BF16 tcgen05 or plain FP32. ll_out: N doubles.
+ * Split-BF16 bound: |err| <= (2^-15 + (2p+2) 2^-23) * sum_i (sum_j |g_ij bt_j| + |o|)
+ *   + 2^-20 n + 2^-21 sum_i softplus(eta_i), with bt_j = beta_j/s_j, o = -sum_j m_j bt_j. */
+int spa_loglik(spa_ctx* ctx, const float* B, int64_t N, double* ll_out);
+int spa_loglik_device(spa_ctx* ctx, const float* B_device, int64_t N, double* ll_device,
+                      void* stream);
+
+/* Gradient of the log posterior at scale c, grad l(beta) + grad log p(beta | a, c)
+ * (grad l = X^T (y - logit^{-1}(eta)); the prior term -(a+1) sgn(beta_j)/(a c + |beta_j|),
+ * or -sgn(beta_j)/c for the double exponential, with sgn(0) = 0). c == 0 returns the
+ * likelihood gradient alone. ll_out: N doubles (may be NULL); grad_out: N*p floats. */
+int spa_grad(spa_ctx* ctx, const float* B, int64_t N, double c, double* ll_out, float* grad_out);
+int spa_grad_device(spa_ctx* ctx, const float* B_device, int64_t N, double c, double* ll_device,
+                    float* grad_device, void* stream);
+
+/* Systematic resampling (Section 4 resamples when ESS < 3N/4; the scheme is systematic):
+ * A_k = min{i : C_i > (k+u)/N}, clamped to N-1, C the cumulative sum of W formed in
+ * blocks of 256 (running sum in each block, running sum of block totals before it,
+ * C_i = carry + local_i), target ((double)k + u)/(double)N rounded to nearest.
+ *   W  N normalised weights (doubles), u in [0,1); idx_out: N int32 ancestor indices.
+ * Bit-exact given W and u. */
+int spa_resample_systematic(const double* W, int64_t N, double u, int32_t* idx_out);
+
+/* log Gt(beta | a, c) = -log(2c) - (a+1) log1p(|beta|/(a c)) per element (eq. gent_prior,
+ * q = 1, mu = 0); nu = +INFINITY gives -log(2c) - |beta|/c. out: k doubles. */
+int spa_prior_logpdf(double nu, double c, const float* beta, int64_t k, double* out);
+
+/* Incremental log-weight per particle for a scale change c_prev -> c_new:
+ * sum_j log p(beta_j | c_new) - log p(beta_j | c_prev) (Section 4: the likelihood
+ * cancels under the reversal backward kernel). B: N*p floats; out: N doubles. */
+int spa_incr_weight(double nu, double c_prev, double c_new, const float* B, int64_t N, int64_t p,
+                    double* out);
+
+/* Log-sum-exp and effective sample size (sum W)^2 / sum W^2 of N log-weights. */
+int spa_lse_ess(const double* logw, int64_t N, double* lse_out, double* ess_out);
+
+/* Weighted per-marker summaries of particles (Section 5.1-5.2): mean, quantiles
+ * Q_q = beta_(k*) with k* = min{k : cumulative sorted weight >= q}, and concentration
+ * 1 - Pr(|beta_j| < Delta). B: N*p floats, W: N normalised weights.
+ * Outputs: mean[p], quant[p*nq], conc[p*nd] (doubles). */
+int spa_summaries(const float* B, const double* W, int64_t N, int64_t p, const double* q,
+                  int32_t nq, const double* deltas, int32_t nd, double* mean, double* quant,
+                  double* conc);
+
+/* The random streams (Philox4x32-10, Salmon et al. SC'11), for stream tests:
+ *   spa_philox4x32_10: count counters (4 uint32 each) under one key -> 4*count outputs;
+ *   spa_normals: the p move normals of (particle, step t, move m) under seed;
+ *   spa_prior_sample: the N*p initial draws from Gt(a, c) under seed. */
+int spa_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out);
+int spa_normals(uint64_t seed, uint32_t particle, uint32_t t, uint32_t m, int64_t p, float* out);
+int spa_prior_sample(uint64_t seed, double nu, double c, int64_t N, int64_t p, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPA_H */

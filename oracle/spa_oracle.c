@@ -80,8 +80,9 @@ static void or_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32
     or_philox4x32_10(ctr, key, out);
 }
 
-/* Uniform on the open interval (0,1) from the top 24 bits. */
-static double or_u01_open(uint32_t u) { return ((double)(u >> 8) + 0.5) * (1.0 / 16777216.0); }
+/* Uniform on the open interval (0,1) from the top 23 bits: (k + 1/2) 2^-23, a value
+ * that single precision also holds exactly. */
+static double or_u01_open(uint32_t u) { return ((double)(u >> 9) + 0.5) * (1.0 / 8388608.0); }
 /* Uniform on [0,1) from the top 24 bits. */
 static double or_u01(uint32_t u) { return (double)(u >> 8) * (1.0 / 16777216.0); }
 

@@ -1,0 +1,310 @@
+// k_loglik_tc.cu -- the particle log-likelihood on the 5th-generation tensor cores.
+//
+// Section 2's log-likelihood of particle k is l_k = sum_i [y_i eta_ki - softplus(eta_ki)],
+// eta = X beta_k. The linear part equals beta_k . (X^T y) and is formed by the proposal
+// kernel. This kernel computes the softplus part for N particles at once as a
+// contraction followed by a row reduction that never leaves the chip:
+//
+//   eta2[k, i] = sum_j A[k, j] * Gb[i, j]      (tcgen05.mma, BF16 x BF16 -> FP32 in TMEM)
+//   partial[k] += sum_i log2(1 + 2^eta2[k, i])  (epilogue warps, ex2/lg2 on the SFU)
+//
+// with A[k] = [hi(bt_k) | lo(bt_k)] the split-BF16 copy of bt_kj = beta_kj log2(e)/s_j
+// (plus the offset -sum_j m_j bt_kj in the ones column), and Gb = [G, 1] the exact BF16
+// genotypes. Both halves of A multiply the same G tile, so each pipeline stage carries
+// A_hi, A_lo and G for one 64-wide k-block; eta2 = eta log2(e) and softplus(eta) =
+// ln(2) * log2(1 + 2^eta2).
+//
+// Tile: 128 particles (M, TMEM lanes) x BN individuals (N, TMEM columns). A persistent
+// grid walks the (particle-tile, individual-tile) units in order; each unit's row sums go
+// to their own slot of `partial`, so the final sum (in the accept kernel) has a fixed
+// order. Warp roles: warp 0 issues TMA loads, warp 1 (one thread) issues the MMAs and owns
+// TMEM, warps 2..9 drain the double-buffered accumulator (warp w reads TMEM lanes
+// 32 (w % 4) .. +31, half (w - 2) / 4 of the columns). Every wait is bounded.
+#include "spa_device.cuh"
+#include "spa_internal.h"
+
+namespace spa {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // BF16 per 128-byte swizzle row
+constexpr int EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+
+template <int BN, int STAGES>
+struct TcCfg {
+    static constexpr int A_TILE = BM * BK * 2;
+    static constexpr int B_TILE = BN * BK * 2;
+    static constexpr int STAGE = 2 * A_TILE + B_TILE;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int NBARS = 2 * STAGES + 5;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
+    static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
+    static constexpr int BYTES = SLOT_OFF + 16;
+    static constexpr int SMEM = BYTES + 1024;  // slack for the 1024-byte alignment of the tiles
+    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
+};
+
+__device__ __forceinline__ float sum_softplus2_32(const float (&v)[32], int valid)
+{
+    float t[32];
+    if (valid >= 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) t[k] = softplus2(v[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) t[k] = (k < valid) ? softplus2(v[k]) : 0.0f;
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) t[k] += t[k + w];
+    return t[0];
+}
+
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n_tiles,
+                int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial, int64_t N_pad,
+                uint32_t* __restrict__ err)
+{
+    using C = TcCfg<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = sbase + C::BAR_OFF;
+    const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
+#define FULL_BAR(s) (bar0 + 8u * (uint32_t)(s))
+#define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
+#define ACCF_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
+#define ACCE_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
+
+    const int64_t U = (int64_t)m_tiles * n_tiles;
+    const int64_t u_begin = U * blockIdx.x / gridDim.x;
+    const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(FULL_BAR(s), 1);
+            mbar_init(EMPTY_BAR(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(ACCF_BAR(b), 1);
+            mbar_init(ACCE_BAR(b), EPI_WARPS);
+        }
+        mbar_init(drain_bar, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t u = u_begin; u < u_end && ok; ++u) {
+                const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
+                    if (!mbar_wait_bounded(EMPTY_BAR(s), ph ^ 1u, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + s * C::STAGE;
+                    mbar_arrive_expect_tx(FULL_BAR(s), (uint32_t)C::STAGE);
+                    tma_load_2d(st, &mapA, FULL_BAR(s), kb * BK, mt * BM);
+                    tma_load_2d(st + C::A_TILE, &mapA, FULL_BAR(s), Kp + kb * BK, mt * BM);
+                    tma_load_2d(st + 2 * C::A_TILE, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                    ++it;
+                }
+            }
+            // Never leave with a copy in flight: the most recent use of each stage must have landed.
+            const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
+            for (uint32_t k = 1; k <= last; ++k) {
+                const uint32_t i2 = it - k;
+                mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+            uint32_t it = 0;
+            int lt = 0;
+            bool ok = true;
+            for (int64_t u = u_begin; u < u_end && ok; ++u, ++lt) {
+                const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+                if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + b * (uint32_t)BN;
+                for (int kb = 0; kb < kblocks; ++kb) {
+                    const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
+                    if (!mbar_wait_bounded(FULL_BAR(s), ph, err)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + s * C::STAGE;
+                    const uint64_t ahi = sdesc_sw128(st);
+                    const uint64_t alo = sdesc_sw128(st + C::A_TILE);
+                    const uint64_t bg = sdesc_sw128(st + 2 * C::A_TILE);
+                    const int nks = (ksteps - 4 * kb) < 4 ? (ksteps - 4 * kb) : 4;
+                    for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
+                        umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
+                    for (int ks = 0; ks < nks; ++ks) umma_bf16(d, alo + 2u * ks, bg + 2u * ks, IDESC, 1u);
+                    umma_commit(EMPTY_BAR(s));
+                    ++it;
+                }
+                if (!ok) break;
+                umma_commit(ACCF_BAR(b));
+            }
+            // Wait for every MMA this thread issued before TMEM can be released.
+            umma_commit(drain_bar);
+            mbar_wait_bounded(drain_bar, 0u, err, 100000000ull);
+        }
+    } else {
+        // --------------------------------------------------------------- epilogue
+        const int quad = warp & 3;         // TMEM lane quadrant this warp may access
+        const int half = (warp - 2) >> 2;  // which half of the BN columns
+        const int row = quad * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        int lt = 0;
+        for (int64_t u = u_begin; u < u_end; ++u, ++lt) {
+            const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+            const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+            if (!mbar_wait_bounded(ACCF_BAR(b), aph, err)) break;
+            tc_fence_after();
+            const int col0 = half * (BN / 2);
+            const int valid = n - nt * BN - col0;
+            float acc = 0.0f;
+#pragma unroll 1
+            for (int c = 0; c < BN / 2; c += 32) {
+                if (valid - c <= 0) break;
+                float v[32];
+                tmem_ld32(tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)(col0 + c), v);
+                acc += sum_softplus2_32(v, valid - c);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ACCE_BAR(b));
+            partial[((int64_t)nt * 2 + half) * N_pad + (int64_t)mt * BM + row] = acc;
+        }
+    }
+#undef FULL_BAR
+#undef EMPTY_BAR
+#undef ACCF_BAR
+#undef ACCE_BAR
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
+                 uint32_t box_outer)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN, int STAGES>
+cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
+                      float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st)
+{
+    using C = TcCfg<BN, STAGES>;
+    k_loglik_tc<BN, STAGES><<<plan.grid, TC_THREADS, C::SMEM, st>>>(mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks,
+                                                                     plan.ksteps, Kp, (int)n, partial, N_pad, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t tc_init_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_loglik_tc<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<256, 3>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_loglik_tc<128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128, 4>::SMEM);
+    return e;
+}
+
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms)
+{
+    TcPlan pl;
+    pl.BN = (n <= 128) ? 128 : 256;
+    pl.n_tiles = (int)((n + pl.BN - 1) / pl.BN);
+    pl.m_tiles = (int)(N_pad / BM);
+    pl.ksteps = (p + 1 + 15) / 16;
+    pl.kblocks = (pl.ksteps + 3) / 4;
+    const int64_t units = (int64_t)pl.m_tiles * pl.n_tiles;
+    pl.grid = (int)(units < num_sms ? units : num_sms);
+    pl.n_parts = 2 * pl.n_tiles;
+    return pl;
+}
+
+bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp)
+{
+    return make_map_2d(map, A, (uint64_t)(2 * Kp), (uint64_t)N_pad, BK, BM);
+}
+
+bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN)
+{
+    return make_map_2d(map, Gbf, (uint64_t)Kp, (uint64_t)n, BK, (uint32_t)BN);
+}
+
+cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
+                             float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st)
+{
+    if (plan.BN == 256) return launch_tc<256, 3>(mapA, mapB, plan, n, Kp, partial, N_pad, err, st);
+    return launch_tc<128, 4>(mapA, mapB, plan, n, Kp, partial, N_pad, err, st);
+}
+
+}  // namespace spa

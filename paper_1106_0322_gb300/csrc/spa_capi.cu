@@ -1,0 +1,1043 @@
+// spa_capi.cu -- the host runtime behind include/spa.h.
+//
+// A context owns one region's genotype store and the device workspace of its sweeps.
+// spa_run enqueues the whole sweep -- init, then per scale step: reweight, log-sum-exp /
+// ESS, conditional resampling, proposal scales, M x (propose, likelihood, accept),
+// summaries -- on one stream, captures it once into a CUDA graph keyed by
+// (T, N, M, config), and replays the graph for later sweeps of the same shape. The
+// schedule and the seed live in device memory, so a replay only re-uploads them.
+// Decisions that depend on data (resample or not) are taken on the device (a flag the
+// resampling kernels read), so the host never waits inside a sweep.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/spa.h"
+#include "spa_device.cuh"
+#include "spa_internal.h"
+
+using namespace spa;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <typename T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Round x up to a multiple of m.
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Workspace {
+    int64_t N = 0, N_pad = 0;
+    float *beta = nullptr, *beta_p = nullptr, *scale = nullptr;
+    __nv_bfloat16* A = nullptr;
+    CUtensorMap mapA;
+    double *lin_p = nullptr, *lp_p = nullptr, *ll = nullptr, *lp = nullptr, *logw = nullptr, *W = nullptr;
+    double *ll_tmp = nullptr, *lp_tmp = nullptr, *cum = nullptr, *colpart = nullptr, *lambda = nullptr;
+    float* partial = nullptr;
+    int32_t* idx = nullptr;
+    int* flag = nullptr;
+    float* eta = nullptr;  // gradient path scratch, allocated on first use
+    float* grad = nullptr;
+};
+
+struct RunBufs {
+    int64_t T = 0;
+    int nq = 0, nd = 0;
+    double *sched = nullptr, *mean = nullptr, *quant = nullptr, *conc = nullptr, *ess = nullptr, *logz = nullptr,
+           *accrate = nullptr;
+    unsigned long long* acc = nullptr;
+    uint8_t* res = nullptr;
+    uint64_t* seed = nullptr;
+};
+
+struct GraphKey {
+    int64_t T = -1, N = -1;
+    int32_t M = -1;
+    spa_config cfg;
+    bool operator==(const GraphKey& o) const
+    {
+        return T == o.T && N == o.N && M == o.M && std::memcmp(&cfg, &o.cfg, sizeof(spa_config)) == 0;
+    }
+};
+
+}  // namespace
+
+struct spa_ctx {
+    int64_t n = 0, p = 0;
+    int Kp = 0;
+    double nu = 1.0;
+    PriorArgs pr{1.0f, 0};
+    int device = 0, num_sms = 0;
+    cudaStream_t own_stream = nullptr;
+    spa_config cfg;
+    std::string err;
+    // genotype store
+    int8_t* G = nullptr;
+    uint8_t* y = nullptr;
+    unsigned long long* sums = nullptr;
+    double *mean = nullptr, *sd = nullptr, *v = nullptr, *unit_c = nullptr;
+    float *l2e_s = nullptr, *mean_f = nullptr, *Xf = nullptr;
+    __nv_bfloat16* Gbf = nullptr;
+    CUtensorMap mapB;
+    int mapB_BN = 0;
+    uint32_t* d_err = nullptr;
+    Workspace ws;
+    RunBufs rb;
+    cudaGraphExec_t gexec = nullptr;
+    GraphKey gkey;
+    int64_t graph_launches = 0;
+    int64_t last_launches = 0;
+
+    cudaStream_t stream() const { return cfg.stream ? static_cast<cudaStream_t>(cfg.stream) : own_stream; }
+};
+
+namespace {
+
+int fail(spa_ctx* c, int code, const std::string& msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_thread_error = msg;
+    return code;
+}
+
+int cuda_fail(spa_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int check_device(spa_ctx* c)
+{
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    if (prop.major != 10)
+        return fail(c, SPA_EUNSUPPORTED, "the library is built for sm_103a (compute capability 10.x)");
+    if (c) {
+        c->device = dev;
+        c->num_sms = prop.multiProcessorCount;
+        CK(tc_init_attributes(), "tensor-core kernel attributes");
+    }
+    return SPA_OK;
+}
+
+int map_device_error(spa_ctx* c, uint32_t e)
+{
+    if (e == 0) return SPA_OK;
+    if (e & DERR_TIMEOUT) return fail(c, SPA_ETIMEOUT, "a bounded device wait gave up");
+    if (e & DERR_INPUT) return fail(c, SPA_EINVAL, "invalid input data (genotype not in {0,1,2}, phenotype not in {0,1}, or a monomorphic marker)");
+    if (e & DERR_NONFINITE) return fail(c, SPA_ENUMERIC, "non-finite log-likelihood or log-weight");
+    if (e & DERR_ESS) return fail(c, SPA_ENUMERIC, "effective sample size below 1");
+    return fail(c, SPA_ECUDA, "unknown device error");
+}
+
+int read_error_word(spa_ctx* c)
+{
+    uint32_t e = 0;
+    CK(cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream()), "read error word");
+    CK(cudaStreamSynchronize(c->stream()), "stream synchronize");
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream()), "reset error word");
+    return map_device_error(c, e);
+}
+
+void free_workspace(Workspace& w)
+{
+    dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
+    dfree(w.lin_p); dfree(w.lp_p); dfree(w.ll); dfree(w.lp); dfree(w.logw); dfree(w.W);
+    dfree(w.ll_tmp); dfree(w.lp_tmp); dfree(w.cum); dfree(w.colpart); dfree(w.lambda);
+    dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
+    w.N = w.N_pad = 0;
+}
+
+void free_runbufs(RunBufs& r)
+{
+    dfree(r.sched); dfree(r.mean); dfree(r.quant); dfree(r.conc); dfree(r.ess); dfree(r.logz); dfree(r.accrate);
+    dfree(r.acc); dfree(r.res); dfree(r.seed);
+    r.T = 0;
+}
+
+void drop_graph(spa_ctx* c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+    c->gkey = GraphKey();
+}
+
+int ensure_mapB(spa_ctx* c, int BN)
+{
+    if (c->mapB_BN == BN) return SPA_OK;
+    if (!tc_make_map_B(&c->mapB, c->Gbf, c->n, c->Kp, BN))
+        return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
+    c->mapB_BN = BN;
+    return SPA_OK;
+}
+
+int ensure_workspace(spa_ctx* c, int64_t N)
+{
+    Workspace& w = c->ws;
+    if (w.N == N) return SPA_OK;
+    drop_graph(c);
+    free_workspace(w);
+    const int64_t p = c->p;
+    const int64_t N_pad = round_up(N, 128);
+    const TcPlan plan = tc_plan(c->n, (int)p, N_pad, c->num_sms);
+    const int64_t simt_parts = (c->n + SIMT_TILE_N - 1) / SIMT_TILE_N;
+    const int64_t parts = plan.n_parts > simt_parts ? plan.n_parts : simt_parts;
+    const int64_t nblk = (N + 255) / 256;
+    cudaError_t e = cudaSuccess;
+#define WA(ptr, cnt) \
+    if (e == cudaSuccess) e = dalloc(&w.ptr, (size_t)(cnt))
+    WA(beta, N * p);
+    WA(beta_p, N * p);
+    WA(scale, p);
+    WA(A, N_pad * 2 * c->Kp);
+    WA(lin_p, N); WA(lp_p, N); WA(ll, N); WA(lp, N); WA(logw, N); WA(W, N);
+    WA(ll_tmp, N); WA(lp_tmp, N);
+    WA(cum, N + nblk + 1);
+    WA(colpart, (int64_t)COLSTAT_SPLITS * p * 2);
+    WA(lambda, 1);
+    WA(partial, parts * N_pad);
+    WA(idx, N);
+    WA(flag, 1);
+#undef WA
+    if (e != cudaSuccess) {
+        free_workspace(w);
+        return cuda_fail(c, e, "workspace allocation");
+    }
+    // The GEMM operand's padding (columns p+1..Kp-1 of both halves, rows N..N_pad-1) stays zero.
+    CK(cudaMemsetAsync(w.A, 0, sizeof(__nv_bfloat16) * (size_t)(N_pad * 2 * c->Kp), c->stream()), "memset A");
+    CK(cudaMemsetAsync(w.partial, 0, sizeof(float) * (size_t)(parts * N_pad), c->stream()), "memset partial");
+    CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->stream()), "memset flag");
+    if (!tc_make_map_A(&w.mapA, w.A, N_pad, c->Kp)) {
+        free_workspace(w);
+        return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the particle operand");
+    }
+    int rc = ensure_mapB(c, plan.BN);
+    if (rc != SPA_OK) return rc;
+    w.N = N;
+    w.N_pad = N_pad;
+    return SPA_OK;
+}
+
+int ensure_runbufs(spa_ctx* c, int64_t T)
+{
+    RunBufs& r = c->rb;
+    const int nq = c->cfg.n_quantiles, nd = c->cfg.n_deltas;
+    if (r.T == T && r.nq == nq && r.nd == nd) return SPA_OK;
+    drop_graph(c);
+    free_runbufs(r);
+    const int64_t p = c->p;
+    cudaError_t e = cudaSuccess;
+#define RA(ptr, cnt) \
+    if (e == cudaSuccess) e = dalloc(&r.ptr, (size_t)(cnt))
+    RA(sched, T);
+    RA(mean, T * p);
+    RA(quant, T * p * (nq > 0 ? nq : 1));
+    RA(conc, T * p * (nd > 0 ? nd : 1));
+    RA(ess, T); RA(logz, T); RA(accrate, T);
+    RA(acc, T + 1);
+    RA(res, T);
+    RA(seed, 1);
+#undef RA
+    if (e != cudaSuccess) {
+        free_runbufs(r);
+        return cuda_fail(c, e, "run buffer allocation");
+    }
+    r.T = T;
+    r.nq = nq;
+    r.nd = nd;
+    return SPA_OK;
+}
+
+// --------------------------------------------------------------------- the sweep
+struct Enq {
+    spa_ctx* c;
+    cudaStream_t st;
+    int64_t launches = 0;
+    cudaError_t e = cudaSuccess;
+    void ck(cudaError_t x)
+    {
+        if (e == cudaSuccess) e = x;
+        ++launches;
+    }
+};
+
+__global__ void k_set_f64(double* p, double v)
+{
+    if (threadIdx.x == 0) *p = v;
+}
+__global__ void k_adapt_lambda(double* lam, const unsigned long long* acc, double denom)
+{
+    if (threadIdx.x == 0 && denom > 0.0) *lam *= exp((double)*acc / denom - 0.574);
+}
+
+// log-likelihood of the current proposals (beta_p) into the partial sums
+void enq_loglik(Enq& q)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
+        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, q.st));
+    } else {
+        q.ck(launch_loglik_simt(w.beta_p, c->Xf, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
+    }
+}
+
+AcceptArgs accept_args(spa_ctx* c, unsigned long long* acc)
+{
+    Workspace& w = c->ws;
+    AcceptArgs a;
+    a.beta = w.beta;
+    a.beta_p = w.beta_p;
+    a.ll = w.ll;
+    a.lp = w.lp;
+    a.lin_p = w.lin_p;
+    a.lp_p = w.lp_p;
+    a.partial = w.partial;
+    if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        a.n_parts = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms).n_parts;
+        a.sp_scale = LN2;
+    } else {
+        a.n_parts = (int)((c->n + SIMT_TILE_N - 1) / SIMT_TILE_N);
+        a.sp_scale = 1.0;
+    }
+    a.ld_part = w.N_pad;
+    a.logw = nullptr;
+    a.acc_count = acc;
+    return a;
+}
+
+void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
+    const AcceptArgs a = accept_args(c, acc);
+    for (int mm = 0; mm < M; ++mm) {
+        const uint32_t m = m0 + (uint32_t)mm;
+        q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
+                               c->mean_f, c->v, w.N, (int)c->p, c->pr, c->rb.sched, t, m, c->rb.seed, 1, q.st));
+        enq_loglik(q);
+        q.ck(launch_accept(a, w.N, (int)c->p, 1, t, m, c->rb.seed, c->d_err, q.st));
+    }
+}
+
+void enq_resample(Enq& q, int t)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    q.ck(launch_resample_index(w.W, w.N, w.cum, w.idx, w.flag, t, c->rb.seed, 0.0, q.st));
+    q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, nullptr, nullptr, w.N, (int)c->p, w.flag,
+                       q.st));
+    q.ck(launch_copyback(w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, nullptr, nullptr, w.logw, w.W, w.N, (int)c->p,
+                         w.flag, q.st));
+}
+
+void enq_colstats(Enq& q, int t)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const int kind = c->cfg.move_kind == SPA_MOVE_MALA ? 1 : 0;
+    q.ck(launch_colstats(w.beta, w.W, w.N, (int)c->p, w.colpart, w.scale, kind, c->cfg.rw_scale,
+                         kind ? w.lambda : nullptr, c->cfg.sd_floor, c->rb.sched, t, q.st));
+    ++q.launches;  // two kernels
+}
+
+int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
+{
+    Enq q;
+    q.c = c;
+    q.st = c->stream();
+    Workspace& w = c->ws;
+    RunBufs& r = c->rb;
+    const spa_config& cfg = c->cfg;
+    const bool tc = cfg.precision == SPA_PREC_SPLIT_BF16;
+    const bool mala = cfg.move_kind == SPA_MOVE_MALA;
+    const int p = (int)c->p;
+    const double denom = (double)w.N * (double)M;
+    SummaryArgs sa;
+    sa.nq = cfg.n_quantiles;
+    sa.nd = cfg.n_deltas;
+    for (int k = 0; k < 8; ++k) {
+        sa.q[k] = cfg.quantiles[k];
+        sa.delta[k] = cfg.deltas[k];
+    }
+    if (q.e == cudaSuccess) q.e = cudaMemsetAsync(r.acc, 0, sizeof(unsigned long long) * (size_t)(T + 1), q.st);
+    if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
+    if (mala) {
+        k_set_f64<<<1, 32, 0, q.st>>>(w.lambda, cfg.mala_h);
+        q.ck(cudaGetLastError());
+    }
+    // t = 0: prior draws, their log-likelihoods, importance weights
+    q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
+    q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
+                           c->mean_f, c->v, w.N, p, c->pr, r.sched, 0, 0u, r.seed, 0, q.st));
+    enq_loglik(q);
+    AcceptArgs a0 = accept_args(c, nullptr);
+    a0.logw = w.logw;
+    q.ck(launch_accept(a0, w.N, p, 0, 0, 0u, r.seed, c->d_err, q.st));
+    const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
+    q.ck(launch_lse_ess(w.logw, w.W, w.N, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag, c->d_err, q.st));
+    uint32_t m_base = 0;
+    if (rm) {
+        enq_resample(q, 0);
+        for (int b = 0; b < cfg.burn_in_steps; ++b) {
+            unsigned long long* scratch = r.acc + T;
+            if (q.e == cudaSuccess) q.e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), q.st);
+            enq_colstats(q, 0);
+            enq_moves(q, 0, m_base, M, scratch);
+            if (mala) {
+                k_adapt_lambda<<<1, 32, 0, q.st>>>(w.lambda, scratch, denom);
+                q.ck(cudaGetLastError());
+            }
+            m_base += (uint32_t)M;
+        }
+        q.ck(launch_mark_uniform(w.N, 0, r.ess, r.res, w.flag, q.st));
+    }
+    for (int64_t t = 0; t < T; ++t) {
+        if (t > 0) {
+            q.ck(launch_reweight(w.beta, w.logw, w.lp, w.N, p, c->pr, r.sched, (int)t, c->d_err, q.st));
+            q.ck(launch_lse_ess(w.logw, w.W, w.N, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag, c->d_err, q.st));
+        }
+        enq_resample(q, (int)t);
+        enq_colstats(q, (int)t);
+        enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
+        q.ck(launch_summaries(w.beta, w.W, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, q.st));
+        if (mala) {
+            k_adapt_lambda<<<1, 32, 0, q.st>>>(w.lambda, r.acc + t, denom);
+            q.ck(cudaGetLastError());
+        }
+    }
+    q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
+    *err_out = q.e;
+    return q.launches;
+}
+
+int validate_config(spa_ctx* c, const spa_config& k)
+{
+    if (k.move_kind != SPA_MOVE_RW && k.move_kind != SPA_MOVE_MALA) return fail(c, SPA_EINVAL, "move_kind");
+    if (k.move_kind == SPA_MOVE_MALA) return fail(c, SPA_EUNSUPPORTED, "MALA moves are not available in this build");
+    if (k.precision != SPA_PREC_SPLIT_BF16 && k.precision != SPA_PREC_FP32) return fail(c, SPA_EINVAL, "precision");
+    if (k.init_mode != SPA_INIT_PRIOR_IS && k.init_mode != SPA_INIT_RESAMPLE_MOVE) return fail(c, SPA_EINVAL, "init_mode");
+    if (k.burn_in_steps < 0) return fail(c, SPA_EINVAL, "burn_in_steps");
+    if (k.n_quantiles < 0 || k.n_quantiles > SPA_MAX_QUANTILES) return fail(c, SPA_EINVAL, "n_quantiles");
+    for (int i = 0; i < k.n_quantiles; ++i)
+        if (!(k.quantiles[i] > 0.0 && k.quantiles[i] < 1.0)) return fail(c, SPA_EINVAL, "quantile level");
+    if (k.n_deltas < 0 || k.n_deltas > SPA_MAX_DELTAS) return fail(c, SPA_EINVAL, "n_deltas");
+    for (int i = 0; i < k.n_deltas; ++i)
+        if (!(k.deltas[i] > 0.0) || !std::isfinite(k.deltas[i])) return fail(c, SPA_EINVAL, "delta");
+    if (!(k.ess_frac >= 0.0 && k.ess_frac <= 1.0)) return fail(c, SPA_EINVAL, "ess_frac");
+    if (!(k.rw_scale > 0.0) || !(k.mala_h > 0.0) || !(k.sd_floor >= 0.0)) return fail(c, SPA_EINVAL, "scale parameters");
+    return SPA_OK;
+}
+
+int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
+{
+    const int64_t n = c->n, p = c->p;
+    cudaStream_t st = c->stream();
+    CK(cudaMemcpyAsync(c->G, G, (size_t)(n * p), cudaMemcpyHostToDevice, st), "copy G");
+    CK(cudaMemcpyAsync(c->y, y, (size_t)n, cudaMemcpyHostToDevice, st), "copy y");
+    CK(cudaMemsetAsync(c->sums, 0, sizeof(unsigned long long) * (size_t)(3 * p + 1), st), "memset sums");
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st), "memset err");
+    CK(launch_store_sums(c->G, c->y, n, p, c->sums, c->d_err, st), "store sums");
+    CK(launch_store_finish(c->G, n, p, c->Kp, c->sums, c->mean, c->sd, c->v, c->l2e_s, c->mean_f, c->Gbf, c->Xf, c->d_err,
+                           st),
+       "store pack");
+    return read_error_word(c);
+}
+
+void destroy(spa_ctx* c)
+{
+    if (!c) return;
+    drop_graph(c);
+    free_workspace(c->ws);
+    free_runbufs(c->rb);
+    dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
+    dfree(c->l2e_s); dfree(c->mean_f); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+void spa_config_default(spa_config* k)
+{
+    if (!k) return;
+    std::memset(k, 0, sizeof(*k));
+    k->move_kind = SPA_MOVE_RW;
+    k->precision = SPA_PREC_SPLIT_BF16;
+    k->init_mode = SPA_INIT_PRIOR_IS;
+    k->burn_in_steps = 0;
+    k->n_quantiles = 3;
+    k->quantiles[0] = 0.05;
+    k->quantiles[1] = 0.5;
+    k->quantiles[2] = 0.95;
+    k->n_deltas = 2;
+    k->deltas[0] = 0.05;
+    k->deltas[1] = 0.1;
+    k->ess_frac = 0.75;
+    k->rw_scale = 2.38;
+    k->mala_h = 1.65;
+    k->sd_floor = 1e-3;
+    k->stream = nullptr;
+}
+
+int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double nu, spa_ctx** out)
+{
+    if (!out) return fail(nullptr, SPA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!G || !y) return fail(nullptr, SPA_EINVAL, "G or y is NULL");
+    if (n < 1 || p < 1 || n > (int64_t)1 << 24 || p > 8192) return fail(nullptr, SPA_EINVAL, "n or p out of range");
+    if (!(nu > 0.0)) return fail(nullptr, SPA_EINVAL, "nu must be > 0 (or +INFINITY)");
+    spa_ctx* c = new (std::nothrow) spa_ctx();
+    if (!c) return fail(nullptr, SPA_ENOMEM, "host allocation");
+    int rc = check_device(c);
+    if (rc != SPA_OK) {
+        g_thread_error = c->err;
+        destroy(c);
+        return rc;
+    }
+    spa_config_default(&c->cfg);
+    c->n = n;
+    c->p = p;
+    c->Kp = (int)round_up(p + 1, 64);
+    c->nu = nu;
+    c->pr.de = std::isinf(nu) ? 1 : 0;
+    c->pr.a = c->pr.de ? 1.0f : (float)nu;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+#define CA(ptr, cnt) \
+    if (e == cudaSuccess) e = dalloc(&c->ptr, (size_t)(cnt))
+    CA(G, n * p);
+    CA(y, n);
+    CA(sums, 3 * p + 1);
+    CA(mean, p); CA(sd, p); CA(v, p); CA(unit_c, 1);
+    CA(l2e_s, p); CA(mean_f, p);
+    CA(Xf, n * p);
+    CA(Gbf, n * c->Kp);
+    CA(d_err, 1);
+#undef CA
+    if (e != cudaSuccess) {
+        g_thread_error = std::string("device allocation: ") + cudaGetErrorString(e);
+        destroy(c);
+        return e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA;
+    }
+    const double one = 1.0;
+    e = cudaMemcpy(c->unit_c, &one, sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        g_thread_error = cudaGetErrorString(e);
+        destroy(c);
+        return SPA_ECUDA;
+    }
+    rc = upload_data(c, G, y);
+    if (rc != SPA_OK) {
+        g_thread_error = c->err;
+        destroy(c);
+        return rc;
+    }
+    *out = c;
+    return SPA_OK;
+}
+
+int spa_set_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!G || !y) return fail(c, SPA_EINVAL, "G or y is NULL");
+    return upload_data(c, G, y);
+}
+
+int spa_set_config(spa_ctx* c, const spa_config* k)
+{
+    if (!c || !k) return fail(c, SPA_EINVAL, "NULL argument");
+    int rc = validate_config(c, *k);
+    if (rc != SPA_OK) return rc;
+    if (std::memcmp(&c->cfg, k, sizeof(spa_config)) != 0) drop_graph(c);
+    c->cfg = *k;
+    return SPA_OK;
+}
+
+int spa_get_config(const spa_ctx* c, spa_config* k)
+{
+    if (!c || !k) return fail(nullptr, SPA_EINVAL, "NULL argument");
+    *k = c->cfg;
+    return SPA_OK;
+}
+
+void spa_destroy(spa_ctx* c) { destroy(c); }
+
+const char* spa_last_error(const spa_ctx* c)
+{
+    if (c) return c->err.c_str();
+    return g_thread_error.c_str();
+}
+
+int64_t spa_last_launch_count(const spa_ctx* c) { return c ? c->last_launches : 0; }
+
+static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int64_t T, int64_t N, int32_t M,
+                      uint64_t seed)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!sched) return fail(c, SPA_EINVAL, "schedule is NULL");
+    if (T < 1 || T > (int64_t)1 << 24) return fail(c, SPA_EINVAL, "T out of range");
+    if (N < 1 || N > (int64_t)1 << 22) return fail(c, SPA_EINVAL, "N out of range");
+    if (M < 0 || M > 65535) return fail(c, SPA_EINVAL, "moves_per_step out of range");
+    if (!sched_on_device)
+        for (int64_t t = 0; t < T; ++t)
+            if (!(sched[t] > 0.0) || !std::isfinite(sched[t])) return fail(c, SPA_EINVAL, "schedule values must be finite and > 0");
+    int rc = validate_config(c, c->cfg);
+    if (rc != SPA_OK) return rc;
+    rc = ensure_workspace(c, N);
+    if (rc != SPA_OK) return rc;
+    rc = ensure_runbufs(c, T);
+    if (rc != SPA_OK) return rc;
+    cudaStream_t st = c->stream();
+    CK(cudaMemcpyAsync(c->rb.sched, sched, sizeof(double) * (size_t)T,
+                       sched_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+       "copy schedule");
+    CK(cudaMemcpyAsync(c->rb.seed, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st), "copy seed");
+    GraphKey key;
+    key.T = T;
+    key.N = N;
+    key.M = M;
+    key.cfg = c->cfg;
+    if (!c->gexec || !(key == c->gkey)) {
+        drop_graph(c);
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t ee = cudaSuccess;
+        const int64_t launches = enqueue_sweep(c, T, M, &ee);
+        cudaError_t ec = cudaStreamEndCapture(st, &g);
+        if (ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(c, ee, "enqueue sweep");
+        }
+        if (ec != cudaSuccess) return cuda_fail(c, ec, "end capture");
+        cudaError_t ei = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            c->gexec = nullptr;
+            return cuda_fail(c, ei, "graph instantiate");
+        }
+        c->gkey = key;
+        c->graph_launches = launches;
+    }
+    CK(cudaGraphLaunch(c->gexec, st), "graph launch");
+    c->last_launches = c->graph_launches;
+    return SPA_OK;
+}
+
+int spa_run(spa_ctx* c, const double* sched, int64_t T, int64_t N, int32_t M, uint64_t seed, spa_result* out)
+{
+    int rc = run_common(c, sched, false, T, N, M, seed);
+    if (rc != SPA_OK) return rc;
+    cudaStream_t st = c->stream();
+    const int64_t p = c->p;
+    const int nq = c->cfg.n_quantiles, nd = c->cfg.n_deltas;
+    if (out) {
+        RunBufs& r = c->rb;
+        auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+            return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+        };
+        CK(d2h(out->mean, r.mean, sizeof(double) * (size_t)(T * p)), "copy mean");
+        CK(d2h(out->quantile, r.quant, sizeof(double) * (size_t)(T * p * nq)), "copy quantiles");
+        CK(d2h(out->conc, r.conc, sizeof(double) * (size_t)(T * p * nd)), "copy concentrations");
+        CK(d2h(out->ess, r.ess, sizeof(double) * (size_t)T), "copy ess");
+        CK(d2h(out->log_z_inc, r.logz, sizeof(double) * (size_t)T), "copy log z");
+        CK(d2h(out->accept_rate, r.accrate, sizeof(double) * (size_t)T), "copy acceptance");
+        CK(d2h(out->resampled, r.res, (size_t)T), "copy resampled");
+    }
+    return read_error_word(c);
+}
+
+int spa_run_device(spa_ctx* c, const double* sched, int64_t T, int64_t N, int32_t M, uint64_t seed, spa_result* out)
+{
+    int rc = run_common(c, sched, true, T, N, M, seed);
+    if (rc != SPA_OK) return rc;
+    if (out) {
+        cudaStream_t st = c->stream();
+        const int64_t p = c->p;
+        const int nq = c->cfg.n_quantiles, nd = c->cfg.n_deltas;
+        RunBufs& r = c->rb;
+        auto d2d = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+            return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st) : cudaSuccess;
+        };
+        CK(d2d(out->mean, r.mean, sizeof(double) * (size_t)(T * p)), "copy mean");
+        CK(d2d(out->quantile, r.quant, sizeof(double) * (size_t)(T * p * nq)), "copy quantiles");
+        CK(d2d(out->conc, r.conc, sizeof(double) * (size_t)(T * p * nd)), "copy concentrations");
+        CK(d2d(out->ess, r.ess, sizeof(double) * (size_t)T), "copy ess");
+        CK(d2d(out->log_z_inc, r.logz, sizeof(double) * (size_t)T), "copy log z");
+        CK(d2d(out->accept_rate, r.accrate, sizeof(double) * (size_t)T), "copy acceptance");
+        CK(d2d(out->resampled, r.res, (size_t)T), "copy resampled");
+    }
+    return SPA_OK;
+}
+
+int spa_sync(spa_ctx* c)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    return read_error_word(c);
+}
+
+int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_result* outs)
+{
+    if (!ctxs || !args || R < 0) return fail(nullptr, SPA_EINVAL, "bad batch arguments");
+    for (int32_t r = 0; r < R; ++r) {
+        spa_ctx* c = ctxs[r];
+        int rc = run_common(c, args->schedules[r], false, args->T[r], args->N[r], args->moves_per_step[r], args->seeds[r]);
+        if (rc != SPA_OK) {
+            g_thread_error = c ? c->err : "NULL context";
+            return rc;
+        }
+    }
+    for (int32_t r = 0; r < R; ++r) {
+        spa_ctx* c = ctxs[r];
+        cudaStream_t st = c->stream();
+        const int64_t T = args->T[r], p = c->p;
+        const int nq = c->cfg.n_quantiles, nd = c->cfg.n_deltas;
+        RunBufs& rb = c->rb;
+        spa_result* out = outs ? &outs[r] : nullptr;
+        if (out) {
+            auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+                return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+            };
+            CK(d2h(out->mean, rb.mean, sizeof(double) * (size_t)(T * p)), "copy mean");
+            CK(d2h(out->quantile, rb.quant, sizeof(double) * (size_t)(T * p * nq)), "copy quantiles");
+            CK(d2h(out->conc, rb.conc, sizeof(double) * (size_t)(T * p * nd)), "copy concentrations");
+            CK(d2h(out->ess, rb.ess, sizeof(double) * (size_t)T), "copy ess");
+            CK(d2h(out->log_z_inc, rb.logz, sizeof(double) * (size_t)T), "copy log z");
+            CK(d2h(out->accept_rate, rb.accrate, sizeof(double) * (size_t)T), "copy acceptance");
+            CK(d2h(out->resampled, rb.res, (size_t)T), "copy resampled");
+        }
+        int rc = read_error_word(c);
+        if (rc != SPA_OK) {
+            g_thread_error = c->err;
+            return rc;
+        }
+    }
+    return SPA_OK;
+}
+
+// ------------------------------------------------------------ per-step entry points
+static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double* ll, bool ll_dev, cudaStream_t st_user)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!B || !ll || N < 1 || N > (int64_t)1 << 22) return fail(c, SPA_EINVAL, "bad arguments");
+    int rc = ensure_workspace(c, N);
+    if (rc != SPA_OK) return rc;
+    cudaStream_t st = st_user ? st_user : c->stream();
+    Workspace& w = c->ws;
+    const int64_t p = c->p;
+    const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
+    if (st_user) CK(cudaStreamSynchronize(c->stream()), "sync context stream");
+    CK(cudaMemcpyAsync(w.beta, B, sizeof(float) * (size_t)(N * p), B_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       st),
+       "copy B");
+    CK(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
+                         c->mean_f, c->v, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st),
+       "pack");
+    if (tc) {
+        const TcPlan plan = tc_plan(c->n, (int)p, w.N_pad, c->num_sms);
+        CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, st), "loglik tc");
+    } else {
+        CK(launch_loglik_simt(w.beta_p, c->Xf, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
+    }
+    AcceptArgs a = accept_args(c, nullptr);
+    a.ll = ll_dev ? ll : w.ll;
+    a.lp = nullptr;
+    CK(launch_accept(a, N, (int)p, 0, 0, 0u, nullptr, c->d_err, st), "finish loglik");
+    if (!ll_dev) CK(cudaMemcpyAsync(ll, w.ll, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st), "copy ll");
+    if (st != c->stream()) CK(cudaStreamSynchronize(st), "sync");
+    return read_error_word(c);
+}
+
+int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (c->ws.N != N || N < 1 || reps < 0) return fail(c, SPA_EINVAL, "no workspace of N particles");
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : c->stream();
+    Workspace& w = c->ws;
+    for (int32_t k = 0; k < reps; ++k) {
+        if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+            const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
+            CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, st), "loglik tc");
+        } else {
+            CK(launch_loglik_simt(w.beta_p, c->Xf, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");
+        }
+    }
+    return SPA_OK;
+}
+
+int spa_loglik(spa_ctx* c, const float* B, int64_t N, double* ll_out)
+{
+    return loglik_impl(c, B, false, N, ll_out, false, nullptr);
+}
+
+int spa_loglik_device(spa_ctx* c, const float* B, int64_t N, double* ll, void* stream)
+{
+    return loglik_impl(c, B, true, N, ll, true, static_cast<cudaStream_t>(stream));
+}
+
+static int grad_impl(spa_ctx* c, const float* B, bool dev, int64_t N, double cs, double* ll, float* grad,
+                     cudaStream_t st_user)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!B || !grad || N < 1 || N > (int64_t)1 << 22) return fail(c, SPA_EINVAL, "bad arguments");
+    if (!(cs >= 0.0) || !std::isfinite(cs)) return fail(c, SPA_EINVAL, "c must be >= 0");
+    int rc = ensure_workspace(c, N);
+    if (rc != SPA_OK) return rc;
+    Workspace& w = c->ws;
+    const int64_t p = c->p, n = c->n;
+    if (!w.eta) {
+        const int64_t tiles = (n + SIMT_TILE_N - 1) / SIMT_TILE_N;
+        cudaError_t e = dalloc(&w.eta, (size_t)(N * n + tiles * N));
+        if (e == cudaSuccess) e = dalloc(&w.grad, (size_t)(N * p));
+        if (e != cudaSuccess) return cuda_fail(c, e, "gradient scratch");
+    }
+    cudaStream_t st = st_user ? st_user : c->stream();
+    if (st_user) CK(cudaStreamSynchronize(c->stream()), "sync context stream");
+    CK(cudaMemcpyAsync(w.beta, B, sizeof(float) * (size_t)(N * p), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+       "copy B");
+    CK(launch_grad_simt(w.beta, c->Xf, c->y, N, n, (int)p, w.eta, dev ? grad : w.grad, dev ? ll : (ll ? w.ll : nullptr),
+                        c->pr, cs, st),
+       "gradient");
+    if (!dev) {
+        CK(cudaMemcpyAsync(grad, w.grad, sizeof(float) * (size_t)(N * p), cudaMemcpyDeviceToHost, st), "copy grad");
+        if (ll) CK(cudaMemcpyAsync(ll, w.ll, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st), "copy ll");
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    return read_error_word(c);
+}
+
+int spa_grad(spa_ctx* c, const float* B, int64_t N, double cs, double* ll_out, float* grad_out)
+{
+    return grad_impl(c, B, false, N, cs, ll_out, grad_out, nullptr);
+}
+
+int spa_grad_device(spa_ctx* c, const float* B, int64_t N, double cs, double* ll, float* grad, void* stream)
+{
+    return grad_impl(c, B, true, N, cs, ll, grad, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- context-free entry points
+namespace {
+
+struct Scratch {
+    std::vector<void*> ptrs;
+    ~Scratch()
+    {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    T* get(size_t count)
+    {
+        void* p = nullptr;
+        if (cudaMalloc(&p, (count ? count : 1) * sizeof(T)) != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T*>(p);
+    }
+};
+
+int finish_free(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamPerThread);
+    if (e != cudaSuccess) return fail(nullptr, e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA,
+                                      std::string(what) + ": " + cudaGetErrorString(e));
+    return SPA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spa_resample_systematic(const double* W, int64_t N, double u, int32_t* idx)
+{
+    if (!W || !idx || N < 1 || N > (int64_t)1 << 24 || !(u >= 0.0 && u < 1.0))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    Scratch s;
+    double* dW = s.get<double>(N);
+    double* dC = s.get<double>(N + (N + 255) / 256 + 1);
+    int32_t* dI = s.get<int32_t>(N);
+    if (!dW || !dC || !dI) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dW, W, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_resample_index(dW, N, dC, dI, nullptr, 0, nullptr, u, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, dI, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "resample");
+}
+
+int spa_prior_logpdf(double nu, double cs, const float* beta, int64_t k, double* out)
+{
+    if (!beta || !out || k < 0 || !(nu > 0.0) || !(cs > 0.0) || !std::isfinite(cs))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (k == 0) return SPA_OK;
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    PriorArgs pr{std::isinf(nu) ? 1.0f : (float)nu, std::isinf(nu) ? 1 : 0};
+    Scratch s;
+    float* dB = s.get<float>(k);
+    double* dO = s.get<double>(k);
+    if (!dB || !dO) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dB, beta, sizeof(float) * (size_t)k, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_prior_logpdf(pr, cs, dB, k, dO, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dO, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "prior logpdf");
+}
+
+int spa_incr_weight(double nu, double c_prev, double c_new, const float* B, int64_t N, int64_t p, double* out)
+{
+    if (!B || !out || N < 1 || p < 1 || !(nu > 0.0) || !(c_prev > 0.0) || !(c_new > 0.0) || !std::isfinite(c_prev) ||
+        !std::isfinite(c_new))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    PriorArgs pr{std::isinf(nu) ? 1.0f : (float)nu, std::isinf(nu) ? 1 : 0};
+    Scratch s;
+    float* dB = s.get<float>(N * p);
+    double* dW = s.get<double>(N);
+    double* dL = s.get<double>(N);
+    double* dS = s.get<double>(2);
+    uint32_t* dE = s.get<uint32_t>(1);
+    if (!dB || !dW || !dL || !dS || !dE) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    const double sched[2] = {c_prev, c_new};
+    cudaError_t e = cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(N * p), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dS, sched, sizeof(sched), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dW, 0, sizeof(double) * (size_t)N, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dE, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_reweight(dB, dW, dL, N, (int)p, pr, dS, 1, dE, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dW, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "incremental weight");
+}
+
+int spa_lse_ess(const double* logw, int64_t N, double* lse, double* ess)
+{
+    if (!logw || N < 1) return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    Scratch s;
+    double* dL = s.get<double>(N);
+    double* dW = s.get<double>(N);
+    double* dOut = s.get<double>(2);
+    uint8_t* dR = s.get<uint8_t>(1);
+    int* dF = s.get<int>(1);
+    uint32_t* dE = s.get<uint32_t>(1);
+    if (!dL || !dW || !dOut || !dR || !dF || !dE) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dL, logw, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dE, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = launch_lse_ess(dL, dW, N, 0, 0, 0.0, dOut + 1, dOut, dR, dF, dE, st);
+    double h[2] = {0.0, 0.0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, dOut, sizeof(h), cudaMemcpyDeviceToHost, st);
+    int rc = finish_free(e, "lse/ess");
+    if (rc != SPA_OK) return rc;
+    if (lse) *lse = h[0];
+    if (ess) *ess = h[1];
+    return SPA_OK;
+}
+
+int spa_summaries(const float* B, const double* W, int64_t N, int64_t p, const double* q, int32_t nq,
+                  const double* deltas, int32_t nd, double* mean, double* quant, double* conc)
+{
+    if (!B || !W || N < 1 || p < 1 || nq < 0 || nq > 8 || nd < 0 || nd > 8 || (nq && !q) || (nd && !deltas))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    SummaryArgs sa;
+    sa.nq = nq;
+    sa.nd = nd;
+    for (int k = 0; k < 8; ++k) {
+        sa.q[k] = k < nq ? q[k] : 0.5;
+        sa.delta[k] = k < nd ? deltas[k] : 1.0;
+    }
+    Scratch s;
+    float* dB = s.get<float>(N * p);
+    double* dW = s.get<double>(N);
+    double* dM = s.get<double>(p);
+    double* dQ = s.get<double>(p * (nq ? nq : 1));
+    double* dC = s.get<double>(p * (nd ? nd : 1));
+    if (!dB || !dW || !dM || !dQ || !dC) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(N * p), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dW, W, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_summaries(dB, dW, N, (int)p, sa, 0, dM, nq ? dQ : nullptr, dC, st);
+    if (e == cudaSuccess && mean) e = cudaMemcpyAsync(mean, dM, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && quant && nq)
+        e = cudaMemcpyAsync(quant, dQ, sizeof(double) * (size_t)(p * nq), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && conc && nd)
+        e = cudaMemcpyAsync(conc, dC, sizeof(double) * (size_t)(p * nd), cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "summaries");
+}
+
+int spa_philox4x32_10(const uint32_t* ctr, const uint32_t* key, int64_t count, uint32_t* out)
+{
+    if (!ctr || !key || !out || count < 0) return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (count == 0) return SPA_OK;
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    Scratch s;
+    uint32_t* dC = s.get<uint32_t>(4 * count);
+    uint32_t* dO = s.get<uint32_t>(4 * count);
+    if (!dC || !dO) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dC, ctr, sizeof(uint32_t) * 4 * (size_t)count, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_philox(dC, make_uint2(key[0], key[1]), count, dO, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dO, sizeof(uint32_t) * 4 * (size_t)count, cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "philox");
+}
+
+int spa_normals(uint64_t seed, uint32_t particle, uint32_t t, uint32_t m, int64_t p, float* out)
+{
+    if (!out || p < 1) return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    Scratch s;
+    float* dO = s.get<float>(p);
+    if (!dO) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = launch_normals(seed, particle, t, m, p, dO, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dO, sizeof(float) * (size_t)p, cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "normals");
+}
+
+int spa_prior_sample(uint64_t seed, double nu, double cs, int64_t N, int64_t p, float* out)
+{
+    if (!out || N < 1 || p < 1 || !(nu > 0.0) || !(cs > 0.0)) return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    PriorArgs pr{std::isinf(nu) ? 1.0f : (float)nu, std::isinf(nu) ? 1 : 0};
+    Scratch s;
+    float* dO = s.get<float>(N * p);
+    if (!dO) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = launch_prior_sample(seed, pr, cs, N, p, dO, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dO, sizeof(float) * (size_t)(N * p), cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "prior sample");
+}
+
+}  // extern "C"

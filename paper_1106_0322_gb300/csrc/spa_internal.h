@@ -1,0 +1,148 @@
+// spa_internal.h -- host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spa {
+
+constexpr double LN2 = 0.69314718055994530941723212145818;
+constexpr double LOG2E = 1.4426950408889634073599246810019;
+
+// Launch helpers return cudaGetLastError() of the launch.
+
+// ----------------------------------------------------------- genotype store
+// Integer column sums of G (S1 = sum g, S2 = sum g^2, SY = sum y g) and the case count,
+// with device-side validation of G in {0,1,2} and y in {0,1} (DERR_INPUT).
+cudaError_t launch_store_sums(const int8_t* G, const uint8_t* y, int64_t n, int64_t p,
+                              unsigned long long* sums /* [3p + 1], zeroed */, uint32_t* err,
+                              cudaStream_t st);
+// Means m_j, population sds s_j and v_j = sum_i y_i x_ij from the integer sums; per-column
+// FP32 constants; the BF16 GEMM operand [n][Kp] = (g_i0..g_i,p-1, 1, 0...); the FP32
+// standardised X [n][p].
+cudaError_t launch_store_finish(const int8_t* G, int64_t n, int64_t p, int Kp, const unsigned long long* sums,
+                                double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f,
+                                __nv_bfloat16* Gbf, float* Xf, uint32_t* err, cudaStream_t st);
+
+// ------------------------------------------------------------- SMC kernels
+struct PriorArgs {
+    float a;   // degrees of freedom (ignored for the double exponential)
+    int de;    // 1: double-exponential prior
+};
+
+cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const double* sched, int t0,
+                              const uint64_t* seed, cudaStream_t st);
+
+// Random-walk proposal (noise = 1) or plain packing of beta (noise = 0): writes beta_p,
+// lin_p = sum_j beta'_j v_j, lp_p = log prior at c_t, and (A != NULL) the split-BF16
+// GEMM operand row [hi(bt) | lo(bt)] with bt_j = beta'_j log2(e)/s_j and the offset
+// o = -sum_j m_j bt_j in column p.
+cudaError_t launch_propose_rw(const float* beta, float* beta_p, __nv_bfloat16* A, int ldA, int Kp,
+                              double* lin_p, double* lp_p, const float* sigma, const float* l2e_over_s,
+                              const float* mean_f, const double* v, int64_t N, int p, PriorArgs pr,
+                              const double* sched, int t, uint32_t m, const uint64_t* seed, int noise,
+                              cudaStream_t st);
+
+// Finish a log-likelihood from the GEMM partial sums and either store it (mode 0) or run
+// the Metropolis-Hastings test against the current state (mode 1).
+struct AcceptArgs {
+    float* beta;
+    const float* beta_p;
+    double* ll;
+    double* lp;
+    const double* lin_p;
+    const double* lp_p;
+    const float* partial;
+    int n_parts;
+    int64_t ld_part;
+    double sp_scale;
+    double* logw;                    // mode 0: logw = ll (prior-IS weights); may be NULL
+    unsigned long long* acc_count;  // mode 1: accepted-proposal counter; may be NULL
+};
+cudaError_t launch_accept(const AcceptArgs& a, int64_t N, int p, int mode, int t, uint32_t m,
+                          const uint64_t* seed, uint32_t* err, cudaStream_t st);
+
+cudaError_t launch_reweight(const float* beta, double* logw, double* lp, int64_t N, int p, PriorArgs pr,
+                            const double* sched, int t, uint32_t* err, cudaStream_t st);
+
+// mode 0: step t >= 1 (log_z[t] = LSE); 1: prior-IS start (log_z[0] = LSE - log N);
+// 2: resample-move start (log_z[0] = LSE - log N, resampling forced, ESS not recorded).
+cudaError_t launch_lse_ess(double* logw, double* W, int64_t N, int t, int mode, double ess_frac, double* ess_out,
+                           double* logz_out, uint8_t* resampled_out, int* flag, uint32_t* err, cudaStream_t st);
+
+cudaError_t launch_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* resampled_out, int* flag, cudaStream_t st);
+
+// Systematic resampling: ancestor indices (bit-exact blocked cumulative sum), gather of
+// particle rows into scratch and copy back. All no-ops when *flag == 0.
+cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32_t* idx, const int* flag,
+                                  int t, const uint64_t* seed, double u_override, cudaStream_t st);
+cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const double* ll,
+                          const double* lp, double* ll_tmp, double* lp_tmp, const float* g, float* g_tmp,
+                          int64_t N, int p, const int* flag, cudaStream_t st);
+cudaError_t launch_copyback(float* beta, const float* beta_tmp, double* ll, double* lp, const double* ll_tmp,
+                            const double* lp_tmp, float* g, const float* g_tmp, double* logw, double* W,
+                            int64_t N, int p, const int* flag, cudaStream_t st);
+
+// Weighted column moments -> per-coordinate proposal scales. kind 0 (RW):
+// sigma_j = lam/sqrt(p) max(sd_j, floor c); kind 1 (MALA): D_j = max(var_j, (floor c)^2).
+constexpr int COLSTAT_SPLITS = 32;
+cudaError_t launch_colstats(const float* beta, const double* W, int64_t N, int p, double* part, float* scale_out,
+                            int kind, double lam_const, const double* lam_dev, double sd_floor,
+                            const double* sched, int t, cudaStream_t st);
+
+// Per-scale summaries of Section 5 for step t.
+struct SummaryArgs {
+    int nq;
+    double q[8];
+    int nd;
+    double delta[8];
+};
+cudaError_t launch_summaries(const float* beta, const double* W, int64_t N, int p, const SummaryArgs& s, int t,
+                             double* mean, double* quant, double* conc, cudaStream_t st);
+
+cudaError_t launch_accept_rate(const unsigned long long* acc_count, int T, double denom, double* rate,
+                               cudaStream_t st);
+
+// Stream-test helpers.
+cudaError_t launch_philox(const uint32_t* ctr, uint2 key, int64_t count, uint32_t* out, cudaStream_t st);
+cudaError_t launch_normals(uint64_t seed, uint32_t particle, uint32_t t, uint32_t m, int64_t p, float* out,
+                           cudaStream_t st);
+cudaError_t launch_prior_sample(uint64_t seed, PriorArgs pr, double c, int64_t N, int64_t p, float* out,
+                                cudaStream_t st);
+cudaError_t launch_prior_logpdf(PriorArgs pr, double c, const float* beta, int64_t k, double* out,
+                                cudaStream_t st);
+
+// ------------------------------------------------------------ likelihood
+// tcgen05 split-BF16 GEMM with fused softplus reduction. partial[(nt*2 + h)*N_pad + i]
+// receives sum over the h-th half of n-tile nt of log2(1 + 2^(eta_i log2 e)).
+struct TcPlan {
+    int BN;          // individuals per n-tile (128 or 256)
+    int n_tiles;     // ceil(n / BN)
+    int m_tiles;     // N_pad / 128
+    int kblocks;     // active 64-wide k-blocks of each half
+    int ksteps;      // active 16-wide k-steps of each half: ceil((p+1)/16)
+    int grid;        // persistent CTAs
+    int n_parts;     // partial sums per particle = 2 * n_tiles
+};
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms);
+// Opt the tensor-core kernels into their dynamic shared memory (once per device, before any capture).
+cudaError_t tc_init_attributes();
+bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp);
+bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN);
+cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n,
+                             int Kp, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st);
+
+// Plain FP32 SIMT path: partial[nt * N_pad + i] = sum over 64-individual tile nt of
+// softplus(eta_i) (natural units).
+constexpr int SIMT_TILE_N = 64;
+cudaError_t launch_loglik_simt(const float* beta_p, const float* Xf, int64_t N, int64_t n, int p, float* partial,
+                               int64_t N_pad, cudaStream_t st);
+
+// Plain FP32 gradient: eta = B X^T materialised, r = y - logit^{-1}(eta); grad = r X
+// (+ prior gradient at c when c > 0); ll = sum y eta - softplus(eta).
+cudaError_t launch_grad_simt(const float* B, const float* Xf, const uint8_t* y, int64_t N, int64_t n, int p,
+                             float* eta_scratch, float* grad, double* ll, PriorArgs pr, double c, cudaStream_t st);
+
+}  // namespace spa

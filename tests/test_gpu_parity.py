@@ -1,0 +1,279 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Integer and index work is compared bit for bit (Philox outputs, resampling ancestors);
+floating point within the bounds stated in include/spa.h and below. Inputs are seeded
+and synthetic (paper_1106_0322_gb300.synth), shaped like the paper's hit regions.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_0322_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def spa():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1106_0322_gb300 as mod
+
+    return mod
+
+
+def split_bound(G, B, p):
+    """Per-particle bound of the split-BF16 log-likelihood error (include/spa.h)."""
+    Gd = G.astype(np.float64)
+    m = Gd.mean(0)
+    s = Gd.std(0)
+    bt = np.abs(B.astype(np.float64) / s)  # (N, p)
+    off = np.abs((B.astype(np.float64) / s) @ m)  # (N,)
+    S1 = Gd @ bt.T + off[None, :]  # (n, N): sum_j |g_ij bt_j| + |o|
+    X = (Gd - m) / s
+    eta = B.astype(np.float64) @ X.T  # (N, n)
+    S2 = np.logaddexp(0.0, eta).sum(axis=1)
+    n = G.shape[0]
+    return (2.0 ** -15 + (2 * p + 2) * 2.0 ** -23) * S1.sum(axis=0) + 2.0 ** -20 * n + 2.0 ** -21 * S2
+
+
+# --------------------------------------------------------------- random streams
+def test_philox_bit_exact(spa):
+    rng = np.random.default_rng(0)
+    ctr = rng.integers(0, 2 ** 32, size=(5000, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0xDEADBEEF, 0x12345678], np.uint32)
+    got = spa.philox4x32_10(ctr, key)
+    for k in range(0, 5000, 97):
+        assert got[k].tolist() == oracle.philox4x32_10(ctr[k], key).tolist()
+    kat = spa.philox4x32_10(np.zeros((1, 4), np.uint32), np.zeros(2, np.uint32))
+    assert kat[0].tolist() == [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]
+
+
+@pytest.mark.parametrize("p", [1, 3, 4, 37, 200])
+def test_normals_match_oracle(spa, p):
+    for (particle, t, m) in [(0, 0, 0), (17, 3, 5), (8191, 199, 9)]:
+        g = spa.normals(1234567, particle, t, m, p).astype(np.float64)
+        o = oracle.normals(1234567, particle, t, m, p)
+        assert np.all(np.abs(g - o) <= 2e-6 * (1 + np.abs(o)))
+
+
+@pytest.mark.parametrize("nu,c", [(1.0, 0.01), (4.0, 0.3), (math.inf, 0.2)])
+def test_prior_sample_matches_oracle(spa, nu, c):
+    g = spa.prior_sample(99, nu, c, 500, 7).astype(np.float64)
+    o = oracle.prior_sample(99, nu, c, 500, 7)
+    assert np.all(np.abs(g - o) <= 2e-5 * np.abs(o) + 1e-30)
+
+
+# ------------------------------------------------------------------ prior terms
+@pytest.mark.parametrize("nu,c", [(1.0, 1.0), (4.0, 0.01), (16.0, 3e-4), (math.inf, 0.5)])
+def test_prior_logpdf(spa, nu, c):
+    beta = synth.random_particles(1, 1000, 3 * c, seed=5)[0]
+    g = spa.prior_logpdf(nu, c, beta)
+    o = oracle.prior_logpdf(nu, c, beta.astype(np.float64))
+    assert np.all(np.abs(g - o) <= 1e-6 * (1 + np.abs(o)))
+
+
+@pytest.mark.parametrize("nu", [1.0, 4.0, math.inf])
+def test_incremental_weight(spa, nu):
+    B = synth.random_particles(300, 200, 0.05, seed=6)
+    for cp, cn in [(0.01, 0.0105), (0.5, 0.3), (1e-3, 1e-3)]:
+        g = spa.incr_weight(nu, cp, cn, B)
+        o = np.array([oracle.log_incr_weight(nu, cp, cn, B[k].astype(np.float64)) for k in range(300)])
+        scale = 200 * abs(math.log(cn / cp)) + np.abs(B).sum(1) / min(cp, cn) * abs(cn - cp) / max(cp, cn) * (
+            nu + 1 if math.isfinite(nu) else 1)
+        assert np.all(np.abs(g - o) <= 1e-6 * (1 + scale))
+        if cp == cn:
+            assert np.all(g == 0.0)
+
+
+# -------------------------------------------------------------------- LSE / ESS
+def test_lse_ess(spa):
+    rng = np.random.default_rng(3)
+    for N in [1, 5, 1024, 8192, 16384, 100000]:
+        lw = rng.normal(size=N) * 4 - 30
+        g = spa.lse_ess(lw)
+        o = oracle.lse_ess(lw)
+        assert abs(g[0] - o[0]) <= 1e-13 * abs(o[0])
+        assert abs(g[1] - o[1]) <= 1e-12 * o[1]
+    assert spa.lse_ess(np.full(4096, -3.0))[1] == pytest.approx(4096.0, rel=1e-14)
+
+
+# ----------------------------------------------------------------- resampling
+@pytest.mark.parametrize("N", [1, 2, 7, 255, 256, 257, 1000, 1024, 8192, 16384, 100003])
+def test_resampling_bit_exact(spa, N):
+    rng = np.random.default_rng(N)
+    for trial in range(3):
+        W = rng.gamma(0.2 + trial, size=N)
+        W /= W.sum()
+        u = float(rng.random())
+        assert np.array_equal(spa.resample_systematic(W, u), oracle.resample_systematic(W, u))
+
+
+def test_resampling_edge_cases(spa):
+    for N in [1, 64, 4096]:
+        W = np.full(N, 1.0 / N)
+        for u in [0.0, 1e-9, 0.5, 0.999999999]:
+            assert np.array_equal(spa.resample_systematic(W, u), oracle.resample_systematic(W, u))
+    W = np.zeros(1000)
+    W[999] = 1.0
+    assert np.all(spa.resample_systematic(W, 0.3) == 999)
+    W = np.zeros(1000)
+    W[0] = 1.0
+    assert np.all(spa.resample_systematic(W, 0.3) == 0)
+    # weights summing slightly below 1: the clamp to N - 1
+    W = np.full(100, 0.00999)
+    assert np.array_equal(spa.resample_systematic(W, 0.9), oracle.resample_systematic(W, 0.9))
+
+
+# ------------------------------------------------------------------ summaries
+@pytest.mark.parametrize("N,p", [(1, 1), (100, 3), (1000, 17), (8192, 40), (16384, 5), (20000, 3)])
+def test_summaries(spa, N, p):
+    rng = np.random.default_rng(N + p)
+    B = (rng.laplace(size=(N, p)) * 0.1).astype(np.float32)
+    B[rng.random((N, p)) < 0.3] = 0.0  # ties
+    B[:, 0] = np.round(B[:, 0], 2)
+    W = rng.gamma(0.5, size=N)
+    W /= W.sum()
+    qs, ds = (0.05, 0.5, 0.95), (0.05, 0.1)
+    mean, quant, conc = spa.summaries(B, W, qs, ds)
+    Bd = B.astype(np.float64)
+    assert np.allclose(mean, W @ Bd, rtol=1e-12, atol=1e-15)
+    for d_i, d in enumerate(ds):
+        assert np.allclose(conc[:, d_i], 1.0 - W @ (np.abs(Bd) < d), rtol=0, atol=1e-13)
+    for j in range(p):
+        ref = oracle.weighted_quantile(Bd[:, j], W, qs)
+        order = np.lexsort((np.arange(N), Bd[:, j]))
+        cum = np.cumsum(W[order])
+        for k, q in enumerate(qs):
+            if quant[j, k] != ref[k]:
+                # only a tie of the cumulative weight with q (within rounding) may differ
+                below = W[Bd[:, j] < quant[j, k]].sum()
+                upto = W[Bd[:, j] <= quant[j, k]].sum()
+                assert below <= q + 1e-12 and upto >= q - 1e-12, (j, k, quant[j, k], ref[k])
+
+
+def test_summaries_equal_weights_exact(spa):
+    rng = np.random.default_rng(9)
+    N, p = 8192, 4
+    B = rng.normal(size=(N, p)).astype(np.float32)
+    W = np.full(N, 1.0 / N)
+    _, quant, _ = spa.summaries(B, W)
+    for j in range(p):
+        assert quant[j].tolist() == oracle.weighted_quantile(B[:, j].astype(np.float64), W, (0.05, 0.5, 0.95)).tolist()
+
+
+# ------------------------------------------------------------------ likelihood
+SMALL_SHAPES = [(2, 1, 1), (7, 3, 5), (200, 10, 1024), (600, 130, 300), (513, 64, 129), (257, 255, 260),
+                (1000, 47, 777)]
+
+
+@pytest.mark.parametrize("n,p,N", SMALL_SHAPES)
+def test_loglik_split_bf16_bound(spa, n, p, N):
+    reg = synth.make_region(max(n, 2), p, 0.9, (0.5, -0.3), seed=n + p)
+    B = synth.random_particles(N, p, 0.3, seed=N)
+    with spa.Region(reg.G, reg.y, 1.0) as r:
+        g = r.loglik(B)
+    o = oracle.loglik(reg.G, reg.y, B.astype(np.float64))
+    bound = split_bound(reg.G, B, p)
+    err = np.abs(g - o)
+    assert np.all(err <= bound), (np.max(err / bound))
+    # and in practice far tighter than the worst case
+    assert np.median(err / bound) < 0.05
+
+
+@pytest.mark.parametrize("n,p,N", SMALL_SHAPES)
+def test_loglik_fp32_relative(spa, n, p, N):
+    reg = synth.make_region(max(n, 2), p, 0.9, (0.5, -0.3), seed=n + p)
+    B = synth.random_particles(N, p, 0.3, seed=N)
+    with spa.Region(reg.G, reg.y, 1.0, config=spa.make_config(precision="fp32")) as r:
+        g = r.loglik(B)
+    o = oracle.loglik(reg.G, reg.y, B.astype(np.float64))
+    assert np.all(np.abs(g - o) <= 1e-5 * np.abs(o))
+
+
+def test_loglik_special_values(spa):
+    reg = synth.make_region(500, 20, 0.9, (0.5,), seed=1)
+    with spa.Region(reg.G, reg.y, 1.0) as r:
+        z = r.loglik(np.zeros((130, 20), np.float32))
+        assert np.allclose(z, -500 * math.log(2), rtol=1e-7)
+        B = synth.random_particles(64, 20, 0.5, seed=2)
+        l1 = r.loglik(B)
+    with spa.Region(reg.G, (1 - reg.y).astype(np.uint8), 1.0) as r2:
+        l2 = r2.loglik(-B)
+    assert np.allclose(l1, l2, rtol=2e-5)
+
+
+@pytest.mark.parametrize("name", ["hit-region", "split-large"])
+def test_loglik_full_size_sampled(spa, name):
+    """The full-size workloads in the launch configuration of the sweep, checked on a
+    sample of particles the oracle evaluates one by one."""
+    w = synth.WORKLOADS[name]
+    reg = synth.workload_region(name)
+    B = synth.random_particles(w["N"], w["p"], 0.05, seed=11)
+    with spa.Region(reg.G, reg.y, w["nu"]) as r:
+        g = r.loglik(B)
+    idx = np.random.default_rng(1).choice(w["N"], size=96, replace=False)
+    idx = np.concatenate([idx, [0, w["N"] - 1]])
+    o = oracle.loglik(reg.G, reg.y, B[idx].astype(np.float64))
+    bound = split_bound(reg.G, B[idx], w["p"])
+    assert np.all(np.abs(g[idx] - o) <= bound)
+    assert np.all(np.isfinite(g))
+
+
+# ------------------------------------------------------------------ gradient
+def test_gradient_matches_oracle_and_differences(spa):
+    reg = synth.make_region(300, 37, 0.9, (0.5, -0.4), seed=3)
+    B = synth.random_particles(70, 37, 0.2, seed=4)
+    with spa.Region(reg.G, reg.y, 2.0) as r:
+        ll, g = r.grad(B, 0.0)
+        llc, gc = r.grad(B, 0.05)
+    o_ll, o_g = oracle.loglik_grad(reg.G, reg.y, B.astype(np.float64))
+    assert np.allclose(ll, o_ll, rtol=1e-5)
+    scale = np.abs((reg.G - reg.G.mean(0)) / reg.G.std(0)).sum(0)
+    assert np.all(np.abs(g - o_g) <= 1e-5 * scale[None, :])
+    # prior term of the posterior gradient at c = 0.05
+    a, c = 2.0, 0.05
+    prior = -(a + 1) * np.sign(B) / (a * c + np.abs(B))
+    assert np.all(np.abs((gc - g) - prior) <= 1e-5 * (1 + np.abs(prior)))
+    # central differences (h = 1e-4, FP64) of the oracle log-likelihood
+    h = 1e-4
+    for k in range(3):
+        for j in range(0, 37, 6):
+            Bp = B[k:k + 1].astype(np.float64).copy()
+            Bm = Bp.copy()
+            Bp[0, j] += h
+            Bm[0, j] -= h
+            fd = (oracle.loglik(reg.G, reg.y, Bp)[0] - oracle.loglik(reg.G, reg.y, Bm)[0]) / (2 * h)
+            assert abs(fd - g[k, j]) <= 1e-4 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------------ errors
+def test_invalid_inputs_rejected(spa):
+    reg = synth.make_region(50, 4, 0.9, (0.5,), seed=3)
+    G = reg.G.copy()
+    G[3, 2] = 3
+    with pytest.raises(spa.SpaError) as e:
+        spa.Region(G, reg.y, 1.0)
+    assert e.value.code == spa.SPA_EINVAL
+    y = reg.y.copy()
+    y[0] = 2
+    with pytest.raises(spa.SpaError):
+        spa.Region(reg.G, y, 1.0)
+    G = reg.G.copy()
+    G[:, 1] = 2
+    with pytest.raises(spa.SpaError):
+        spa.Region(G, reg.y, 1.0)
+    with pytest.raises(spa.SpaError):
+        spa.Region(reg.G, reg.y, 0.0)
+    with spa.Region(reg.G, reg.y, 1.0) as r:
+        with pytest.raises(spa.SpaError):
+            r.run([0.1, -1.0], N=16, moves_per_step=1, seed=1)
+        with pytest.raises(spa.SpaError):
+            r.run([0.1, float("nan")], N=16, moves_per_step=1, seed=1)
+        with pytest.raises(spa.SpaError):
+            r.run([0.1], N=0, moves_per_step=1, seed=1)
+        out = r.run([0.1, 0.2], N=16, moves_per_step=1, seed=1)  # still usable after errors
+        assert np.all(np.isfinite(out["mean"]))

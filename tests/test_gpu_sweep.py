@@ -1,0 +1,136 @@
+"""End-to-end parity of the GPU SPA sweep (spa_run) with the oracle and with quadrature.
+
+SMC is randomized, so the sweep is compared in distribution: posterior means,
+concentrations and log-evidence from R independent seeds on each side must agree within
+Monte Carlo standard errors, and for p <= 2 both must match grid quadrature of pi_t.
+With the same seed both sides draw the same random numbers, so their first step agrees
+closely as well.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1106_0322_gb300 import synth
+from tests.quadrature import Posterior
+from tests.test_oracle_smc import _check, _zscores
+
+pytestmark = pytest.mark.gpu
+
+R = 8
+
+
+@pytest.fixture(scope="module")
+def spa():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1106_0322_gb300 as mod
+
+    return mod
+
+
+def _two_sample_z(a, b, floor):
+    a, b = np.asarray(a), np.asarray(b)
+    se2 = a.var(axis=0, ddof=1) / a.shape[0] + b.var(axis=0, ddof=1) / b.shape[0]
+    return np.abs(a.mean(0) - b.mean(0)) / (np.sqrt(se2) + floor)
+
+
+def _gpu_runs(spa, reg, nu, sched, N, M, cfg, seeds):
+    with spa.Region(reg.G, reg.y, nu, config=cfg) as r:
+        return [r.run(sched, N, M, s) for s in seeds]
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "fp32"])
+def test_plain_small_workload_matches_oracle(spa, precision):
+    w = synth.WORKLOADS["plain-small"]
+    reg = synth.workload_region("plain-small")
+    sched = synth.geometric_schedule(w["T"])
+    seeds = list(range(1, R + 1))
+    g = _gpu_runs(spa, reg, w["nu"], sched, w["N"], w["M"], spa.make_config(precision=precision), seeds)
+    o = [oracle.run(reg.G, reg.y, w["nu"], sched, w["N"], w["M"], seed=100 + s) for s in seeds]
+    _check(_two_sample_z([r["mean"] for r in g], [r["mean"] for r in o], 2e-4), "mean")
+    _check(_two_sample_z([r["conc"] for r in g], [r["conc"] for r in o], 2e-3), "conc")
+    _check(_two_sample_z([np.cumsum(r["log_z_inc"]) for r in g], [np.cumsum(r["log_z_inc"]) for r in o], 2e-3),
+           "log Z")
+    _check(_two_sample_z([r["accept_rate"] for r in g], [r["accept_rate"] for r in o], 2e-3), "acceptance")
+    for r in g:
+        assert np.all(r["ess"] >= 1.0) and np.all(r["ess"] <= w["N"] * (1 + 1e-9))
+        qs = r["quantile"]
+        assert np.all(qs[:, :, 0] <= qs[:, :, 1]) and np.all(qs[:, :, 1] <= qs[:, :, 2])
+
+
+def test_same_seed_first_step_agrees(spa):
+    w = synth.WORKLOADS["plain-small"]
+    reg = synth.workload_region("plain-small")
+    sched = synth.geometric_schedule(w["T"])
+    with spa.Region(reg.G, reg.y, w["nu"]) as r:
+        g = r.run(sched, w["N"], w["M"], 5)
+    o = oracle.run(reg.G, reg.y, w["nu"], sched, w["N"], w["M"], seed=5)
+    # identical prior draws and weights at t = 0: the log-evidence estimate agrees closely
+    assert abs(g["log_z_inc"][0] - o["log_z_inc"][0]) < 1e-3
+    assert abs(g["ess"][0] - o["ess"][0]) < 1e-3 * o["ess"][0]
+    assert g["resampled"][0] == o["resampled"][0]
+    assert np.max(np.abs(g["mean"][0] - o["mean"][0])) < 5e-3
+
+
+@pytest.mark.parametrize("p,a,direction", [(1, 1.0, "s2d"), (2, 4.0, "d2s"), (1, math.inf, "d2s")])
+def test_sweep_matches_quadrature(spa, p, a, direction):
+    reg = synth.make_region(200, p, 0.9, (0.6,) * p, seed=2024 + p)
+    sched = synth.geometric_schedule(16, -6.0, 0.0, sparse_to_diffuse=(direction == "s2d"))
+    init = "prior_is" if direction == "s2d" else "resample_move"
+    cfg = spa.make_config(init=init, burn_in_steps=25)
+    runs = _gpu_runs(spa, reg, a, sched, 2048, 4, cfg, list(range(100, 100 + R)))
+    post = Posterior(reg.G, reg.y, a, sched)
+    truth_mean = np.array([post.mean(c) for c in sched])
+    truth_conc = np.array([[post.conc(c, d) for d in (0.05, 0.1)] for c in sched])
+    truth_logz = np.array([post.log_z(c) for c in sched])
+    _check(_zscores([r["mean"] for r in runs], truth_mean, 2e-4), "mean")
+    _check(_zscores(np.stack([r["conc"].transpose(0, 2, 1) for r in runs]), truth_conc, 2e-3), "conc")
+    _check(_zscores(np.stack([np.cumsum(r["log_z_inc"]) for r in runs]), truth_logz, 2e-3), "log Z")
+
+
+def test_sweep_is_deterministic_and_graph_reuse(spa):
+    reg = synth.make_region(300, 20, 0.9, (0.5,), seed=8)
+    sched = synth.geometric_schedule(8)
+    with spa.Region(reg.G, reg.y, 1.0) as r:
+        a = r.run(sched, 1000, 3, 42)
+        n1 = r.last_launch_count()
+        b = r.run(sched, 1000, 3, 42)
+        c = r.run(sched, 1000, 3, 43)
+        assert n1 > 8 * 3 * 3
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert not np.array_equal(a["mean"], c["mean"])
+
+
+@pytest.mark.parametrize("N,M,T,p", [(1, 2, 3, 4), (300, 1, 4, 1), (129, 0, 2, 7), (5000, 2, 1, 33)])
+def test_sweep_edge_shapes(spa, N, M, T, p):
+    reg = synth.make_region(150, p, 0.9, (0.5,), seed=N + p)
+    sched = synth.geometric_schedule(T, -3.0, 0.0)
+    with spa.Region(reg.G, reg.y, 2.0) as r:
+        out = r.run(sched, N, M, 7)
+    o = oracle.run(reg.G, reg.y, 2.0, sched, N, M, seed=7)
+    for k in ("mean", "quantile", "conc", "ess", "log_z_inc", "accept_rate"):
+        assert np.all(np.isfinite(out[k])), k
+    assert abs(out["log_z_inc"][0] - o["log_z_inc"][0]) < 1e-3 * max(1.0, abs(o["log_z_inc"][0]))
+    if M == 0:
+        assert np.all(out["accept_rate"] == 0.0)
+    if N == 1:
+        assert np.all(out["ess"] == 1.0) and not out["resampled"].any()
+
+
+def test_run_batch_matches_individual_runs(spa):
+    regs = [synth.make_region(200 + 50 * k, 5 + 3 * k, 0.9, (0.5,), seed=k) for k in range(3)]
+    sched = [synth.geometric_schedule(5 + k) for k in range(3)]
+    rs = [spa.Region(g.G, g.y, 1.0 + k) for k, g in enumerate(regs)]
+    try:
+        outs = spa.run_batch(rs, sched, [256, 300, 128], [2, 1, 3], [1, 2, 3])
+        for k in range(3):
+            ind = rs[k].run(sched[k], [256, 300, 128][k], [2, 1, 3][k], k + 1)
+            for key in ind:
+                assert np.array_equal(ind[key], outs[k][key]), (k, key)
+    finally:
+        for r in rs:
+            r.close()

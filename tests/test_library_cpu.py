@@ -1,0 +1,100 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds, loads and exports
+every entry point include/spa.h declares, and the ctypes structs match the header."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "spa.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(spa_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1106_0322_gb300 import _build
+
+    _build.build()
+    import paper_1106_0322_gb300 as spa
+
+    return spa.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("spa_create", "spa_set_config", "spa_run", "spa_run_batch", "spa_destroy", "spa_last_error",
+                     "spa_loglik", "spa_grad", "spa_resample_systematic", "spa_prior_logpdf"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    import paper_1106_0322_gb300 as spa
+
+    names = _declared()
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(spa.EXPORTED)
+    out = subprocess.run(["nm", "-D", "--defined-only", spa.library_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (spa_[a-z0-9_]+)$", out, flags=re.M))
+    assert set(names) <= exported
+
+
+def test_library_is_built_for_sm103a_only(lib):
+    import paper_1106_0322_gb300 as spa
+
+    out = subprocess.run(["cuobjdump", "--list-elf", spa.library_path()], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("cuobjdump unavailable")
+    assert "sm_103a" in out.stdout
+    assert "sm_90" not in out.stdout and "sm_100." not in out.stdout
+
+
+def test_struct_layouts_match_header():
+    import ctypes as C
+
+    import paper_1106_0322_gb300 as spa
+
+    # int32 x5, double[8], int32, double[8], 4 doubles, pointer (LP64, natural alignment)
+    assert C.sizeof(spa.Config) == 20 + 4 + 64 + 4 + 4 + 64 + 32 + 8
+    assert C.sizeof(spa.Result) == 7 * 8
+    assert C.sizeof(spa.BatchArgs) == 5 * 8
+
+
+def test_default_config(lib):
+    import paper_1106_0322_gb300 as spa
+
+    cfg = spa.default_config()
+    assert cfg.move_kind == spa.MOVE_RW and cfg.precision == spa.PREC_SPLIT_BF16
+    assert cfg.n_quantiles == 3 and list(cfg.quantiles[:3]) == [0.05, 0.5, 0.95]
+    assert cfg.n_deltas == 2 and list(cfg.deltas[:2]) == [0.05, 0.1]
+    assert cfg.ess_frac == 0.75 and cfg.rw_scale == 2.38 and cfg.mala_h == 1.65
+
+
+def test_null_arguments_are_rejected_without_a_gpu(lib):
+    import ctypes as C
+
+    import paper_1106_0322_gb300 as spa
+
+    h = C.c_void_p()
+    assert lib.spa_create(None, None, 10, 2, 1.0, C.byref(h)) == spa.SPA_EINVAL
+    assert b"NULL" in lib.spa_last_error(None)
+    assert lib.spa_run(None, None, 1, 1, 1, 0, None) == spa.SPA_EINVAL
+    assert lib.spa_last_launch_count(None) == 0
+    lib.spa_destroy(None)
+
+
+def test_product_path_has_no_oracle_dependency():
+    # the CUDA library and its binding never import or load the oracle
+    pkg = os.path.join(ROOT, "paper_1106_0322_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text and "spa_oracle" not in text, f
