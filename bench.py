@@ -241,7 +241,11 @@ def main():
     region = synth.workload_region(args.workload)
     sched_h = synth.geometric_schedule(w["T"])
     sched_d = torch.tensor(sched_h, dtype=torch.float64, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # A dedicated stream: the library runs on it and the events are recorded on it (the
+    # legacy default stream has handle 0, which the library reads as "its own stream").
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    assert stream.cuda_stream != 0
     cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream)
     reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
     T, p = w["T"], w["p"]

@@ -31,6 +31,7 @@ constexpr int BM = 128;
 constexpr int BK = 64;  // BF16 per 128-byte swizzle row
 constexpr int EPI_WARPS = 8;
 constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int ADJ_BN_SMALL = 208;  // p + padding <= 208 covers the p = 200 workloads in one N tile
 
 template <int BN, int STAGES>
 struct TcCfg {
@@ -65,11 +66,64 @@ __device__ __forceinline__ float sum_softplus2_32(const float (&v)[32], int vali
     return t[0];
 }
 
-template <int BN, int STAGES>
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Residual mode: besides the softplus sum, r = y - logit^{-1}(eta) for the 32 columns of
+// this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into *rsum.
+// eta2 = eta log2(e): with e = 2^-|eta2|, softplus2 = max(eta2, 0) + log2(1 + e) and
+// logit^{-1}(eta) = 1/(1 + e) for eta >= 0, e/(1 + e) otherwise (one ex2 shared).
+__device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, const float* __restrict__ yv,
+                                             __nv_bfloat16* __restrict__ rrow, int64_t n_r, float& rsum)
+{
+    float sp[32];
+    __align__(16) __nv_bfloat16 hi[32];
+    __align__(16) __nv_bfloat16 lo[32];
+    float rs[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float x = v[k];
+        const float e = ex2_approx(-fabsf(x));
+        const float onepe = 1.0f + e;
+        const float inv = rcp_approx(onepe);
+        const float sig = (x >= 0.0f) ? inv : e * inv;
+        const bool ok = k < valid;
+        sp[k] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
+        const float r = ok ? __ldg(yv + k) - sig : 0.0f;
+        rs[k] = r;
+        split_bf16(r, hi[k], lo[k]);
+    }
+    // 16-byte stores of the 32 hi and 32 lo values (rrow is 64-byte aligned)
+    uint4* dh = reinterpret_cast<uint4*>(rrow);
+    uint4* dl = reinterpret_cast<uint4*>(rrow + n_r);
+    const uint4* sh = reinterpret_cast<const uint4*>(hi);
+    const uint4* sl = reinterpret_cast<const uint4*>(lo);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        dh[q] = sh[q];
+        dl[q] = sl[q];
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            sp[k] += sp[k + w];
+            rs[k] += rs[k + w];
+        }
+    rsum += rs[0];
+    return sp[0];
+}
+
+template <int BN, int STAGES, bool RESID>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n_tiles,
                 int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial, int64_t N_pad,
-                uint32_t* __restrict__ err)
+                uint32_t* __restrict__ err, const float* __restrict__ yv, __nv_bfloat16* __restrict__ R, int64_t n_r,
+                float* __restrict__ rsum_part)
 {
     using C = TcCfg<BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
@@ -195,18 +249,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const int col0 = half * (BN / 2);
             const int valid = n - nt * BN - col0;
-            float acc = 0.0f;
+            float acc = 0.0f, rsum = 0.0f;
 #pragma unroll 1
             for (int c = 0; c < BN / 2; c += 32) {
                 if (valid - c <= 0) break;
                 float v[32];
                 tmem_ld32(tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)(col0 + c), v);
-                acc += sum_softplus2_32(v, valid - c);
+                if (RESID) {
+                    const int64_t i0 = (int64_t)nt * BN + col0 + c;
+                    acc += resid_chunk(v, valid - c, yv + i0, R + ((int64_t)mt * BM + row) * 2 * n_r + i0, n_r, rsum);
+                } else {
+                    acc += sum_softplus2_32(v, valid - c);
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(ACCE_BAR(b));
             partial[((int64_t)nt * 2 + half) * N_pad + (int64_t)mt * BM + row] = acc;
+            if (RESID) rsum_part[((int64_t)nt * 2 + half) * N_pad + (int64_t)mt * BM + row] = rsum;
         }
     }
 #undef FULL_BAR
@@ -219,6 +279,176 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+// ----------------------------------------------------------------------- adjoint
+// C[k, j] = sum_i r_ki g_ij for 128 particles x BN2 markers, contracting over the
+// individuals of this CTA's k-range: A = [R_hi | R_lo] (N_pad x 2 n_r), B = G^T
+// (markers x n_r, exact BF16), both K-major with the 128-byte swizzle. One output tile per
+// CTA; warps 2..5 copy the FP32 accumulator to gpart[ks][particle][marker]. The final
+// gradient (C - m_j sum_i r_ki) / s_j is formed by k_grad_finish.
+constexpr int ADJ_THREADS = 64 + 32 * 4;
+
+template <int BN2, int STAGES>
+struct AdjCfg {
+    static constexpr int A_TILE = BM * BK * 2;
+    static constexpr int B_TILE = BN2 * BK * 2;
+    static constexpr int STAGE = 2 * A_TILE + B_TILE;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int NBARS = 2 * STAGES + 2;  // full, empty, acc_full, drain
+    static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
+    static constexpr int SMEM = SLOT_OFF + 16 + 1024;
+    static constexpr uint32_t TMEM_COLS = 256;
+    static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
+    static_assert(SMEM <= 232448, "shared memory budget");
+    static_assert(BN2 % 16 == 0 && BN2 <= 256, "MMA N");
+};
+
+template <int BN2, int STAGES>
+__global__ void __launch_bounds__(ADJ_THREADS, 1)
+    k_adjoint_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapGT, int m_tiles,
+                 int p_tiles, int kblocks, int ksplit, int n_r, int p, float* __restrict__ gpart, int64_t N_pad,
+                 uint32_t* __restrict__ err)
+{
+    using C = AdjCfg<BN2, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = sbase + C::BAR_OFF;
+    const uint32_t accf_bar = bar0 + 8u * (uint32_t)(2 * STAGES);
+    const uint32_t drain_bar = accf_bar + 8u;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
+#define FULL_BAR(s) (bar0 + 8u * (uint32_t)(s))
+#define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
+    // unit = (mt, pt, ks)
+    const int u = blockIdx.x;
+    const int ks = u % ksplit;
+    const int pt = (u / ksplit) % p_tiles;
+    const int mt = u / (ksplit * p_tiles);
+    const int kb0 = (int)((int64_t)kblocks * ks / ksplit), kb1 = (int)((int64_t)kblocks * (ks + 1) / ksplit);
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < STAGES; ++q) {
+            mbar_init(FULL_BAR(q), 1);
+            mbar_init(EMPTY_BAR(q), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(drain_bar, 1);
+        mbar_fence_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&mapR);
+        tma_prefetch_desc(&mapGT);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int kb = kb0; kb < kb1; ++kb) {
+                const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
+                if (!mbar_wait_bounded(EMPTY_BAR(q), ph ^ 1u, err)) break;
+                const uint32_t st = sbase + q * C::STAGE;
+                mbar_arrive_expect_tx(FULL_BAR(q), (uint32_t)C::STAGE);
+                tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
+                tma_load_2d(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM);
+                tma_load_2d(st + 2 * C::A_TILE, &mapGT, FULL_BAR(q), kb * BK, pt * BN2);
+                ++it;
+            }
+            const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
+            for (uint32_t k = 1; k <= last; ++k) {
+                const uint32_t i2 = it - k;
+                mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN2);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int kb = kb0; kb < kb1; ++kb) {
+                const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
+                if (!mbar_wait_bounded(FULL_BAR(q), ph, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + q * C::STAGE;
+                const uint64_t ahi = sdesc_sw128(st), alo = sdesc_sw128(st + C::A_TILE);
+                const uint64_t bg = sdesc_sw128(st + 2 * C::A_TILE);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) umma_bf16(tmem_base, ahi + 2u * k, bg + 2u * k, IDESC, (kb > kb0 || k) ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) umma_bf16(tmem_base, alo + 2u * k, bg + 2u * k, IDESC, 1u);
+                umma_commit(EMPTY_BAR(q));
+                ++it;
+            }
+            if (ok) umma_commit(accf_bar);
+            umma_commit(drain_bar);
+            mbar_wait_bounded(drain_bar, 0u, err, 100000000ull);
+        }
+    } else {
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const int cols = (p - pt * BN2) < BN2 ? (p - pt * BN2) : BN2;
+        if (kb1 > kb0 && mbar_wait_bounded(accf_bar, 0u, err)) {
+            tc_fence_after();
+            float* out = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + row) * p + (int64_t)pt * BN2;
+#pragma unroll 1
+            for (int c = 0; c < cols; c += 32) {
+                float v[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (c + k < cols) out[c + k] = v[k];
+            }
+        } else if (kb1 <= kb0) {
+            float* out = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + row) * p + (int64_t)pt * BN2;
+            for (int c = 0; c < cols; ++c) out[c] = 0.0f;
+        }
+    }
+#undef FULL_BAR
+#undef EMPTY_BAR
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+// grad l_kj = (sum_s C_s[k, j] - m_j sum_i r_ki) / s_j (+ the prior gradient at scale c > 0).
+__global__ void k_grad_finish(const float* __restrict__ gpart, int ksplit, const float* __restrict__ rsum_part,
+                              int n_parts, int64_t N_pad, int64_t N, int p, const double* __restrict__ mean,
+                              const double* __restrict__ sd, const float* __restrict__ B, PriorArgs pr, double c,
+                              float* __restrict__ grad)
+{
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
+    double rs = 0.0;
+    for (int q = lane; q < n_parts; q += 32) rs += (double)rsum_part[(int64_t)q * N_pad + k];
+    rs = warp_sum(rs);
+    for (int j = lane; j < p; j += 32) {
+        double g = 0.0;
+        for (int q = 0; q < ksplit; ++q) g += (double)gpart[((int64_t)q * N_pad + k) * p + j];
+        g = (g - mean[j] * rs) / sd[j];
+        if (c > 0.0) {
+            const float b = B[k * p + j];
+            const double sg = (b > 0.0f) ? 1.0 : ((b < 0.0f) ? -1.0 : 0.0);
+            g += pr.de ? -sg / c : -((double)pr.a + 1.0) * sg / ((double)pr.a * c + fabs((double)b));
+        }
+        grad[k * p + j] = (float)g;
     }
 }
 
@@ -255,13 +485,14 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, bool RESID>
 cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
-                      float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st)
+                      float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra, cudaStream_t st)
 {
     using C = TcCfg<BN, STAGES>;
-    k_loglik_tc<BN, STAGES><<<plan.grid, TC_THREADS, C::SMEM, st>>>(mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks,
-                                                                     plan.ksteps, Kp, (int)n, partial, N_pad, err);
+    k_loglik_tc<BN, STAGES, RESID><<<plan.grid, TC_THREADS, C::SMEM, st>>>(
+        mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err,
+        ra ? ra->yv : nullptr, ra ? ra->R : nullptr, ra ? ra->n_r : 0, ra ? ra->rsum_part : nullptr);
     return cudaGetLastError();
 }
 
@@ -269,10 +500,16 @@ cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const Tc
 
 cudaError_t tc_init_attributes()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_loglik_tc<256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcCfg<256, 3>::SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_loglik_tc<128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<128, 4>::SMEM);
+    cudaError_t e = cudaSuccess;
+#define SET_SMEM(kern, bytes) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+    SET_SMEM((k_loglik_tc<256, 3, false>), (TcCfg<256, 3>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, false>), (TcCfg<128, 4>::SMEM));
+    SET_SMEM((k_loglik_tc<256, 3, true>), (TcCfg<256, 3>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, true>), (TcCfg<128, 4>::SMEM));
+    SET_SMEM((k_adjoint_tc<ADJ_BN_SMALL, 3>), (AdjCfg<ADJ_BN_SMALL, 3>::SMEM));
+    SET_SMEM((k_adjoint_tc<256, 3>), (AdjCfg<256, 3>::SMEM));
+#undef SET_SMEM
     return e;
 }
 
@@ -301,10 +538,65 @@ bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp
 }
 
 cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
-                             float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st)
+                             float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st, const ResidArgs* ra)
 {
-    if (plan.BN == 256) return launch_tc<256, 3>(mapA, mapB, plan, n, Kp, partial, N_pad, err, st);
-    return launch_tc<128, 4>(mapA, mapB, plan, n, Kp, partial, N_pad, err, st);
+    if (ra) {
+        if (plan.BN == 256) return launch_tc<256, 3, true>(mapA, mapB, plan, n, Kp, partial, N_pad, err, ra, st);
+        return launch_tc<128, 4, true>(mapA, mapB, plan, n, Kp, partial, N_pad, err, ra, st);
+    }
+    if (plan.BN == 256) return launch_tc<256, 3, false>(mapA, mapB, plan, n, Kp, partial, N_pad, err, nullptr, st);
+    return launch_tc<128, 4, false>(mapA, mapB, plan, n, Kp, partial, N_pad, err, nullptr, st);
+}
+
+AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms)
+{
+    AdjPlan a;
+    a.n_r = (n + 63) / 64 * 64;
+    a.kblocks = (int)(a.n_r / 64);
+    a.BN2 = (p <= ADJ_BN_SMALL) ? ADJ_BN_SMALL : 256;
+    a.p_tiles = (p + a.BN2 - 1) / a.BN2;
+    a.m_tiles = (int)(N_pad / BM);
+    const int base = a.m_tiles * a.p_tiles;
+    int ks = num_sms / (base > 0 ? base : 1);
+    if (ks < 1) ks = 1;
+    if (ks > a.kblocks) ks = a.kblocks;
+    if (ks > 8) ks = 8;
+    a.ksplit = ks;
+    a.grid = base * ks;
+    return a;
+}
+
+bool adj_make_map_R(CUtensorMap* map, const __nv_bfloat16* R, int64_t N_pad, int64_t n_r)
+{
+    return make_map_2d(map, R, (uint64_t)(2 * n_r), (uint64_t)N_pad, BK, BM);
+}
+
+bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n_r, int BN2)
+{
+    return make_map_2d(map, GT, (uint64_t)n_r, (uint64_t)p, BK, (uint32_t)BN2);
+}
+
+cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p,
+                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st)
+{
+    if (a.BN2 == ADJ_BN_SMALL) {
+        k_adjoint_tc<ADJ_BN_SMALL, 3><<<a.grid, ADJ_THREADS, AdjCfg<ADJ_BN_SMALL, 3>::SMEM, st>>>(
+            mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit, (int)a.n_r, p, gpart, N_pad, err);
+    } else {
+        k_adjoint_tc<256, 3><<<a.grid, ADJ_THREADS, AdjCfg<256, 3>::SMEM, st>>>(mapR, mapGT, a.m_tiles, a.p_tiles,
+                                                                               a.kblocks, a.ksplit, (int)a.n_r, p, gpart,
+                                                                               N_pad, err);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
+                               int64_t N, int p, const double* mean, const double* sd, const float* B, PriorArgs pr,
+                               double c, float* grad, cudaStream_t st)
+{
+    k_grad_finish<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean, sd, B,
+                                                           pr, c, grad);
+    return cudaGetLastError();
 }
 
 }  // namespace spa

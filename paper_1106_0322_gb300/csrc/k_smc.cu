@@ -107,6 +107,142 @@ __global__ void __launch_bounds__(256) k_propose_rw(const float* __restrict__ be
     }
 }
 
+// ----------------------------------------------------------------- MALA proposal
+// beta' = beta + (h^2/2) D grad log pi_t(beta) + h D^{1/2} xi with D = diag(D_j) and
+// h = lambda p^{-1/6}; grad log pi_t = grad l (stored per particle) + the prior gradient
+// -(a+1) sgn(beta)/(a c + |beta|) (double exponential: -sgn(beta)/c). Also stores
+// sum_j xi_j^2, since log q(beta'|beta) = -sum_j xi_j^2 / 2 + const.
+__device__ __forceinline__ float dlogprior(float b, float a1, float ac, float inv_c, int de)
+{
+    const float sg = (b > 0.0f) ? 1.0f : ((b < 0.0f) ? -1.0f : 0.0f);
+    return de ? -sg * inv_c : -a1 * sg / (ac + fabsf(b));
+}
+
+__global__ void __launch_bounds__(256) k_propose_mala(const float* __restrict__ beta, const float* __restrict__ gl,
+                                                     float* __restrict__ beta_p, __nv_bfloat16* __restrict__ A, int ldA,
+                                                     int Kp, double* __restrict__ lin_p, double* __restrict__ lp_p,
+                                                     double* __restrict__ xi2, const float* __restrict__ D,
+                                                     const double* __restrict__ lam, const float* __restrict__ l2e_over_s,
+                                                     const float* __restrict__ mean_f, const double* __restrict__ v,
+                                                     int64_t N, int p, PriorArgs pr, const double* __restrict__ sched,
+                                                     int t, uint32_t m, const uint64_t* __restrict__ seedp)
+{
+    const int64_t i = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const uint64_t seed = *seedp;
+    const double c = sched[t];
+    const float ac = (float)((double)pr.a * c), a1 = pr.a + 1.0f, inv_c = (float)(1.0 / c);
+    const double hd = *lam * pow((double)p, -1.0 / 6.0);
+    const float h = (float)hd, h2 = (float)(0.5 * hd * hd);
+    const float* row = beta + i * p;
+    const float* grow = gl + i * p;
+    float* rowp = beta_p + i * p;
+    double lin = 0.0, lterm = 0.0, off = 0.0, zz = 0.0;
+    const int groups = (p + 3) >> 2;
+    for (int g = lane; g < groups; g += 32) {
+        const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
+        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = 4 * g + k;
+            if (j < p) {
+                const float b0 = row[j];
+                const float grad = grow[j] + dlogprior(b0, a1, ac, inv_c, pr.de);
+                const float Dj = D[j];
+                const float b = b0 + h2 * Dj * grad + h * sqrtf(Dj) * z[k];
+                rowp[j] = b;
+                zz += (double)z[k] * (double)z[k];
+                lin += (double)b * v[j];
+                lterm += (double)prior_term(b, ac, pr.de);
+                if (A) {
+                    const float bt = b * l2e_over_s[j];
+                    __nv_bfloat16 hi, lo;
+                    split_bf16(bt, hi, lo);
+                    A[i * ldA + j] = hi;
+                    A[i * ldA + Kp + j] = lo;
+                    off += (double)mean_f[j] * (double)bt;
+                }
+            }
+        }
+    }
+    lin = warp_sum(lin);
+    lterm = warp_sum(lterm);
+    off = warp_sum(off);
+    zz = warp_sum(zz);
+    if (lane == 0) {
+        lin_p[i] = lin;
+        lp_p[i] = prior_from_terms(lterm, p, (double)pr.a, c, pr.de);
+        xi2[i] = zz;
+        if (A) {
+            __nv_bfloat16 hi, lo;
+            split_bf16((float)(-off), hi, lo);
+            A[i * ldA + p] = hi;
+            A[i * ldA + Kp + p] = lo;
+        }
+    }
+}
+
+// MH test of a MALA proposal: log alpha = l' + lp' - l - lp + log q(beta|beta') - log q(beta'|beta),
+// log q(beta|beta') = -sum_j (beta_j - beta'_j - (h^2/2) D_j g'_j)^2 / (2 h^2 D_j),
+// log q(beta'|beta) = -sum_j xi_j^2 / 2. On acceptance the state and its gradient move.
+__global__ void __launch_bounds__(256) k_accept_mala(AcceptArgs a, float* __restrict__ gl, const float* __restrict__ gl_p,
+                                                    const double* __restrict__ xi2, const float* __restrict__ D,
+                                                    const double* __restrict__ lam, int64_t N, int p, PriorArgs pr,
+                                                    const double* __restrict__ sched, int t, uint32_t m,
+                                                    const uint64_t* __restrict__ seedp, uint32_t* __restrict__ err)
+{
+    __shared__ unsigned int block_acc;
+    if (threadIdx.x == 0) block_acc = 0;
+    __syncthreads();
+    const int64_t i = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (i < N) {
+        const double c = sched[t];
+        const float ac = (float)((double)pr.a * c), a1 = pr.a + 1.0f, inv_c = (float)(1.0 / c);
+        const double hd = *lam * pow((double)p, -1.0 / 6.0);
+        const float h2 = (float)(0.5 * hd * hd);
+        const float* b0 = a.beta + i * p;
+        const float* b1 = a.beta_p + i * p;
+        const float* g1 = gl_p + i * p;
+        double bwd = 0.0;
+        for (int j = lane; j < p; j += 32) {
+            const float gp = g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de);
+            const float d = b0[j] - b1[j] - h2 * D[j] * gp;
+            bwd += (double)d * (double)d / (double)D[j];
+        }
+        bwd = warp_sum(bwd);
+        int accept = 0;
+        if (lane == 0) {
+            double sp = 0.0;
+            for (int s = 0; s < a.n_parts; ++s) sp += (double)a.partial[(int64_t)s * a.ld_part + i];
+            const double llp = a.lin_p[i] - a.sp_scale * sp;
+            if (!isfinite(llp)) atomicOr(err, DERR_NONFINITE);
+            const double log_alpha =
+                (llp + a.lp_p[i]) - (a.ll[i] + a.lp[i]) - bwd / (2.0 * hd * hd) + 0.5 * xi2[i];
+            const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m),
+                                          seed_key(*seedp));
+            accept = log(u01_open_d(u.x)) < log_alpha;
+            if (accept) {
+                a.ll[i] = llp;
+                a.lp[i] = a.lp_p[i];
+            }
+        }
+        accept = __shfl_sync(0xffffffffu, accept, 0);
+        if (accept) {
+            float* dst = a.beta + i * p;
+            float* gdst = gl + i * p;
+            for (int j = lane; j < p; j += 32) {
+                dst[j] = b1[j];
+                gdst[j] = g1[j];
+            }
+            if (lane == 0) atomicAdd(&block_acc, 1u);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && block_acc && a.acc_count) atomicAdd(a.acc_count, (unsigned long long)block_acc);
+}
+
 // --------------------------------------------------------------- finish / MH test
 __global__ void __launch_bounds__(256) k_accept(AcceptArgs a, int64_t N, int p, int mode, int t, uint32_t m,
                                                 const uint64_t* __restrict__ seedp, uint32_t* __restrict__ err)
@@ -633,6 +769,25 @@ cudaError_t launch_propose_rw(const float* beta, float* beta_p, __nv_bfloat16* A
 {
     k_propose_rw<<<warps_grid(N), 32 * WARPS_PER_BLOCK, 0, st>>>(beta, beta_p, A, ldA, Kp, lin_p, lp_p, sigma, l2e_over_s,
                                                                   mean_f, v, N, p, pr, sched, t, m, seed, noise);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propose_mala(const float* beta, const float* gl, float* beta_p, __nv_bfloat16* A, int ldA, int Kp,
+                                double* lin_p, double* lp_p, double* xi2, const float* D, const double* lam,
+                                const float* l2e_over_s, const float* mean_f, const double* v, int64_t N, int p,
+                                PriorArgs pr, const double* sched, int t, uint32_t m, const uint64_t* seed, cudaStream_t st)
+{
+    k_propose_mala<<<warps_grid(N), 32 * WARPS_PER_BLOCK, 0, st>>>(beta, gl, beta_p, A, ldA, Kp, lin_p, lp_p, xi2, D, lam,
+                                                                    l2e_over_s, mean_f, v, N, p, pr, sched, t, m, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accept_mala(const AcceptArgs& a, float* gl, const float* gl_p, const double* xi2, const float* D,
+                               const double* lam, int64_t N, int p, PriorArgs pr, const double* sched, int t, uint32_t m,
+                               const uint64_t* seed, uint32_t* err, cudaStream_t st)
+{
+    k_accept_mala<<<warps_grid(N), 32 * WARPS_PER_BLOCK, 0, st>>>(a, gl, gl_p, xi2, D, lam, N, p, pr, sched, t, m, seed,
+                                                                   err);
     return cudaGetLastError();
 }
 

@@ -103,7 +103,29 @@ __global__ void k_store_pack(const int8_t* __restrict__ G, int64_t n, int64_t p,
     }
 }
 
+// G^T as BF16 [p][n_r] (zero beyond n) for the adjoint, and y as floats.
+__global__ void k_store_pack_t(const int8_t* __restrict__ G, const uint8_t* __restrict__ y, int64_t n, int64_t p,
+                               int64_t n_r, __nv_bfloat16* __restrict__ GT, float* __restrict__ yv)
+{
+    const int64_t total = p * n_r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / n_r;
+        const int64_t i = e - j * n_r;
+        GT[e] = __float2bfloat16_rn(i < n ? (float)G[i * p + j] : 0.0f);
+        if (j == 0 && i < n) yv[i] = (float)y[i];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_store_pack_t(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, int64_t n_r,
+                                __nv_bfloat16* GT, float* yv, cudaStream_t st)
+{
+    const int64_t total = p * n_r;
+    const unsigned blocks = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+    k_store_pack_t<<<blocks, 256, 0, st>>>(G, y, n, p, n_r, GT, yv);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_store_sums(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, unsigned long long* sums,
                               uint32_t* err, cudaStream_t st)

@@ -55,6 +55,15 @@ struct Workspace {
     int* flag = nullptr;
     float* eta = nullptr;  // gradient path scratch, allocated on first use
     float* grad = nullptr;
+    // MALA: log-likelihood gradient of the current and the proposed particles, sum xi^2
+    float* gl = nullptr;
+    float* gl_p = nullptr;
+    double* xi2 = nullptr;
+    // tensor-core adjoint: residuals r (BF16 hi | lo), their row sums, C = R G partials
+    __nv_bfloat16* R = nullptr;
+    float* rsum = nullptr;
+    float* gpart = nullptr;
+    CUtensorMap mapR;
 };
 
 struct RunBufs {
@@ -97,6 +106,11 @@ struct spa_ctx {
     __nv_bfloat16* Gbf = nullptr;
     CUtensorMap mapB;
     int mapB_BN = 0;
+    __nv_bfloat16* GT = nullptr;  // [p][n_r] for the adjoint
+    float* yv = nullptr;
+    int64_t n_r = 0;
+    CUtensorMap mapGT;
+    int mapGT_BN = 0;
     uint32_t* d_err = nullptr;
     Workspace ws;
     RunBufs rb;
@@ -172,6 +186,7 @@ void free_workspace(Workspace& w)
     dfree(w.lin_p); dfree(w.lp_p); dfree(w.ll); dfree(w.lp); dfree(w.logw); dfree(w.W);
     dfree(w.ll_tmp); dfree(w.lp_tmp); dfree(w.cum); dfree(w.colpart); dfree(w.lambda);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
+    dfree(w.gl); dfree(w.gl_p); dfree(w.xi2); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
     w.N = w.N_pad = 0;
 }
 
@@ -245,6 +260,49 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     return SPA_OK;
 }
 
+int ensure_adjoint_buffers(spa_ctx* c)
+{
+    Workspace& w = c->ws;
+    if (w.R) return SPA_OK;
+    const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
+    const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
+    cudaError_t e = dalloc(&w.R, (size_t)(w.N_pad * 2 * a.n_r));
+    if (e == cudaSuccess) e = dalloc(&w.rsum, (size_t)(plan.n_parts * w.N_pad));
+    if (e == cudaSuccess) e = dalloc(&w.gpart, (size_t)(a.ksplit * w.N_pad * c->p));
+    if (e == cudaSuccess && !w.gl_p) e = dalloc(&w.gl_p, (size_t)(w.N * c->p));
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint buffers");
+    // residual columns n..n_r-1 and rows N..N_pad-1 stay zero
+    CK(cudaMemsetAsync(w.R, 0, sizeof(__nv_bfloat16) * (size_t)(w.N_pad * 2 * a.n_r), c->stream()), "memset R");
+    if (!adj_make_map_R(&w.mapR, w.R, w.N_pad, a.n_r)) return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for R");
+    if (c->mapGT_BN != a.BN2) {
+        if (!adj_make_map_GT(&c->mapGT, c->GT, (int)c->p, a.n_r, a.BN2))
+            return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for G^T");
+        c->mapGT_BN = a.BN2;
+    }
+    return SPA_OK;
+}
+
+int ensure_mala_buffers(spa_ctx* c)
+{
+    Workspace& w = c->ws;
+    if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        int rc = ensure_adjoint_buffers(c);
+        if (rc != SPA_OK) return rc;
+    }
+    const bool plain = c->cfg.precision != SPA_PREC_SPLIT_BF16;
+    if (w.gl && (w.eta || !plain)) return SPA_OK;
+    const int64_t N = w.N, p = c->p, n = c->n;
+    const int64_t tiles = (n + SIMT_TILE_N - 1) / SIMT_TILE_N;
+    cudaError_t e = cudaSuccess;
+    if (!w.gl) e = dalloc(&w.gl, (size_t)(N * p));
+    if (e == cudaSuccess && !w.gl_p) e = dalloc(&w.gl_p, (size_t)(N * p));
+    if (e == cudaSuccess && !w.xi2) e = dalloc(&w.xi2, (size_t)N);
+    if (e == cudaSuccess && plain && !w.eta) e = dalloc(&w.eta, (size_t)(N * n + tiles * N));
+    if (e == cudaSuccess && plain && !w.grad) e = dalloc(&w.grad, (size_t)(N * p));
+    if (e != cudaSuccess) return cuda_fail(c, e, "MALA buffers");
+    return SPA_OK;
+}
+
 int ensure_runbufs(spa_ctx* c, int64_t T)
 {
     RunBufs& r = c->rb;
@@ -287,6 +345,22 @@ struct Enq {
         ++launches;
     }
 };
+
+// gradient of the log-likelihood at the packed particles (beta_p / A) into out, on the
+// tensor cores: residual likelihood pass, C = R G, finish. Also leaves the softplus
+// partials of those particles in w.partial.
+void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
+    const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
+    ResidArgs ra{c->yv, w.R, a.n_r, w.rsum};
+    q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, q.st, &ra));
+    q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st));
+    q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean, c->sd, Bsrc, c->pr,
+                            cs, out, q.st));
+}
 
 __global__ void k_set_f64(double* p, double v)
 {
@@ -340,6 +414,25 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     Workspace& w = c->ws;
     const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
     const AcceptArgs a = accept_args(c, acc);
+    if (c->cfg.move_kind == SPA_MOVE_MALA) {
+        for (int mm = 0; mm < M; ++mm) {
+            const uint32_t m = m0 + (uint32_t)mm;
+            q.ck(launch_propose_mala(w.beta, w.gl, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.xi2,
+                                     w.scale, w.lambda, c->l2e_s, c->mean_f, c->v, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
+                                     c->rb.seed, q.st));
+            if (tc) {
+                enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
+            } else {
+                enq_loglik(q);
+                q.ck(launch_grad_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.eta, w.gl_p, nullptr, c->pr, 0.0,
+                                      q.st));
+                ++q.launches;  // the plain adjoint is two kernels
+            }
+            q.ck(launch_accept_mala(a, w.gl, w.gl_p, w.xi2, w.scale, w.lambda, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
+                                    c->rb.seed, c->d_err, q.st));
+        }
+        return;
+    }
     for (int mm = 0; mm < M; ++mm) {
         const uint32_t m = m0 + (uint32_t)mm;
         q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
@@ -354,10 +447,11 @@ void enq_resample(Enq& q, int t)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     q.ck(launch_resample_index(w.W, w.N, w.cum, w.idx, w.flag, t, c->rb.seed, 0.0, q.st));
-    q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, nullptr, nullptr, w.N, (int)c->p, w.flag,
-                       q.st));
-    q.ck(launch_copyback(w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, nullptr, nullptr, w.logw, w.W, w.N, (int)c->p,
-                         w.flag, q.st));
+    const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
+    q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr,
+                       mala ? w.gl_p : nullptr, w.N, (int)c->p, w.flag, q.st));
+    q.ck(launch_copyback(w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr, mala ? w.gl_p : nullptr,
+                         w.logw, w.W, w.N, (int)c->p, w.flag, q.st));
 }
 
 void enq_colstats(Enq& q, int t)
@@ -399,7 +493,15 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
     q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
                            c->mean_f, c->v, w.N, p, c->pr, r.sched, 0, 0u, r.seed, 0, q.st));
-    enq_loglik(q);
+    if (mala && tc) {
+        enq_grad_tc(q, w.gl, w.beta, 0.0, w.N);  // also leaves the softplus partials of the draws
+    } else {
+        enq_loglik(q);
+        if (mala) {
+            q.ck(launch_grad_simt(w.beta, c->Xf, c->y, w.N, c->n, p, w.eta, w.gl, nullptr, c->pr, 0.0, q.st));
+            ++q.launches;
+        }
+    }
     AcceptArgs a0 = accept_args(c, nullptr);
     a0.logw = w.logw;
     q.ck(launch_accept(a0, w.N, p, 0, 0, 0u, r.seed, c->d_err, q.st));
@@ -443,7 +545,6 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
 int validate_config(spa_ctx* c, const spa_config& k)
 {
     if (k.move_kind != SPA_MOVE_RW && k.move_kind != SPA_MOVE_MALA) return fail(c, SPA_EINVAL, "move_kind");
-    if (k.move_kind == SPA_MOVE_MALA) return fail(c, SPA_EUNSUPPORTED, "MALA moves are not available in this build");
     if (k.precision != SPA_PREC_SPLIT_BF16 && k.precision != SPA_PREC_FP32) return fail(c, SPA_EINVAL, "precision");
     if (k.init_mode != SPA_INIT_PRIOR_IS && k.init_mode != SPA_INIT_RESAMPLE_MOVE) return fail(c, SPA_EINVAL, "init_mode");
     if (k.burn_in_steps < 0) return fail(c, SPA_EINVAL, "burn_in_steps");
@@ -470,6 +571,7 @@ int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
     CK(launch_store_finish(c->G, n, p, c->Kp, c->sums, c->mean, c->sd, c->v, c->l2e_s, c->mean_f, c->Gbf, c->Xf, c->d_err,
                            st),
        "store pack");
+    CK(launch_store_pack_t(c->G, c->y, n, p, c->n_r, c->GT, c->yv, st), "store pack transposed");
     return read_error_word(c);
 }
 
@@ -480,7 +582,7 @@ void destroy(spa_ctx* c)
     free_workspace(c->ws);
     free_runbufs(c->rb);
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
-    dfree(c->l2e_s); dfree(c->mean_f); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err);
+    dfree(c->l2e_s); dfree(c->mean_f); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -544,6 +646,9 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     CA(l2e_s, p); CA(mean_f, p);
     CA(Xf, n * p);
     CA(Gbf, n * c->Kp);
+    c->n_r = round_up(n, 64);
+    CA(GT, p * c->n_r);
+    CA(yv, n);
     CA(d_err, 1);
 #undef CA
     if (e != cudaSuccess) {
@@ -619,6 +724,10 @@ static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int
     if (rc != SPA_OK) return rc;
     rc = ensure_runbufs(c, T);
     if (rc != SPA_OK) return rc;
+    if (c->cfg.move_kind == SPA_MOVE_MALA) {
+        rc = ensure_mala_buffers(c);
+        if (rc != SPA_OK) return rc;
+    }
     cudaStream_t st = c->stream();
     CK(cudaMemcpyAsync(c->rb.sched, sched, sizeof(double) * (size_t)T,
                        sched_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
@@ -816,6 +925,36 @@ static int grad_impl(spa_ctx* c, const float* B, bool dev, int64_t N, double cs,
     if (rc != SPA_OK) return rc;
     Workspace& w = c->ws;
     const int64_t p = c->p, n = c->n;
+    if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        rc = ensure_adjoint_buffers(c);
+        if (rc != SPA_OK) return rc;
+        if (!w.grad) {
+            cudaError_t e = dalloc(&w.grad, (size_t)(N * p));
+            if (e != cudaSuccess) return cuda_fail(c, e, "gradient buffer");
+        }
+        cudaStream_t st = st_user ? st_user : c->stream();
+        if (st_user) CK(cudaStreamSynchronize(c->stream()), "sync context stream");
+        CK(cudaMemcpyAsync(w.beta, B, sizeof(float) * (size_t)(N * p),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st),
+           "copy B");
+        Enq q;
+        q.c = c;
+        q.st = st;
+        q.ck(launch_propose_rw(w.beta, w.beta_p, w.A, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s, c->mean_f,
+                               c->v, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st));
+        enq_grad_tc(q, dev ? grad : w.grad, w.beta, cs, N);
+        AcceptArgs a = accept_args(c, nullptr);
+        a.ll = (dev && ll) ? ll : w.ll;
+        a.lp = nullptr;
+        q.ck(launch_accept(a, N, (int)p, 0, 0, 0u, nullptr, c->d_err, st));
+        if (q.e != cudaSuccess) return cuda_fail(c, q.e, "gradient (tensor cores)");
+        if (!dev) {
+            CK(cudaMemcpyAsync(grad, w.grad, sizeof(float) * (size_t)(N * p), cudaMemcpyDeviceToHost, st), "copy grad");
+            if (ll) CK(cudaMemcpyAsync(ll, w.ll, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st), "copy ll");
+        }
+        CK(cudaStreamSynchronize(st), "sync");
+        return read_error_word(c);
+    }
     if (!w.eta) {
         const int64_t tiles = (n + SIMT_TILE_N - 1) / SIMT_TILE_N;
         cudaError_t e = dalloc(&w.eta, (size_t)(N * n + tiles * N));

@@ -26,6 +26,9 @@ cudaError_t launch_store_finish(const int8_t* G, int64_t n, int64_t p, int Kp, c
                                 double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f,
                                 __nv_bfloat16* Gbf, float* Xf, uint32_t* err, cudaStream_t st);
 
+cudaError_t launch_store_pack_t(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, int64_t n_r,
+                                __nv_bfloat16* GT, float* yv, cudaStream_t st);
+
 // ------------------------------------------------------------- SMC kernels
 struct PriorArgs {
     float a;   // degrees of freedom (ignored for the double exponential)
@@ -63,6 +66,17 @@ struct AcceptArgs {
 };
 cudaError_t launch_accept(const AcceptArgs& a, int64_t N, int p, int mode, int t, uint32_t m,
                           const uint64_t* seed, uint32_t* err, cudaStream_t st);
+
+// MALA proposal (needs grad l at beta in gl, D_j from launch_colstats kind 1, lambda on the
+// device) and its MH test with the Langevin q-correction; accepted rows move beta and gl.
+cudaError_t launch_propose_mala(const float* beta, const float* gl, float* beta_p, __nv_bfloat16* A, int ldA, int Kp,
+                                double* lin_p, double* lp_p, double* xi2, const float* D, const double* lam,
+                                const float* l2e_over_s, const float* mean_f, const double* v, int64_t N, int p,
+                                PriorArgs pr, const double* sched, int t, uint32_t m, const uint64_t* seed,
+                                cudaStream_t st);
+cudaError_t launch_accept_mala(const AcceptArgs& a, float* gl, const float* gl_p, const double* xi2, const float* D,
+                               const double* lam, int64_t N, int p, PriorArgs pr, const double* sched, int t, uint32_t m,
+                               const uint64_t* seed, uint32_t* err, cudaStream_t st);
 
 cudaError_t launch_reweight(const float* beta, double* logw, double* lp, int64_t N, int p, PriorArgs pr,
                             const double* sched, int t, uint32_t* err, cudaStream_t st);
@@ -131,8 +145,32 @@ TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms);
 cudaError_t tc_init_attributes();
 bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp);
 bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN);
+// Residual mode of the likelihood kernel (the adjoint's first half): also writes
+// r = y - logit^{-1}(eta) as BF16 hi | lo rows of R [N_pad][2 n_r] and its row sums.
+struct ResidArgs {
+    const float* yv;         // y as floats, n entries
+    __nv_bfloat16* R;        // [N_pad][2 n_r], columns >= n stay zero
+    int64_t n_r;             // round_up(n, 64)
+    float* rsum_part;        // same layout as the softplus partials
+};
 cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n,
-                             int Kp, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st);
+                             int Kp, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
+                             const ResidArgs* resid = nullptr);
+
+// The adjoint's second half: C = R G (tcgen05, split-BF16 R, exact G^T [p][n_r]) into
+// gpart[ksplit][N_pad][p], then grad l = (sum C - m_j sum r) / s_j (+ prior gradient).
+struct AdjPlan {
+    int64_t n_r;
+    int kblocks, BN2, p_tiles, m_tiles, ksplit, grid;
+};
+AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms);
+bool adj_make_map_R(CUtensorMap* map, const __nv_bfloat16* R, int64_t N_pad, int64_t n_r);
+bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n_r, int BN2);
+cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p, float* gpart,
+                              int64_t N_pad, uint32_t* err, cudaStream_t st);
+cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
+                               int64_t N, int p, const double* mean, const double* sd, const float* B, PriorArgs pr,
+                               double c, float* grad, cudaStream_t st);
 
 // Plain FP32 SIMT path: partial[nt * N_pad + i] = sum over 64-individual tile nt of
 // softplus(eta_i) (natural units).

@@ -225,9 +225,10 @@ def test_loglik_full_size_sampled(spa, name):
 
 # ------------------------------------------------------------------ gradient
 def test_gradient_matches_oracle_and_differences(spa):
+    """The plain FP32 adjoint: 1e-5 relative to sum_i |x_ij|."""
     reg = synth.make_region(300, 37, 0.9, (0.5, -0.4), seed=3)
     B = synth.random_particles(70, 37, 0.2, seed=4)
-    with spa.Region(reg.G, reg.y, 2.0) as r:
+    with spa.Region(reg.G, reg.y, 2.0, config=spa.make_config(precision="fp32")) as r:
         ll, g = r.grad(B, 0.0)
         llc, gc = r.grad(B, 0.05)
     o_ll, o_g = oracle.loglik_grad(reg.G, reg.y, B.astype(np.float64))
@@ -248,6 +249,45 @@ def test_gradient_matches_oracle_and_differences(spa):
             Bm[0, j] -= h
             fd = (oracle.loglik(reg.G, reg.y, Bp)[0] - oracle.loglik(reg.G, reg.y, Bm)[0]) / (2 * h)
             assert abs(fd - g[k, j]) <= 1e-4 * max(1.0, abs(fd))
+
+
+def grad_split_bound(G, B):
+    """Per-entry bound of the split-BF16 (tensor-core) log-likelihood gradient.
+
+    r_i = y_i - logit^{-1}(eta_i) inherits the eta error (|d r / d eta| <= 1/4) plus 2^-20 from
+    the ex2 / rcp approximations; r is split hi + lo (2^-16), products with g are exact,
+    and at most 2 n_r terms are accumulated in FP32; the row sum of r feeds the mean term."""
+    Gd = G.astype(np.float64)
+    n, p = G.shape
+    m, s = Gd.mean(0), Gd.std(0)
+    X = (Gd - m) / s
+    Bd = B.astype(np.float64)
+    eta = Bd @ X.T  # (N, n)
+    r = np.abs(0.5 - 1.0 / (1.0 + np.exp(-eta))) + 0.5  # >= |y - sigma|
+    bt = np.abs(Bd / s)
+    off = np.abs((Bd / s) @ m)
+    e_eta = (2.0 ** -15 + (2 * p + 2) * 2.0 ** -23) * (bt @ Gd.T + off[:, None])  # (N, n)
+    n_r = (n + 63) // 64 * 64
+    acc = (2.0 ** -15 + 2 * n_r * 2.0 ** -23) * (r @ Gd) + m[None, :] * n * 2.0 ** -23 * r.sum(1)[:, None]
+    return acc / s[None, :] + (e_eta / 4 + 2.0 ** -20) @ np.abs(X)
+
+
+@pytest.mark.parametrize("n,p,N", [(7, 3, 5), (300, 37, 70), (600, 130, 300), (2000, 200, 256), (1000, 300, 129)])
+def test_gradient_tensor_core_bound(spa, n, p, N):
+    reg = synth.make_region(n, p, 0.9, (0.5, -0.4), seed=n + 3 * p)
+    B = synth.random_particles(N, p, 0.2, seed=N + 1)
+    with spa.Region(reg.G, reg.y, 2.0) as r:
+        ll, g = r.grad(B, 0.0)
+        _, gc = r.grad(B, 0.05)
+    o_ll, o_g = oracle.loglik_grad(reg.G, reg.y, B.astype(np.float64))
+    assert np.all(np.abs(ll - o_ll) <= split_bound(reg.G, B, p))
+    bound = grad_split_bound(reg.G, B)
+    err = np.abs(g - o_g)
+    assert np.all(err <= bound), np.max(err / bound)
+    assert np.median(err / bound) < 0.05
+    a, c = 2.0, 0.05
+    prior = -(a + 1) * np.sign(B) / (a * c + np.abs(B))
+    assert np.all(np.abs((gc - g) - prior) <= 1e-5 * (1 + np.abs(prior)) + 2 * bound)
 
 
 # ------------------------------------------------------------------ errors

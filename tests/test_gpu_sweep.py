@@ -75,12 +75,13 @@ def test_same_seed_first_step_agrees(spa):
     assert np.max(np.abs(g["mean"][0] - o["mean"][0])) < 5e-3
 
 
-@pytest.mark.parametrize("p,a,direction", [(1, 1.0, "s2d"), (2, 4.0, "d2s"), (1, math.inf, "d2s")])
-def test_sweep_matches_quadrature(spa, p, a, direction):
+@pytest.mark.parametrize("p,a,direction,move", [(1, 1.0, "s2d", "rw"), (2, 4.0, "d2s", "rw"), (1, math.inf, "d2s", "rw"),
+                                                (2, 2.0, "d2s", "mala")])
+def test_sweep_matches_quadrature(spa, p, a, direction, move):
     reg = synth.make_region(200, p, 0.9, (0.6,) * p, seed=2024 + p)
     sched = synth.geometric_schedule(16, -6.0, 0.0, sparse_to_diffuse=(direction == "s2d"))
     init = "prior_is" if direction == "s2d" else "resample_move"
-    cfg = spa.make_config(init=init, burn_in_steps=25)
+    cfg = spa.make_config(move=move, init=init, burn_in_steps=25)
     runs = _gpu_runs(spa, reg, a, sched, 2048, 4, cfg, list(range(100, 100 + R)))
     post = Posterior(reg.G, reg.y, a, sched)
     truth_mean = np.array([post.mean(c) for c in sched])
@@ -134,3 +135,46 @@ def test_run_batch_matches_individual_runs(spa):
     finally:
         for r in rs:
             r.close()
+
+
+@pytest.mark.parametrize("precision", ["split_bf16", "fp32"])
+def test_mala_sweep_matches_oracle(spa, precision):
+    """MALA moves (the adjoint-driven kernel) on a reduced copy of the MALA workload."""
+    reg = synth.make_region(400, 24, 0.95, (0.3, 0.5, -0.4), seed=1003)
+    sched = synth.geometric_schedule(20)
+    seeds = list(range(1, R + 1))
+    cfg = spa.make_config(move="mala", precision=precision)
+    g = _gpu_runs(spa, reg, 2.0, sched, 1024, 5, cfg, seeds)
+    ocfg = oracle.make_config(move="mala")
+    o = [oracle.run(reg.G, reg.y, 2.0, sched, 1024, 5, seed=100 + s, cfg=ocfg) for s in seeds]
+    _check(_two_sample_z([r["mean"] for r in g], [r["mean"] for r in o], 2e-4), "mean")
+    _check(_two_sample_z([r["conc"] for r in g], [r["conc"] for r in o], 2e-3), "conc")
+    _check(_two_sample_z([np.cumsum(r["log_z_inc"]) for r in g], [np.cumsum(r["log_z_inc"]) for r in o], 2e-3),
+           "log Z")
+    acc = np.mean([r["accept_rate"] for r in g], axis=0)
+    assert np.mean(acc[5:]) > 0.3  # the adaptive step reaches a working acceptance
+
+
+def test_autograd_loglik_backward_is_the_adjoint(spa):
+    torch = pytest.importorskip("torch")
+    reg = synth.make_region(300, 16, 0.9, (0.5, -0.4), seed=21)
+    B = synth.random_particles(40, 16, 0.3, seed=22)
+    with spa.Region(reg.G, reg.y, 1.0) as r:
+        Bt = torch.tensor(B, device="cuda", requires_grad=True)
+        ll = spa.loglik_autograd(Bt, r)
+        w = torch.linspace(0.5, 1.5, 40, device="cuda", dtype=torch.float64)
+        (ll * w).sum().backward()
+        got = Bt.grad.cpu().numpy()
+    o_ll, o_g = oracle.loglik_grad(reg.G, reg.y, B.astype(np.float64))
+    bound = split_bound_local(reg.G, B)
+    assert np.all(np.abs(ll.detach().cpu().numpy() - o_ll) <= bound)
+    wts = np.linspace(0.5, 1.5, 40)[:, None]
+    from tests.test_gpu_parity import grad_split_bound
+
+    assert np.all(np.abs(got - o_g * wts) <= grad_split_bound(reg.G, B) * wts + 1e-6)
+
+
+def split_bound_local(G, B):
+    from tests.test_gpu_parity import split_bound
+
+    return split_bound(G, B, B.shape[1])
