@@ -189,6 +189,29 @@ int spa_grad_device(spa_ctx* ctx, const float* B_device, int64_t N, double c, do
  * Bit-exact given W and u. */
 int spa_resample_systematic(const double* W, int64_t N, double u, int32_t* idx_out);
 
+/* Allocation-free variant of spa_resample_systematic (the paper has no counterpart: it
+ * is a deployment convenience). For callers that cannot call cudaMalloc: a process whose
+ * device memory is held by another allocator's pool, a latency-critical path where an
+ * allocation would synchronise the device, a service that must not grow its device
+ * footprint after start-up. The caller passes DEVICE buffers; the call allocates nothing.
+ *   W_device    N normalised weights (doubles, device memory)
+ *   u           the uniform in [0,1)
+ *   idx_device  N int32 ancestor indices (device memory), bit-identical to
+ *               spa_resample_systematic's for the same W and u
+ *   stream      cudaStream_t to enqueue on (NULL: the legacy default stream); returns
+ *               without synchronising
+ * The kernel's scratch (N + ceil(N/256) + 1 doubles) is a fixed device array of
+ * SPA_NOALLOC_RESAMPLE_MAX_N + 1025 doubles (about 2.1 MB), held by every GPU that loads
+ * the library until the process exits. N > SPA_NOALLOC_RESAMPLE_MAX_N is rejected with
+ * SPA_EINVAL (message in spa_last_error(NULL)). The first call on a device looks the
+ * array's address up (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture. All calls share the array: calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race and must be serialised by
+ * the caller. Nothing needs to start at zero: each call writes every entry it reads. */
+#define SPA_NOALLOC_RESAMPLE_MAX_N 262144
+int spa_resample_systematic_noalloc(const double* W_device, int64_t N, double u, int32_t* idx_device,
+                                    void* stream);
+
 /* log Gt(beta | a, c) = -log(2c) - (a+1) log1p(|beta|/(a c)) per element (eq. gent_prior,
  * q = 1, mu = 0); nu = +INFINITY gives -log(2c) - |beta|/c. out: k doubles. */
 int spa_prior_logpdf(double nu, double c, const float* beta, int64_t k, double* out);

@@ -85,6 +85,7 @@ _SIGS = {
     "spa_grad_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p,
                                   C.c_void_p]),
     "spa_resample_systematic": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
+    "spa_resample_systematic_noalloc": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
     "spa_prior_logpdf": (C.c_int, [C.c_double, C.c_double, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_incr_weight": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int64, C.c_int64,
                                   C.c_void_p]),
@@ -311,6 +312,16 @@ def resample_systematic(W, u: float) -> np.ndarray:
     idx = np.zeros(W.size, np.int32)
     _check(load().spa_resample_systematic(_ptr(W), W.size, float(u), _ptr(idx)))
     return idx
+
+
+NOALLOC_RESAMPLE_MAX_N = 262144
+
+
+def resample_systematic_noalloc(W_dev, u: float, idx_dev, stream: int = 0):
+    """Allocation-free systematic resampling on device buffers (torch tensors): W_dev float64,
+    idx_dev int32, both of length N <= NOALLOC_RESAMPLE_MAX_N. Enqueued on `stream`."""
+    _check(load().spa_resample_systematic_noalloc(_ptr(W_dev), W_dev.numel(), float(u), _ptr(idx_dev),
+                                                  stream or None))
 
 
 def prior_logpdf(nu: float, c: float, beta) -> np.ndarray:

@@ -23,7 +23,11 @@ using namespace spa;
 
 namespace {
 
-thread_local std::string g_thread_error;
+// Message of the last failed context-free call on this thread (fixed storage: setting it
+// never allocates).
+thread_local char g_thread_error[512] = {0};
+
+void set_thread_error_str(const std::string& m) { std::snprintf(g_thread_error, sizeof(g_thread_error), "%s", m.c_str()); }
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
@@ -88,6 +92,16 @@ struct GraphKey {
 
 }  // namespace
 
+namespace spa {
+void set_thread_error(const char* msg, int64_t value)
+{
+    if (value >= 0)
+        std::snprintf(g_thread_error, sizeof(g_thread_error), "%s%lld", msg, (long long)value);
+    else
+        std::snprintf(g_thread_error, sizeof(g_thread_error), "%s", msg);
+}
+}  // namespace spa
+
 struct spa_ctx {
     int64_t n = 0, p = 0;
     int Kp = 0;
@@ -129,7 +143,7 @@ int fail(spa_ctx* c, int code, const std::string& msg)
     if (c)
         c->err = msg;
     else
-        g_thread_error = msg;
+        set_thread_error_str(msg);
     return code;
 }
 
@@ -625,7 +639,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     if (!c) return fail(nullptr, SPA_ENOMEM, "host allocation");
     int rc = check_device(c);
     if (rc != SPA_OK) {
-        g_thread_error = c->err;
+        set_thread_error_str(c->err);
         destroy(c);
         return rc;
     }
@@ -652,20 +666,20 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     CA(d_err, 1);
 #undef CA
     if (e != cudaSuccess) {
-        g_thread_error = std::string("device allocation: ") + cudaGetErrorString(e);
+        set_thread_error_str(std::string("device allocation: ") + cudaGetErrorString(e));
         destroy(c);
         return e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA;
     }
     const double one = 1.0;
     e = cudaMemcpy(c->unit_c, &one, sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        g_thread_error = cudaGetErrorString(e);
+        set_thread_error_str(cudaGetErrorString(e));
         destroy(c);
         return SPA_ECUDA;
     }
     rc = upload_data(c, G, y);
     if (rc != SPA_OK) {
-        g_thread_error = c->err;
+        set_thread_error_str(c->err);
         destroy(c);
         return rc;
     }
@@ -702,7 +716,7 @@ void spa_destroy(spa_ctx* c) { destroy(c); }
 const char* spa_last_error(const spa_ctx* c)
 {
     if (c) return c->err.c_str();
-    return g_thread_error.c_str();
+    return g_thread_error;
 }
 
 int64_t spa_last_launch_count(const spa_ctx* c) { return c ? c->last_launches : 0; }
@@ -823,7 +837,7 @@ int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, s
         spa_ctx* c = ctxs[r];
         int rc = run_common(c, args->schedules[r], false, args->T[r], args->N[r], args->moves_per_step[r], args->seeds[r]);
         if (rc != SPA_OK) {
-            g_thread_error = c ? c->err : "NULL context";
+            set_thread_error_str(c ? c->err : std::string("NULL context"));
             return rc;
         }
     }
@@ -848,7 +862,7 @@ int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, s
         }
         int rc = read_error_word(c);
         if (rc != SPA_OK) {
-            g_thread_error = c->err;
+            set_thread_error_str(c->err);
             return rc;
         }
     }

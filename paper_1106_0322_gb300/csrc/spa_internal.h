@@ -13,6 +13,10 @@ constexpr double LOG2E = 1.4426950408889634073599246810019;
 
 // Launch helpers return cudaGetLastError() of the launch.
 
+// Set the message spa_last_error(NULL) returns on this thread ("msg" followed by value
+// when value >= 0). Writes into fixed storage; never allocates.
+void set_thread_error(const char* msg, int64_t value = -1);
+
 // ----------------------------------------------------------- genotype store
 // Integer column sums of G (S1 = sum g, S2 = sum g^2, SY = sum y g) and the case count,
 // with device-side validation of G in {0,1,2} and y in {0,1} (DERR_INPUT).
