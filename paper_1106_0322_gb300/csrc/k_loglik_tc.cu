@@ -1,18 +1,17 @@
 // k_loglik_tc.cu -- the particle log-likelihood on the 5th-generation tensor cores.
 //
 // Section 2's log-likelihood of particle k is l_k = sum_i [y_i eta_ki - softplus(eta_ki)],
-// eta = X beta_k. The linear part equals beta_k . (X^T y) and is formed by the proposal
-// kernel. This kernel computes the softplus part for N particles at once as a
-// contraction followed by a row reduction that never leaves the chip:
+// eta = X beta_k. This kernel computes it for N particles at once as a contraction
+// followed by a row reduction that never leaves the chip:
 //
 //   eta2[k, i] = sum_j A[k, j] * Gb[i, j]      (tcgen05.mma, BF16 x BF16 -> FP32 in TMEM)
-//   partial[k] += sum_i log2(1 + 2^eta2[k, i])  (epilogue warps, ex2/lg2 on the SFU)
+//   partial[k] += sum_i y_i eta2 - log2(1 + 2^eta2[k, i])  (epilogue warps, ex2/lg2 on the SFU)
 //
 // with A[k] = [hi(bt_k) | lo(bt_k)] the split-BF16 copy of bt_kj = beta_kj log2(e)/s_j
 // (plus the offset -sum_j m_j bt_kj in the ones column), and Gb = [G, 1] the exact BF16
 // genotypes. Both halves of A multiply the same G tile, so each pipeline stage carries
-// A_hi, A_lo and G for one 64-wide k-block; eta2 = eta log2(e) and softplus(eta) =
-// ln(2) * log2(1 + 2^eta2).
+// A_hi, A_lo and G for one 64-wide k-block; eta2 = eta log2(e), so l = ln(2) * sum of
+// [y eta2 - log2(1 + 2^eta2)]. y is read as a bitmask, one 32-bit word per 32 individuals.
 //
 // Tile: 128 particles (M, TMEM lanes) x BN individuals (N, TMEM columns). A persistent
 // grid walks the (particle-tile, individual-tile) units in order; each unit's row sums go
@@ -49,15 +48,17 @@ struct TcCfg {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
 };
 
-__device__ __forceinline__ float sum_softplus2_32(const float (&v)[32], int valid)
+// Sum over 32 columns of the base-2 log-likelihood terms y eta2 - log2(1 + 2^eta2); bit k of
+// ybits is y of column k.
+__device__ __forceinline__ float sum_ll2_32(const float (&v)[32], int valid, uint32_t ybits)
 {
     float t[32];
     if (valid >= 32) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) t[k] = softplus2(v[k]);
+        for (int k = 0; k < 32; ++k) t[k] = (((ybits >> k) & 1u) ? v[k] : 0.0f) - softplus2(v[k]);
     } else {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) t[k] = (k < valid) ? softplus2(v[k]) : 0.0f;
+        for (int k = 0; k < 32; ++k) t[k] = (k < valid) ? (((ybits >> k) & 1u) ? v[k] : 0.0f) - softplus2(v[k]) : 0.0f;
     }
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1)
@@ -73,11 +74,11 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Residual mode: besides the softplus sum, r = y - logit^{-1}(eta) for the 32 columns of
-// this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into *rsum.
+// Residual mode: besides the log-likelihood sum, r = y - logit^{-1}(eta) for the 32 columns
+// of this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into *rsum.
 // eta2 = eta log2(e): with e = 2^-|eta2|, softplus2 = max(eta2, 0) + log2(1 + e) and
 // logit^{-1}(eta) = 1/(1 + e) for eta >= 0, e/(1 + e) otherwise (one ex2 shared).
-__device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, const float* __restrict__ yv,
+__device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, uint32_t ybits,
                                              __nv_bfloat16* __restrict__ rrow, int64_t n_r, float& rsum)
 {
     float sp[32];
@@ -92,8 +93,9 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, co
         const float inv = rcp_approx(onepe);
         const float sig = (x >= 0.0f) ? inv : e * inv;
         const bool ok = k < valid;
-        sp[k] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
-        const float r = ok ? __ldg(yv + k) - sig : 0.0f;
+        const bool yk = (ybits >> k) & 1u;
+        sp[k] = ok ? (yk ? x : 0.0f) - (fmaxf(x, 0.0f) + lg2_approx(onepe)) : 0.0f;
+        const float r = ok ? (yk ? 1.0f : 0.0f) - sig : 0.0f;
         rs[k] = r;
         split_bf16(r, hi[k], lo[k]);
     }
@@ -122,8 +124,8 @@ template <int BN, int STAGES, bool RESID>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n_tiles,
                 int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial, int64_t N_pad,
-                uint32_t* __restrict__ err, const float* __restrict__ yv, __nv_bfloat16* __restrict__ R, int64_t n_r,
-                float* __restrict__ rsum_part)
+                uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
+                int64_t n_r, float* __restrict__ rsum_part)
 {
     using C = TcCfg<BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
@@ -250,17 +252,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int col0 = half * (BN / 2);
             const int valid = n - nt * BN - col0;
             float acc = 0.0f, rsum = 0.0f;
-#pragma unroll 1
-            for (int c = 0; c < BN / 2; c += 32) {
+            // software pipeline over the 32-column chunks: the TMEM load of chunk k+1 is in
+            // flight while chunk k is reduced
+            constexpr int NCH = (BN / 2) / 32;
+            const uint32_t tbase = tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)col0;
+            uint32_t ra[32], rb[32];
+            if (valid > 0) {
+                tmem_ld32_async(tbase, ra);
+                tmem_wait_ld(ra);
+            }
+#pragma unroll
+            for (int ch = 0; ch < NCH; ++ch) {
+                const int c = ch * 32;
                 if (valid - c <= 0) break;
+                uint32_t(&cur)[32] = (ch & 1) ? rb : ra;
+                uint32_t(&nxt)[32] = (ch & 1) ? ra : rb;
+                const bool more = (ch + 1 < NCH) && (valid - c - 32 > 0);
+                if (more) tmem_ld32_async(tbase + (uint32_t)(c + 32), nxt);
                 float v[32];
-                tmem_ld32(tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)(col0 + c), v);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(cur[k]);
+                const int64_t i0 = (int64_t)nt * BN + col0 + c;
+                const uint32_t yb = __ldg(ybits + (i0 >> 5));
                 if (RESID) {
-                    const int64_t i0 = (int64_t)nt * BN + col0 + c;
-                    acc += resid_chunk(v, valid - c, yv + i0, R + ((int64_t)mt * BM + row) * 2 * n_r + i0, n_r, rsum);
+                    acc += resid_chunk(v, valid - c, yb, R + ((int64_t)mt * BM + row) * 2 * n_r + i0, n_r, rsum);
                 } else {
-                    acc += sum_softplus2_32(v, valid - c);
+                    acc += sum_ll2_32(v, valid - c, yb);
                 }
+                if (more) tmem_wait_ld(nxt);
             }
             tc_fence_before();
             __syncwarp();
@@ -487,12 +506,13 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
 
 template <int BN, int STAGES, bool RESID>
 cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
-                      float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra, cudaStream_t st)
+                      const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
+                      cudaStream_t st)
 {
     using C = TcCfg<BN, STAGES>;
     k_loglik_tc<BN, STAGES, RESID><<<plan.grid, TC_THREADS, C::SMEM, st>>>(
-        mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err,
-        ra ? ra->yv : nullptr, ra ? ra->R : nullptr, ra ? ra->n_r : 0, ra ? ra->rsum_part : nullptr);
+        mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits,
+        ra ? ra->R : nullptr, ra ? ra->n_r : 0, ra ? ra->rsum_part : nullptr);
     return cudaGetLastError();
 }
 
@@ -538,14 +558,15 @@ bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp
 }
 
 cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
-                             float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st, const ResidArgs* ra)
+                             const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
+                             const ResidArgs* ra)
 {
     if (ra) {
-        if (plan.BN == 256) return launch_tc<256, 3, true>(mapA, mapB, plan, n, Kp, partial, N_pad, err, ra, st);
-        return launch_tc<128, 4, true>(mapA, mapB, plan, n, Kp, partial, N_pad, err, ra, st);
+        if (plan.BN == 256) return launch_tc<256, 3, true>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st);
+        return launch_tc<128, 4, true>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st);
     }
-    if (plan.BN == 256) return launch_tc<256, 3, false>(mapA, mapB, plan, n, Kp, partial, N_pad, err, nullptr, st);
-    return launch_tc<128, 4, false>(mapA, mapB, plan, n, Kp, partial, N_pad, err, nullptr, st);
+    if (plan.BN == 256) return launch_tc<256, 3, false>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, nullptr, st);
+    return launch_tc<128, 4, false>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, nullptr, st);
 }
 
 AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms)

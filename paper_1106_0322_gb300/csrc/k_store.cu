@@ -116,7 +116,25 @@ __global__ void k_store_pack_t(const int8_t* __restrict__ G, const uint8_t* __re
     }
 }
 
+__global__ void k_store_ybits(const uint8_t* __restrict__ y, int64_t n, int64_t words, uint32_t* __restrict__ ybits)
+{
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= words) return;
+    uint32_t v = 0u;
+    for (int k = 0; k < 32; ++k) {
+        const int64_t i = w * 32 + k;
+        if (i < n && y[i]) v |= 1u << k;
+    }
+    ybits[w] = v;
+}
+
 }  // namespace
+
+cudaError_t launch_store_ybits(const uint8_t* y, int64_t n, int64_t words, uint32_t* ybits, cudaStream_t st)
+{
+    k_store_ybits<<<(unsigned)((words + 127) / 128), 128, 0, st>>>(y, n, words, ybits);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_store_pack_t(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, int64_t n_r,
                                 __nv_bfloat16* GT, float* yv, cudaStream_t st)

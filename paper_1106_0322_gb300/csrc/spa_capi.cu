@@ -52,17 +52,23 @@ struct Workspace {
     float *beta = nullptr, *beta_p = nullptr, *scale = nullptr;
     __nv_bfloat16* A = nullptr;
     CUtensorMap mapA;
-    double *lin_p = nullptr, *lp_p = nullptr, *ll = nullptr, *lp = nullptr, *logw = nullptr, *W = nullptr;
-    double *ll_tmp = nullptr, *lp_tmp = nullptr, *cum = nullptr, *colpart = nullptr, *lambda = nullptr;
+    float2* lpt_p = nullptr;  // compensated log-prior term sums of the proposals
+    double *ll = nullptr, *lp = nullptr, *logw = nullptr, *W = nullptr;
+    float* Wf = nullptr;
+    uint32_t* wfix = nullptr;
+    double *ll_tmp = nullptr, *lp_tmp = nullptr, *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
+    unsigned int* lse_counter = nullptr;
+    float4* colpart = nullptr;
+    float* h = nullptr;  // MALA step h = lambda p^(-1/6)
     float* partial = nullptr;
     int32_t* idx = nullptr;
     int* flag = nullptr;
     float* eta = nullptr;  // gradient path scratch, allocated on first use
     float* grad = nullptr;
-    // MALA: log-likelihood gradient of the current and the proposed particles, sum xi^2
+    // MALA: log-likelihood gradient of the current and the proposed particles, forward residual sums
     float* gl = nullptr;
     float* gl_p = nullptr;
-    double* xi2 = nullptr;
+    float2* fwd = nullptr;
     // tensor-core adjoint: residuals r (BF16 hi | lo), their row sums, C = R G partials
     __nv_bfloat16* R = nullptr;
     float* rsum = nullptr;
@@ -122,6 +128,8 @@ struct spa_ctx {
     int mapB_BN = 0;
     __nv_bfloat16* GT = nullptr;  // [p][n_r] for the adjoint
     float* yv = nullptr;
+    uint32_t* ybits = nullptr;  // y as a bitmask, one word per 32 individuals
+    int64_t ywords = 0;
     int64_t n_r = 0;
     CUtensorMap mapGT;
     int mapGT_BN = 0;
@@ -167,10 +175,11 @@ int check_device(spa_ctx* c)
     CK(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
     if (prop.major != 10)
         return fail(c, SPA_EUNSUPPORTED, "the library is built for sm_103a (compute capability 10.x)");
+    CK(tc_init_attributes(), "tensor-core kernel attributes");
+    CK(smc_init_attributes(), "summaries kernel attributes");
     if (c) {
         c->device = dev;
         c->num_sms = prop.multiProcessorCount;
-        CK(tc_init_attributes(), "tensor-core kernel attributes");
     }
     return SPA_OK;
 }
@@ -197,10 +206,11 @@ int read_error_word(spa_ctx* c)
 void free_workspace(Workspace& w)
 {
     dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
-    dfree(w.lin_p); dfree(w.lp_p); dfree(w.ll); dfree(w.lp); dfree(w.logw); dfree(w.W);
-    dfree(w.ll_tmp); dfree(w.lp_tmp); dfree(w.cum); dfree(w.colpart); dfree(w.lambda);
+    dfree(w.lpt_p); dfree(w.ll); dfree(w.lp); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix);
+    dfree(w.ll_tmp); dfree(w.lp_tmp); dfree(w.cum); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
+    dfree(w.lse_scratch); dfree(w.lse_counter);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
-    dfree(w.gl); dfree(w.gl_p); dfree(w.xi2); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
+    dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
     w.N = w.N_pad = 0;
 }
 
@@ -246,11 +256,14 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     WA(beta_p, N * p);
     WA(scale, p);
     WA(A, N_pad * 2 * c->Kp);
-    WA(lin_p, N); WA(lp_p, N); WA(ll, N); WA(lp, N); WA(logw, N); WA(W, N);
+    WA(lpt_p, N); WA(ll, N); WA(lp, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
     WA(ll_tmp, N); WA(lp_tmp, N);
     WA(cum, N + nblk + 1);
-    WA(colpart, (int64_t)COLSTAT_SPLITS * p * 2);
+    WA(colpart, (int64_t)COLSTAT_SPLITS * p);
     WA(lambda, 1);
+    WA(h, 1);
+    WA(lse_scratch, LSE_SCRATCH);
+    WA(lse_counter, 1);
     WA(partial, parts * N_pad);
     WA(idx, N);
     WA(flag, 1);
@@ -263,6 +276,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     CK(cudaMemsetAsync(w.A, 0, sizeof(__nv_bfloat16) * (size_t)(N_pad * 2 * c->Kp), c->stream()), "memset A");
     CK(cudaMemsetAsync(w.partial, 0, sizeof(float) * (size_t)(parts * N_pad), c->stream()), "memset partial");
     CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->stream()), "memset flag");
+    CK(cudaMemsetAsync(w.lse_counter, 0, sizeof(unsigned int), c->stream()), "memset counter");
     if (!tc_make_map_A(&w.mapA, w.A, N_pad, c->Kp)) {
         free_workspace(w);
         return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the particle operand");
@@ -310,7 +324,7 @@ int ensure_mala_buffers(spa_ctx* c)
     cudaError_t e = cudaSuccess;
     if (!w.gl) e = dalloc(&w.gl, (size_t)(N * p));
     if (e == cudaSuccess && !w.gl_p) e = dalloc(&w.gl_p, (size_t)(N * p));
-    if (e == cudaSuccess && !w.xi2) e = dalloc(&w.xi2, (size_t)N);
+    if (e == cudaSuccess && !w.fwd) e = dalloc(&w.fwd, (size_t)N);
     if (e == cudaSuccess && plain && !w.eta) e = dalloc(&w.eta, (size_t)(N * n + tiles * N));
     if (e == cudaSuccess && plain && !w.grad) e = dalloc(&w.grad, (size_t)(N * p));
     if (e != cudaSuccess) return cuda_fail(c, e, "MALA buffers");
@@ -369,20 +383,11 @@ void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     Workspace& w = c->ws;
     const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
-    ResidArgs ra{c->yv, w.R, a.n_r, w.rsum};
-    q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, q.st, &ra));
+    ResidArgs ra{w.R, a.n_r, w.rsum};
+    q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra));
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean, c->sd, Bsrc, c->pr,
                             cs, out, q.st));
-}
-
-__global__ void k_set_f64(double* p, double v)
-{
-    if (threadIdx.x == 0) *p = v;
-}
-__global__ void k_adapt_lambda(double* lam, const unsigned long long* acc, double denom)
-{
-    if (threadIdx.x == 0 && denom > 0.0) *lam *= exp((double)*acc / denom - 0.574);
 }
 
 // log-likelihood of the current proposals (beta_p) into the partial sums
@@ -392,9 +397,9 @@ void enq_loglik(Enq& q)
     Workspace& w = c->ws;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
         const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
-        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, q.st));
+        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
     } else {
-        q.ck(launch_loglik_simt(w.beta_p, c->Xf, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
+        q.ck(launch_loglik_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
     }
 }
 
@@ -406,8 +411,7 @@ AcceptArgs accept_args(spa_ctx* c, unsigned long long* acc)
     a.beta_p = w.beta_p;
     a.ll = w.ll;
     a.lp = w.lp;
-    a.lin_p = w.lin_p;
-    a.lp_p = w.lp_p;
+    a.lpt_p = w.lpt_p;
     a.partial = w.partial;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
         a.n_parts = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms).n_parts;
@@ -431,8 +435,8 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     if (c->cfg.move_kind == SPA_MOVE_MALA) {
         for (int mm = 0; mm < M; ++mm) {
             const uint32_t m = m0 + (uint32_t)mm;
-            q.ck(launch_propose_mala(w.beta, w.gl, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.xi2,
-                                     w.scale, w.lambda, c->l2e_s, c->mean_f, c->v, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
+            q.ck(launch_propose_mala(w.beta, w.gl, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.fwd,
+                                     w.scale, w.h, c->l2e_s, c->mean_f, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
                                      c->rb.seed, q.st));
             if (tc) {
                 enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
@@ -442,17 +446,17 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
                                       q.st));
                 ++q.launches;  // the plain adjoint is two kernels
             }
-            q.ck(launch_accept_mala(a, w.gl, w.gl_p, w.xi2, w.scale, w.lambda, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
+            q.ck(launch_accept_mala(a, w.gl, w.gl_p, w.fwd, w.scale, w.h, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
                                     c->rb.seed, c->d_err, q.st));
         }
         return;
     }
     for (int mm = 0; mm < M; ++mm) {
         const uint32_t m = m0 + (uint32_t)mm;
-        q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
-                               c->mean_f, c->v, w.N, (int)c->p, c->pr, c->rb.sched, t, m, c->rb.seed, 1, q.st));
+        q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
+                               c->mean_f, w.N, (int)c->p, c->pr, c->rb.sched, t, m, c->rb.seed, 1, q.st));
         enq_loglik(q);
-        q.ck(launch_accept(a, w.N, (int)c->p, 1, t, m, c->rb.seed, c->d_err, q.st));
+        q.ck(launch_accept(a, w.N, (int)c->p, c->pr, c->rb.sched, 1, t, m, c->rb.seed, c->d_err, q.st));
     }
 }
 
@@ -461,11 +465,13 @@ void enq_resample(Enq& q, int t)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     q.ck(launch_resample_index(w.W, w.N, w.cum, w.idx, w.flag, t, c->rb.seed, 0.0, q.st));
+    ++q.launches;  // scan + search
     const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
     q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr,
                        mala ? w.gl_p : nullptr, w.N, (int)c->p, w.flag, q.st));
+    WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
     q.ck(launch_copyback(w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr, mala ? w.gl_p : nullptr,
-                         w.logw, w.W, w.N, (int)c->p, w.flag, q.st));
+                         wa, w.N, (int)c->p, w.flag, q.st));
 }
 
 void enq_colstats(Enq& q, int t)
@@ -473,8 +479,8 @@ void enq_colstats(Enq& q, int t)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     const int kind = c->cfg.move_kind == SPA_MOVE_MALA ? 1 : 0;
-    q.ck(launch_colstats(w.beta, w.W, w.N, (int)c->p, w.colpart, w.scale, kind, c->cfg.rw_scale,
-                         kind ? w.lambda : nullptr, c->cfg.sd_floor, c->rb.sched, t, q.st));
+    q.ck(launch_colstats(w.beta, w.Wf, w.N, (int)c->p, w.colpart, w.scale, kind, c->cfg.rw_scale,
+                         kind ? w.lambda : nullptr, c->cfg.sd_floor, c->rb.sched, t, kind ? w.h : nullptr, q.st));
     ++q.launches;  // two kernels
 }
 
@@ -499,14 +505,12 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     }
     if (q.e == cudaSuccess) q.e = cudaMemsetAsync(r.acc, 0, sizeof(unsigned long long) * (size_t)(T + 1), q.st);
     if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
-    if (mala) {
-        k_set_f64<<<1, 32, 0, q.st>>>(w.lambda, cfg.mala_h);
-        q.ck(cudaGetLastError());
-    }
+    if (mala) q.ck(launch_set_f64(w.lambda, cfg.mala_h, q.st));
+    const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
     // t = 0: prior draws, their log-likelihoods, importance weights
     q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
-    q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
-                           c->mean_f, c->v, w.N, p, c->pr, r.sched, 0, 0u, r.seed, 0, q.st));
+    q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
+                           c->mean_f, w.N, p, c->pr, r.sched, 0, 0u, r.seed, 0, q.st));
     if (mala && tc) {
         enq_grad_tc(q, w.gl, w.beta, 0.0, w.N);  // also leaves the softplus partials of the draws
     } else {
@@ -518,9 +522,11 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     }
     AcceptArgs a0 = accept_args(c, nullptr);
     a0.logw = w.logw;
-    q.ck(launch_accept(a0, w.N, p, 0, 0, 0u, r.seed, c->d_err, q.st));
+    q.ck(launch_accept(a0, w.N, p, c->pr, r.sched, 0, 0, 0u, r.seed, c->d_err, q.st));
     const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
-    q.ck(launch_lse_ess(w.logw, w.W, w.N, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag, c->d_err, q.st));
+    q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
+                        c->d_err, q.st));
+    ++q.launches;  // log-sum-exp is two kernels
     uint32_t m_base = 0;
     if (rm) {
         enq_resample(q, 0);
@@ -529,10 +535,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
             if (q.e == cudaSuccess) q.e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), q.st);
             enq_colstats(q, 0);
             enq_moves(q, 0, m_base, M, scratch);
-            if (mala) {
-                k_adapt_lambda<<<1, 32, 0, q.st>>>(w.lambda, scratch, denom);
-                q.ck(cudaGetLastError());
-            }
+            if (mala) q.ck(launch_adapt_lambda(w.lambda, scratch, denom, q.st));
             m_base += (uint32_t)M;
         }
         q.ck(launch_mark_uniform(w.N, 0, r.ess, r.res, w.flag, q.st));
@@ -540,16 +543,15 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0) {
             q.ck(launch_reweight(w.beta, w.logw, w.lp, w.N, p, c->pr, r.sched, (int)t, c->d_err, q.st));
-            q.ck(launch_lse_ess(w.logw, w.W, w.N, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag, c->d_err, q.st));
+            q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
+                                c->d_err, q.st));
+            ++q.launches;
         }
         enq_resample(q, (int)t);
         enq_colstats(q, (int)t);
         enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
-        q.ck(launch_summaries(w.beta, w.W, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, q.st));
-        if (mala) {
-            k_adapt_lambda<<<1, 32, 0, q.st>>>(w.lambda, r.acc + t, denom);
-            q.ck(cudaGetLastError());
-        }
+        q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, q.st));
+        if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
     }
     q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
     *err_out = q.e;
@@ -586,6 +588,7 @@ int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
                            st),
        "store pack");
     CK(launch_store_pack_t(c->G, c->y, n, p, c->n_r, c->GT, c->yv, st), "store pack transposed");
+    CK(launch_store_ybits(c->y, n, c->ywords, c->ybits, st), "store y bits");
     return read_error_word(c);
 }
 
@@ -597,6 +600,7 @@ void destroy(spa_ctx* c)
     free_runbufs(c->rb);
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
+    dfree(c->ybits);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -663,6 +667,8 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     c->n_r = round_up(n, 64);
     CA(GT, p * c->n_r);
     CA(yv, n);
+    c->ywords = round_up(n, 256) / 32;
+    CA(ybits, c->ywords);
     CA(d_err, 1);
 #undef CA
     if (e != cudaSuccess) {
@@ -884,19 +890,19 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
     CK(cudaMemcpyAsync(w.beta, B, sizeof(float) * (size_t)(N * p), B_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        st),
        "copy B");
-    CK(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s,
-                         c->mean_f, c->v, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st),
+    CK(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
+                         c->mean_f, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st),
        "pack");
     if (tc) {
         const TcPlan plan = tc_plan(c->n, (int)p, w.N_pad, c->num_sms);
-        CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, st), "loglik tc");
+        CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st), "loglik tc");
     } else {
-        CK(launch_loglik_simt(w.beta_p, c->Xf, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
+        CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
     }
     AcceptArgs a = accept_args(c, nullptr);
     a.ll = ll_dev ? ll : w.ll;
     a.lp = nullptr;
-    CK(launch_accept(a, N, (int)p, 0, 0, 0u, nullptr, c->d_err, st), "finish loglik");
+    CK(launch_accept(a, N, (int)p, c->pr, c->unit_c, 0, 0, 0u, nullptr, c->d_err, st), "finish loglik");
     if (!ll_dev) CK(cudaMemcpyAsync(ll, w.ll, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st), "copy ll");
     if (st != c->stream()) CK(cudaStreamSynchronize(st), "sync");
     return read_error_word(c);
@@ -911,9 +917,10 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
     for (int32_t k = 0; k < reps; ++k) {
         if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
             const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
-            CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, w.partial, w.N_pad, c->d_err, st), "loglik tc");
+            CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+               "loglik tc");
         } else {
-            CK(launch_loglik_simt(w.beta_p, c->Xf, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");
+            CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");
         }
     }
     return SPA_OK;
@@ -954,13 +961,13 @@ static int grad_impl(spa_ctx* c, const float* B, bool dev, int64_t N, double cs,
         Enq q;
         q.c = c;
         q.st = st;
-        q.ck(launch_propose_rw(w.beta, w.beta_p, w.A, 2 * c->Kp, c->Kp, w.lin_p, w.lp_p, w.scale, c->l2e_s, c->mean_f,
-                               c->v, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st));
+        q.ck(launch_propose_rw(w.beta, w.beta_p, w.A, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s, c->mean_f, N,
+                               (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st));
         enq_grad_tc(q, dev ? grad : w.grad, w.beta, cs, N);
         AcceptArgs a = accept_args(c, nullptr);
         a.ll = (dev && ll) ? ll : w.ll;
         a.lp = nullptr;
-        q.ck(launch_accept(a, N, (int)p, 0, 0, 0u, nullptr, c->d_err, st));
+        q.ck(launch_accept(a, N, (int)p, c->pr, c->unit_c, 0, 0, 0u, nullptr, c->d_err, st));
         if (q.e != cudaSuccess) return cuda_fail(c, q.e, "gradient (tensor cores)");
         if (!dev) {
             CK(cudaMemcpyAsync(grad, w.grad, sizeof(float) * (size_t)(N * p), cudaMemcpyDeviceToHost, st), "copy grad");
@@ -1100,15 +1107,22 @@ int spa_lse_ess(const double* logw, int64_t N, double* lse, double* ess)
     Scratch s;
     double* dL = s.get<double>(N);
     double* dW = s.get<double>(N);
+    float* dWf = s.get<float>(N);
+    uint32_t* dFix = s.get<uint32_t>(N);
+    double* dS = s.get<double>(LSE_SCRATCH);
+    unsigned int* dC = s.get<unsigned int>(1);
     double* dOut = s.get<double>(2);
     uint8_t* dR = s.get<uint8_t>(1);
     int* dF = s.get<int>(1);
     uint32_t* dE = s.get<uint32_t>(1);
-    if (!dL || !dW || !dOut || !dR || !dF || !dE) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    if (!dL || !dW || !dWf || !dFix || !dS || !dC || !dOut || !dR || !dF || !dE)
+        return fail(nullptr, SPA_ENOMEM, "device allocation");
     cudaStream_t st = cudaStreamPerThread;
+    const WeightArrays wa{dL, dW, dWf, dFix};
     cudaError_t e = cudaMemcpyAsync(dL, logw, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dE, 0, sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = launch_lse_ess(dL, dW, N, 0, 0, 0.0, dOut + 1, dOut, dR, dF, dE, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dC, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = launch_lse_ess(wa, N, dS, dC, 0, 0, 0.0, dOut + 1, dOut, dR, dF, dE, st);
     double h[2] = {0.0, 0.0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, dOut, sizeof(h), cudaMemcpyDeviceToHost, st);
     int rc = finish_free(e, "lse/ess");
@@ -1134,14 +1148,17 @@ int spa_summaries(const float* B, const double* W, int64_t N, int64_t p, const d
     Scratch s;
     float* dB = s.get<float>(N * p);
     double* dW = s.get<double>(N);
+    float* dWf = s.get<float>(N);
+    uint32_t* dFix = s.get<uint32_t>(N);
     double* dM = s.get<double>(p);
     double* dQ = s.get<double>(p * (nq ? nq : 1));
     double* dC = s.get<double>(p * (nd ? nd : 1));
-    if (!dB || !dW || !dM || !dQ || !dC) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    if (!dB || !dW || !dWf || !dFix || !dM || !dQ || !dC) return fail(nullptr, SPA_ENOMEM, "device allocation");
     cudaStream_t st = cudaStreamPerThread;
     cudaError_t e = cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(N * p), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dW, W, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_summaries(dB, dW, N, (int)p, sa, 0, dM, nq ? dQ : nullptr, dC, st);
+    if (e == cudaSuccess) e = launch_weight_forms(dW, N, dWf, dFix, st);
+    if (e == cudaSuccess) e = launch_summaries(dB, dWf, dFix, N, (int)p, sa, 0, dM, nq ? dQ : nullptr, dC, st);
     if (e == cudaSuccess && mean) e = cudaMemcpyAsync(mean, dM, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && quant && nq)
         e = cudaMemcpyAsync(quant, dQ, sizeof(double) * (size_t)(p * nq), cudaMemcpyDeviceToHost, st);

@@ -80,6 +80,40 @@ __device__ __forceinline__ float prior_draw(uint64_t seed, uint32_t particle, ui
     return (us >> 31) ? -mag : mag;
 }
 
+// ------------------------------------------------- compensated FP32 summation
+// A float pair (s, c) whose value is s + c. Each addition uses the error-free TwoSum
+// transformation (Knuth; Moller), so a sum of k terms carries an error of about
+// 2^-24 |sum| + k 2^-48 sum|x|: double-like accuracy at FP32 cost. On GB300 the
+// CUDA-core FP64 rate is a small fraction of FP32, so per-element sums use this.
+struct FSum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x;
+        const float z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ void add(FSum o)
+    {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ FSum warp_sum(FSum v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FSum w;
+        w.s = __shfl_xor_sync(0xffffffffu, v.s, o);
+        w.c = __shfl_xor_sync(0xffffffffu, v.c, o);
+        v.add(w);
+    }
+    return v;
+}
+
 // ---------------------------------------------------------- reductions / helpers
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
@@ -244,6 +278,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Asynchronous form: issue the load into r, then tmem_wait_ld(r) before reading r. The
+// wait names r as in/out operands so the compiler cannot move reads of r above it.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
 }
 
 // ------------------------------------------------------------ fast base-2 math
