@@ -75,13 +75,15 @@ def test_same_seed_first_step_agrees(spa):
     assert np.max(np.abs(g["mean"][0] - o["mean"][0])) < 5e-3
 
 
-@pytest.mark.parametrize("p,a,direction,move", [(1, 1.0, "s2d", "rw"), (2, 4.0, "d2s", "rw"), (1, math.inf, "d2s", "rw"),
-                                                (2, 2.0, "d2s", "mala")])
-def test_sweep_matches_quadrature(spa, p, a, direction, move):
+# (p, a, direction, move, sparse end log c). Where the posterior turns bimodal (p = 2) the
+# SMC estimate itself is biased at this budget beyond some scale -- the oracle shows the
+# same bias with 32 seeds -- so the quadrature pin stops there (MALA's drift is poor at the
+# prior's cusp: log c = -5; 4 random-walk moves at a = 4: -4.5), and the full path is
+# compared with the oracle instead (test_sparse_end_matches_oracle).
+@pytest.mark.parametrize("p,a,direction,move,lo", [(1, 1.0, "s2d", "rw", -6.0), (2, 4.0, "d2s", "rw", -4.5),
+                                                   (1, math.inf, "d2s", "rw", -6.0), (2, 2.0, "d2s", "mala", -5.0)])
+def test_sweep_matches_quadrature(spa, p, a, direction, move, lo):
     reg = synth.make_region(200, p, 0.9, (0.6,) * p, seed=2024 + p)
-    # MALA's drift is poor at the prior's cusp: below log c = -5 this bimodal case is at the
-    # edge of what 8 seeds can resolve even for the oracle, so its path stops there
-    lo = -5.0 if move == "mala" else -6.0
     sched = synth.geometric_schedule(16, lo, 0.0, sparse_to_diffuse=(direction == "s2d"))
     init = "prior_is" if direction == "s2d" else "resample_move"
     cfg = spa.make_config(move=move, init=init, burn_in_steps=25)
@@ -93,6 +95,22 @@ def test_sweep_matches_quadrature(spa, p, a, direction, move):
     _check(_zscores([r["mean"] for r in runs], truth_mean, 2e-4), "mean")
     _check(_zscores(np.stack([r["conc"].transpose(0, 2, 1) for r in runs]), truth_conc, 2e-3), "conc")
     _check(_zscores(np.stack([np.cumsum(r["log_z_inc"]) for r in runs]), truth_logz, 2e-3), "log Z")
+
+
+@pytest.mark.parametrize("move", ["rw", "mala"])
+def test_sparse_end_matches_oracle(spa, move):
+    """The bimodal p = 2 path down to log c = -6, where the algorithm's own estimate drifts
+    from quadrature: the GPU sweep must drift like the oracle's (two-sample, R seeds each)."""
+    reg = synth.make_region(200, 2, 0.9, (0.6, 0.6), seed=2026)
+    sched = synth.geometric_schedule(16, -6.0, 0.0, sparse_to_diffuse=False)
+    a = 4.0 if move == "rw" else 2.0
+    cfg = spa.make_config(move=move, init="resample_move", burn_in_steps=25)
+    g = _gpu_runs(spa, reg, a, sched, 2048, 4, cfg, list(range(100, 100 + R)))
+    ocfg = oracle.make_config(move=move, init="mcmc", burn_in_steps=25)
+    o = [oracle.run(reg.G, reg.y, a, sched, 2048, 4, seed=500 + s, cfg=ocfg) for s in range(R)]
+    _check(_two_sample_z([r["mean"] for r in g], [r["mean"] for r in o], 2e-4), "mean")
+    _check(_two_sample_z([np.cumsum(r["log_z_inc"]) for r in g], [np.cumsum(r["log_z_inc"]) for r in o], 2e-3),
+           "log Z")
 
 
 def test_sweep_is_deterministic_and_graph_reuse(spa):
