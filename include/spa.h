@@ -141,8 +141,8 @@ int spa_run_device(spa_ctx* ctx, const double* scale_schedule_device, int64_t T,
 /* Wait for work enqueued on the context's stream and report device-side errors. */
 int spa_sync(spa_ctx* ctx);
 
-/* Batched sweeps over R independent regions (each context its own data, nu and
- * config), all enqueued before any is waited for. */
+/* Batched sweeps over R independent regions (Section 5 runs the sweep per region; each
+ * context keeps its own data, nu and config). */
 typedef struct spa_batch_args {
     const double* const* schedules;  /* R host pointers, schedule of region r      */
     const int64_t* T;                /* [R] schedule lengths                        */
@@ -150,10 +150,40 @@ typedef struct spa_batch_args {
     const int32_t* moves_per_step;   /* [R]                                         */
     const uint64_t* seeds;           /* [R]                                         */
 } spa_batch_args;
+/* One-shot batch: spa_batch_create + spa_batch_run + spa_batch_destroy. outs: R results
+ * (or NULL). */
 int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_result* outs);
+
+/* A reusable batch: the R sweeps are captured into ONE CUDA graph whose R branches (one
+ * per context, on the context's stream) run concurrently on the GPU, and every
+ * spa_batch_run is a single graph launch on the batch's own stream. Each region's
+ * likelihood tile shape comes from the library's tuner (timed once per shape).
+ * Contexts must be distinct and outlive the batch; their schedules (args->schedules,
+ * copied here), T, N and moves_per_step are fixed at creation. Results are bit-identical
+ * to spa_run of each context with the same seed.
+ * Errors: SPA_EINVAL (NULL or repeated contexts, bad sizes or schedule values),
+ * SPA_ENOMEM, SPA_ECUDA; the message is spa_last_error(NULL). */
+typedef struct spa_batch spa_batch;
+int spa_batch_create(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_batch** out);
+/* Run all R sweeps once. seeds: R seeds, or NULL for the seeds given at creation.
+ * outs: R caller-allocated results (fields may be NULL), or NULL. Blocks until done.
+ * SPA_EINVAL if a context's workspace, run buffers or config changed since creation
+ * (spa_run with other shapes, spa_set_config, spa_loglik with another N); a device error
+ * of region r is reported as that region's code, with spa_last_error(ctxs[r]). */
+int spa_batch_run(spa_batch* batch, const uint64_t* seeds, spa_result* outs);
+/* Kernel launches in one spa_batch_run (all regions). */
+int64_t spa_batch_launch_count(const spa_batch* batch);
+void spa_batch_destroy(spa_batch* batch);
 
 /* Number of kernels the last spa_run / spa_run_device of this context launched. */
 int64_t spa_last_launch_count(const spa_ctx* ctx);
+
+/* Individuals per n-tile (128 or 256) of the tensor-core likelihood kernel for the
+ * context's current workspace, or 0 before the first run. The library times both widths
+ * once per shape (device, N, n, p) and keeps the faster; the environment variable
+ * SPA_LOGLIK_BN=128|256, read when a workspace is created, fixes it instead. The width
+ * does not change any result (partial sums are per 32 individuals either way). */
+int spa_loglik_tile_width(const spa_ctx* ctx);
 
 /* Enqueue `reps` launches of the context's likelihood kernel (split-BF16 tcgen05 or
  * FP32 SIMT, per the configuration) on `stream` over the particles last packed for

@@ -77,7 +77,12 @@ _SIGS = {
                                  C.POINTER(Result)]),
     "spa_sync": (C.c_int, [C.c_void_p]),
     "spa_run_batch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(BatchArgs), C.c_void_p]),
+    "spa_batch_create": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(BatchArgs), C.POINTER(C.c_void_p)]),
+    "spa_batch_run": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "spa_batch_launch_count": (C.c_int64, [C.c_void_p]),
+    "spa_batch_destroy": (None, [C.c_void_p]),
     "spa_last_launch_count": (C.c_int64, [C.c_void_p]),
+    "spa_loglik_tile_width": (C.c_int, [C.c_void_p]),
     "spa_loglik_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "spa_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_loglik_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -241,6 +246,10 @@ class Region:
     def last_launch_count(self) -> int:
         return int(load().spa_last_launch_count(self._h))
 
+    def loglik_tile_width(self) -> int:
+        """n-tile width of the tensor-core likelihood kernel (0 before the first run)."""
+        return int(load().spa_loglik_tile_width(self._h))
+
     def loglik_repeat(self, N: int, reps: int, stream: int = 0):
         _check(load().spa_loglik_repeat(self._h, int(N), int(reps), stream or None), self._h)
 
@@ -288,22 +297,67 @@ def _result_struct(out: dict) -> Result:
     return r
 
 
-def run_batch(regions, schedules, N, moves_per_step, seeds) -> list:
-    """spa_run_batch over several Regions; returns one output dict per region."""
+def _batch_args(regions, schedules, N, moves_per_step, seeds):
     R = len(regions)
     handles = (C.c_void_p * R)(*[r.handle.value for r in regions])
     scheds = [np.ascontiguousarray(s, dtype=np.float64) for s in schedules]
     sp = (C.c_void_p * R)(*[s.ctypes.data for s in scheds])
-    T = np.array([s.size for s in scheds], np.int64)
-    Ns = np.array(N, np.int64)
-    Ms = np.array(moves_per_step, np.int32)
-    Ss = np.array(seeds, np.uint64)
-    args = BatchArgs(C.cast(sp, C.c_void_p), _ptr(T), _ptr(Ns), _ptr(Ms), _ptr(Ss))
+    keep = dict(handles=handles, scheds=scheds, sp=sp, T=np.array([s.size for s in scheds], np.int64),
+                N=np.array(N, np.int64), M=np.array(moves_per_step, np.int32), S=np.array(seeds, np.uint64))
+    args = BatchArgs(C.cast(sp, C.c_void_p), _ptr(keep["T"]), _ptr(keep["N"]), _ptr(keep["M"]), _ptr(keep["S"]))
+    return args, keep
+
+
+def _batch_outputs(regions, T):
     outs = [_alloc_result(T[r], regions[r].p, regions[r].config().n_quantiles, regions[r].config().n_deltas)
-            for r in range(R)]
-    structs = (Result * R)(*[_result_struct(o) for o in outs])
-    _check(load().spa_run_batch(handles, R, C.byref(args), C.cast(structs, C.c_void_p)))
+            for r in range(len(regions))]
+    structs = (Result * len(regions))(*[_result_struct(o) for o in outs])
+    return outs, structs
+
+
+def run_batch(regions, schedules, N, moves_per_step, seeds) -> list:
+    """spa_run_batch over several Regions; returns one output dict per region."""
+    args, keep = _batch_args(regions, schedules, N, moves_per_step, seeds)
+    outs, structs = _batch_outputs(regions, keep["T"])
+    _check(load().spa_run_batch(keep["handles"], len(regions), C.byref(args), C.cast(structs, C.c_void_p)))
     return outs
+
+
+class Batch:
+    """spa_batch: the sweeps of several Regions captured into one CUDA graph (one branch
+    per region, run concurrently), launched once per run()."""
+
+    def __init__(self, regions, schedules, N, moves_per_step, seeds):
+        self.regions = list(regions)
+        args, keep = _batch_args(self.regions, schedules, N, moves_per_step, seeds)
+        self._T = keep["T"]
+        h = C.c_void_p()
+        _check(load().spa_batch_create(keep["handles"], len(self.regions), C.byref(args), C.byref(h)))
+        self.handle = h
+
+    def run(self, seeds=None) -> list:
+        outs, structs = _batch_outputs(self.regions, self._T)
+        sp = None
+        if seeds is not None:
+            sarr = np.ascontiguousarray(seeds, dtype=np.uint64)
+            assert sarr.size == len(self.regions)
+            sp = _ptr(sarr)
+        _check(load().spa_batch_run(self.handle, sp, C.cast(structs, C.c_void_p)))
+        return outs
+
+    def launch_count(self) -> int:
+        return int(load().spa_batch_launch_count(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().spa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------ context-free calls

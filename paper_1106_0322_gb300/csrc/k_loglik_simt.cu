@@ -1,8 +1,10 @@
 // k_loglik_simt.cu -- the plain FP32 path: the same log-likelihood on CUDA cores (FFMA).
 //
 // eta = X beta with the standardised FP32 X (Section 3) and FP32 accumulation, then
-// y eta - softplus(eta), softplus(eta) = max(eta, 0) + log1p(exp(-|eta|)) with the accurate
-// FP32 functions, summed per particle over each 64-individual tile. This is the comparator the split-BF16
+// softplus(eta) = max(eta, 0) + log1p(exp(-|eta|)) with the accurate FP32 functions, summed
+// per particle over each 64-individual tile (the linear half sum_i y_i eta_i = beta . X^T y
+// is a p-length dot product the move kernels form). The gradient path (mode 1) keeps the
+// full y eta - softplus(eta) per tile for its log-likelihood output. This is the comparator the split-BF16
 // tensor-core path is measured against; it is also the gradient (adjoint) kernel pair
 // behind spa_grad: grad l = X^T (y - logit^{-1}(eta)).
 #include "spa_device.cuh"
@@ -19,7 +21,8 @@ constexpr int TK = 16;  // k-chunk
 __device__ __forceinline__ float softplus_acc(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
 
 // 256 threads = 16 x 16; thread (ty, tx) owns particles ty*4..+3 and individuals tx*4..+3.
-// partial = sum over the tile of y eta - softplus(eta); mode 1 also stores eta to eta_out [N][n].
+// mode 0: partial = -sum over the tile of softplus(eta); mode 1: partial = sum over the tile
+// of y eta - softplus(eta), and eta stored to eta_out [N][n].
 template <int MODE>
 __global__ void __launch_bounds__(256) k_eta_tile(const float* __restrict__ B, const float* __restrict__ Xf,
                                                   const uint8_t* __restrict__ y, int64_t N, int64_t n, int p,
@@ -70,7 +73,7 @@ __global__ void __launch_bounds__(256) k_eta_tile(const float* __restrict__ B, c
             if (gr < n) {
                 const float e = acc[x][z];
                 if (MODE == 0) {
-                    s += (y[gr] ? e : 0.0f) - softplus_acc(e);
+                    s -= softplus_acc(e);
                 } else {
                     s += (y[gr] ? e : 0.0f) - softplus_acc(e);
                     if (gi < N) eta_out[gi * n + gr] = e;

@@ -1,24 +1,26 @@
 // k_loglik_tc.cu -- the particle log-likelihood on the 5th-generation tensor cores.
 //
 // Section 2's log-likelihood of particle k is l_k = sum_i [y_i eta_ki - softplus(eta_ki)],
-// eta = X beta_k. This kernel computes it for N particles at once as a contraction
-// followed by a row reduction that never leaves the chip:
+// eta = X beta_k. Its first half is linear in beta: sum_i y_i eta_ki = beta_k . (X^T y), a
+// p-length dot product that the move kernels form per particle. This kernel computes the
+// n-length second half for N particles at once as a contraction followed by a row
+// reduction that never leaves the chip:
 //
-//   eta2[k, i] = sum_j A[k, j] * Gb[i, j]      (tcgen05.mma, BF16 x BF16 -> FP32 in TMEM)
-//   partial[k] += sum_i y_i eta2 - log2(1 + 2^eta2[k, i])  (epilogue warps, ex2/lg2 on the SFU)
+//   eta2[k, i] = sum_j A[k, j] * Gb[i, j]       (tcgen05.mma, BF16 x BF16 -> FP32 in TMEM)
+//   partial[c][k] = -sum_{i in chunk c} log2(1 + 2^eta2[k, i])   (epilogue warps, ex2/lg2)
 //
 // with A[k] = [hi(bt_k) | lo(bt_k)] the split-BF16 copy of bt_kj = beta_kj log2(e)/s_j
 // (plus the offset -sum_j m_j bt_kj in the ones column), and Gb = [G, 1] the exact BF16
 // genotypes. Both halves of A multiply the same G tile, so each pipeline stage carries
-// A_hi, A_lo and G for one 64-wide k-block; eta2 = eta log2(e), so l = ln(2) * sum of
-// [y eta2 - log2(1 + 2^eta2)]. y is read as a bitmask, one 32-bit word per 32 individuals.
+// A_hi, A_lo and G for one 64-wide k-block; eta2 = eta log2(e), so the softplus half of l
+// is ln(2) * sum_c partial[c]. One partial per 32-individual chunk c: the chunk sums do not
+// depend on the tile shape, so the result is the same for every BN the tuner picks.
 //
 // Tile: 128 particles (M, TMEM lanes) x BN individuals (N, TMEM columns). A persistent
-// grid walks the (particle-tile, individual-tile) units in order; each unit's row sums go
-// to their own slot of `partial`, so the final sum (in the accept kernel) has a fixed
-// order. Warp roles: warp 0 issues TMA loads, warp 1 (one thread) issues the MMAs and owns
-// TMEM, warps 2..9 drain the double-buffered accumulator (warp w reads TMEM lanes
-// 32 (w % 4) .. +31, half (w - 2) / 4 of the columns). Every wait is bounded.
+// grid walks the (particle-tile, individual-tile) units in order. Warp roles: warp 0
+// issues TMA loads, warp 1 (one thread) issues the MMAs and owns TMEM, the epilogue warps
+// drain the double-buffered accumulator (warp w reads TMEM lanes 32 (w % 4) .. +31 and
+// one of EPI/4 column groups). Every wait is bounded.
 #include "spa_device.cuh"
 #include "spa_internal.h"
 
@@ -28,17 +30,31 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // BF16 per 128-byte swizzle row
-constexpr int EPI_WARPS = 8;
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+// epilogue warps: 16 for the log-likelihood (4 per TMEM lane quadrant, to hide the SFU and
+// TMEM latencies), 8 for the residual variant, whose per-chunk state is larger
+template <bool RESID>
+struct Epi {
+    static constexpr int WARPS = RESID ? 8 : 16;
+    static constexpr int THREADS = 64 + 32 * WARPS;
+    static constexpr int GROUPS = WARPS / 4;  // column groups per tile
+};
 constexpr int ADJ_BN_SMALL = 208;  // p + padding <= 208 covers the p = 200 workloads in one N tile
 
-template <int BN, int STAGES>
+// Shared-memory plan. Streaming (AR = false): every stage carries A_hi, A_lo and the G tile
+// of one k-block. A-resident (AR = true, K <= 256): the particle tile's A_hi | A_lo for all
+// k-blocks stays in shared memory while the CTA walks consecutive n-tiles of the same
+// particle tile, and the stages carry only G, halving what each SM pulls from L2.
+constexpr int KB_RES = 4;  // k-blocks of a resident A (Kp <= 256)
+
+template <int BN, int STAGES, bool AR = false>
 struct TcCfg {
     static constexpr int A_TILE = BM * BK * 2;
     static constexpr int B_TILE = BN * BK * 2;
-    static constexpr int STAGE = 2 * A_TILE + B_TILE;
-    static constexpr int BAR_OFF = STAGES * STAGE;
-    static constexpr int NBARS = 2 * STAGES + 5;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
+    static constexpr int A_RES = AR ? KB_RES * 2 * A_TILE : 0;
+    static constexpr int STAGE = AR ? B_TILE : 2 * A_TILE + B_TILE;
+    static constexpr int BAR_OFF = A_RES + STAGES * STAGE;
+    // full[S], empty[S], acc_full[2], acc_empty[2], drain, a_full, a_empty
+    static constexpr int NBARS = 2 * STAGES + 7;
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
     static constexpr int BYTES = SLOT_OFF + 16;
     static constexpr int SMEM = BYTES + 1024;  // slack for the 1024-byte alignment of the tiles
@@ -48,17 +64,16 @@ struct TcCfg {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
 };
 
-// Sum over 32 columns of the base-2 log-likelihood terms y eta2 - log2(1 + 2^eta2); bit k of
-// ybits is y of column k.
-__device__ __forceinline__ float sum_ll2_32(const float (&v)[32], int valid, uint32_t ybits)
+// Sum over the first `valid` of 32 columns of softplus2(eta2) = log2(1 + 2^eta2).
+__device__ __forceinline__ float sum_sp2_32(const uint32_t (&r)[32], int valid)
 {
     float t[32];
     if (valid >= 32) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) t[k] = (((ybits >> k) & 1u) ? v[k] : 0.0f) - softplus2(v[k]);
+        for (int k = 0; k < 32; ++k) t[k] = softplus2(__uint_as_float(r[k]));
     } else {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) t[k] = (k < valid) ? (((ybits >> k) & 1u) ? v[k] : 0.0f) - softplus2(v[k]) : 0.0f;
+        for (int k = 0; k < 32; ++k) t[k] = (k < valid) ? softplus2(__uint_as_float(r[k])) : 0.0f;
     }
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1)
@@ -74,8 +89,8 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// Residual mode: besides the log-likelihood sum, r = y - logit^{-1}(eta) for the 32 columns
-// of this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into *rsum.
+// Residual mode: besides the softplus sum, r = y - logit^{-1}(eta) for the 32 columns of
+// this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into rsum.
 // eta2 = eta log2(e): with e = 2^-|eta2|, softplus2 = max(eta2, 0) + log2(1 + e) and
 // logit^{-1}(eta) = 1/(1 + e) for eta >= 0, e/(1 + e) otherwise (one ex2 shared).
 __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, uint32_t ybits,
@@ -94,7 +109,7 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
         const float sig = (x >= 0.0f) ? inv : e * inv;
         const bool ok = k < valid;
         const bool yk = (ybits >> k) & 1u;
-        sp[k] = ok ? (yk ? x : 0.0f) - (fmaxf(x, 0.0f) + lg2_approx(onepe)) : 0.0f;
+        sp[k] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
         const float r = ok ? (yk ? 1.0f : 0.0f) - sig : 0.0f;
         rs[k] = r;
         split_bf16(r, hi[k], lo[k]);
@@ -116,24 +131,27 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
             sp[k] += sp[k + w];
             rs[k] += rs[k + w];
         }
-    rsum += rs[0];
+    rsum = rs[0];
     return sp[0];
 }
 
-template <int BN, int STAGES, bool RESID>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int BN, int STAGES, bool RESID, bool AR>
+__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n_tiles,
                 int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial, int64_t N_pad,
                 uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
                 int64_t n_r, float* __restrict__ rsum_part)
 {
-    using C = TcCfg<BN, STAGES>;
+    using C = TcCfg<BN, STAGES, AR>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
+    const uint32_t stage0 = sbase + C::A_RES;  // first pipeline stage
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = sbase + C::BAR_OFF;
     const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
+    const uint32_t afull_bar = bar0 + 8 * (2 * STAGES + 5);
+    const uint32_t aempty_bar = bar0 + 8 * (2 * STAGES + 6);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
 #define FULL_BAR(s) (bar0 + 8u * (uint32_t)(s))
 #define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
@@ -151,9 +169,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(ACCF_BAR(b), 1);
-            mbar_init(ACCE_BAR(b), EPI_WARPS);
+            mbar_init(ACCE_BAR(b), Epi<RESID>::WARPS);
         }
         mbar_init(drain_bar, 1);
+        mbar_init(afull_bar, 1);
+        mbar_init(aempty_bar, 1);
         mbar_fence_init();
     }
     if (warp == 0 && lane == 0) {
@@ -174,28 +194,50 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            int epoch = -1, cur_mt = -1;  // A-resident: one epoch per run of units with the same m-tile
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
                 const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+                if (AR && mt != cur_mt) {
+                    ++epoch;
+                    // the previous epoch's MMAs must be done with the resident A
+                    if (epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((epoch - 1) & 1), err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(afull_bar, (uint32_t)(kblocks * 2 * C::A_TILE));
+                    for (int kb = 0; kb < kblocks; ++kb) {
+                        const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
+                        tma_load_2d(a, &mapA, afull_bar, kb * BK, mt * BM);
+                        tma_load_2d(a + C::A_TILE, &mapA, afull_bar, Kp + kb * BK, mt * BM);
+                    }
+                    cur_mt = mt;
+                }
                 for (int kb = 0; kb < kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
                     if (!mbar_wait_bounded(EMPTY_BAR(s), ph ^ 1u, err)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t st = sbase + s * C::STAGE;
+                    const uint32_t st = stage0 + s * C::STAGE;
                     mbar_arrive_expect_tx(FULL_BAR(s), (uint32_t)C::STAGE);
-                    tma_load_2d(st, &mapA, FULL_BAR(s), kb * BK, mt * BM);
-                    tma_load_2d(st + C::A_TILE, &mapA, FULL_BAR(s), Kp + kb * BK, mt * BM);
-                    tma_load_2d(st + 2 * C::A_TILE, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                    if (AR) {
+                        tma_load_2d(st, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                    } else {
+                        tma_load_2d(st, &mapA, FULL_BAR(s), kb * BK, mt * BM);
+                        tma_load_2d(st + C::A_TILE, &mapA, FULL_BAR(s), Kp + kb * BK, mt * BM);
+                        tma_load_2d(st + 2 * C::A_TILE, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                    }
                     ++it;
                 }
             }
-            // Never leave with a copy in flight: the most recent use of each stage must have landed.
+            // Never leave with a copy in flight: the most recent use of each stage must have landed,
+            // and so must the last resident A.
             const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
             for (uint32_t k = 1; k <= last; ++k) {
                 const uint32_t i2 = it - k;
                 mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
             }
+            if (AR && epoch >= 0) mbar_wait_bounded(afull_bar, (uint32_t)(epoch & 1), err, 100000000ull);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
@@ -204,11 +246,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t it = 0;
             int lt = 0;
             bool ok = true;
+            int epoch = -1, cur_mt = -1;
             for (int64_t u = u_begin; u < u_end && ok; ++u, ++lt) {
+                const int mt = (int)(u / n_tiles);
                 const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
                 if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err)) {
                     ok = false;
                     break;
+                }
+                if (AR && mt != cur_mt) {
+                    ++epoch;
+                    if (!mbar_wait_bounded(afull_bar, (uint32_t)(epoch & 1), err)) {
+                        ok = false;
+                        break;
+                    }
+                    cur_mt = mt;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
@@ -219,10 +271,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = sbase + s * C::STAGE;
-                    const uint64_t ahi = sdesc_sw128(st);
-                    const uint64_t alo = sdesc_sw128(st + C::A_TILE);
-                    const uint64_t bg = sdesc_sw128(st + 2 * C::A_TILE);
+                    const uint32_t st = stage0 + s * C::STAGE;
+                    const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
+                    const uint64_t ahi = sdesc_sw128(a);
+                    const uint64_t alo = sdesc_sw128(a + C::A_TILE);
+                    const uint64_t bg = sdesc_sw128(AR ? st : st + 2 * C::A_TILE);
                     const int nks = (ksteps - 4 * kb) < 4 ? (ksteps - 4 * kb) : 4;
                     for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
                         umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
@@ -232,6 +285,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (!ok) break;
                 umma_commit(ACCF_BAR(b));
+                // the resident A is free once this unit's MMAs are done, if the next unit
+                // belongs to another particle tile
+                if (AR && u + 1 < u_end && (int)((u + 1) / n_tiles) != mt) umma_commit(aempty_bar);
             }
             // Wait for every MMA this thread issued before TMEM can be released.
             umma_commit(drain_bar);
@@ -239,53 +295,59 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
     } else {
         // --------------------------------------------------------------- epilogue
-        const int quad = warp & 3;         // TMEM lane quadrant this warp may access
-        const int half = (warp - 2) >> 2;  // which half of the BN columns
+        using E = Epi<RESID>;
+        constexpr int CPW = BN / 32 / E::GROUPS;  // 32-column chunks per warp and tile
+        const int quad = warp & 3;                // TMEM lane quadrant this warp may access
+        const int grp = (warp - 2) >> 2;          // column group
         const int row = quad * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
+        const int col0 = grp * CPW * 32;
         int lt = 0;
         for (int64_t u = u_begin; u < u_end; ++u, ++lt) {
             const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
             const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
             if (!mbar_wait_bounded(ACCF_BAR(b), aph, err)) break;
             tc_fence_after();
-            const int col0 = half * (BN / 2);
-            const int valid = n - nt * BN - col0;
-            float acc = 0.0f, rsum = 0.0f;
-            // software pipeline over the 32-column chunks: the TMEM load of chunk k+1 is in
-            // flight while chunk k is reduced
-            constexpr int NCH = (BN / 2) / 32;
+            const int valid0 = n - nt * BN - col0;  // valid columns from col0 on
             const uint32_t tbase = tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)col0;
-            uint32_t ra[32], rb[32];
-            if (valid > 0) {
-                tmem_ld32_async(tbase, ra);
-                tmem_wait_ld(ra);
-            }
+            const int64_t prow = (int64_t)mt * BM + row;
+            const int64_t gc0 = ((int64_t)nt * BN + col0) >> 5;  // global index of the first chunk
+            if (!RESID) {
+                // all of this warp's chunks in flight at once, then the buffer goes back to the MMA
+                uint32_t r[CPW][32];
 #pragma unroll
-            for (int ch = 0; ch < NCH; ++ch) {
-                const int c = ch * 32;
-                if (valid - c <= 0) break;
-                uint32_t(&cur)[32] = (ch & 1) ? rb : ra;
-                uint32_t(&nxt)[32] = (ch & 1) ? ra : rb;
-                const bool more = (ch + 1 < NCH) && (valid - c - 32 > 0);
-                if (more) tmem_ld32_async(tbase + (uint32_t)(c + 32), nxt);
-                float v[32];
+                for (int ch = 0; ch < CPW; ++ch) tmem_ld32_async(tbase + (uint32_t)(32 * ch), r[ch]);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(cur[k]);
-                const int64_t i0 = (int64_t)nt * BN + col0 + c;
-                const uint32_t yb = __ldg(ybits + (i0 >> 5));
-                if (RESID) {
-                    acc += resid_chunk(v, valid - c, yb, R + ((int64_t)mt * BM + row) * 2 * n_r + i0, n_r, rsum);
-                } else {
-                    acc += sum_ll2_32(v, valid - c, yb);
+                for (int ch = 0; ch < CPW; ++ch) tmem_wait_ld(r[ch]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACCE_BAR(b));
+#pragma unroll
+                for (int ch = 0; ch < CPW; ++ch) {
+                    const int valid = valid0 - 32 * ch;
+                    if (valid <= 0) break;
+                    partial[(gc0 + ch) * N_pad + prow] = -sum_sp2_32(r[ch], valid);
                 }
-                if (more) tmem_wait_ld(nxt);
+            } else {
+                for (int ch = 0; ch < CPW; ++ch) {
+                    const int valid = valid0 - 32 * ch;
+                    if (valid <= 0) break;
+                    uint32_t r[32];
+                    tmem_ld32_async(tbase + (uint32_t)(32 * ch), r);
+                    tmem_wait_ld(r);
+                    float v[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+                    const int64_t i0 = (int64_t)nt * BN + col0 + 32 * ch;
+                    float rs;
+                    const float sp = resid_chunk(v, valid, __ldg(ybits + (i0 >> 5)), R + prow * 2 * n_r + i0, n_r, rs);
+                    partial[(gc0 + ch) * N_pad + prow] = -sp;
+                    rsum_part[(gc0 + ch) * N_pad + prow] = rs;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(ACCE_BAR(b));
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(ACCE_BAR(b));
-            partial[((int64_t)nt * 2 + half) * N_pad + (int64_t)mt * BM + row] = acc;
-            if (RESID) rsum_part[((int64_t)nt * 2 + half) * N_pad + (int64_t)mt * BM + row] = rsum;
         }
     }
 #undef FULL_BAR
@@ -447,27 +509,31 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 }
 
 // grad l_kj = (sum_s C_s[k, j] - m_j sum_i r_ki) / s_j (+ the prior gradient at scale c > 0).
+// One warp per particle, FP32: the K-split partials and the residual chunk sums are added
+// with compensation, and C - m_j sum r is formed by one fused multiply-add.
 __global__ void k_grad_finish(const float* __restrict__ gpart, int ksplit, const float* __restrict__ rsum_part,
-                              int n_parts, int64_t N_pad, int64_t N, int p, const double* __restrict__ mean,
-                              const double* __restrict__ sd, const float* __restrict__ B, PriorArgs pr, double c,
+                              int n_parts, int64_t N_pad, int64_t N, int p, const float* __restrict__ mean_f,
+                              const float* __restrict__ inv_sd, const float* __restrict__ B, PriorArgs pr, double c,
                               float* __restrict__ grad)
 {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= N) return;
-    double rs = 0.0;
-    for (int q = lane; q < n_parts; q += 32) rs += (double)rsum_part[(int64_t)q * N_pad + k];
-    rs = warp_sum(rs);
+    FSum rq;
+    for (int q = lane; q < n_parts; q += 32) rq.add(rsum_part[(int64_t)q * N_pad + k]);
+    rq = warp_sum(rq);
+    const float rs = rq.value();
+    const float a1 = pr.a + 1.0f, ac = (float)((double)pr.a * c), inv_c = c > 0.0 ? (float)(1.0 / c) : 0.0f;
     for (int j = lane; j < p; j += 32) {
-        double g = 0.0;
-        for (int q = 0; q < ksplit; ++q) g += (double)gpart[((int64_t)q * N_pad + k) * p + j];
-        g = (g - mean[j] * rs) / sd[j];
+        FSum g;
+        for (int q = 0; q < ksplit; ++q) g.add(gpart[((int64_t)q * N_pad + k) * p + j]);
+        float gv = fmaf(-mean_f[j], rs, g.value()) * inv_sd[j];
         if (c > 0.0) {
             const float b = B[k * p + j];
-            const double sg = (b > 0.0f) ? 1.0 : ((b < 0.0f) ? -1.0 : 0.0);
-            g += pr.de ? -sg / c : -((double)pr.a + 1.0) * sg / ((double)pr.a * c + fabs((double)b));
+            const float sg = (b > 0.0f) ? 1.0f : ((b < 0.0f) ? -1.0f : 0.0f);
+            gv += pr.de ? -sg * inv_c : -a1 * sg / (ac + fabsf(b));
         }
-        grad[k * p + j] = (float)g;
+        grad[k * p + j] = gv;
     }
 }
 
@@ -504,13 +570,13 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool RESID>
+template <int BN, int STAGES, bool RESID, bool AR>
 cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
                       cudaStream_t st)
 {
-    using C = TcCfg<BN, STAGES>;
-    k_loglik_tc<BN, STAGES, RESID><<<plan.grid, TC_THREADS, C::SMEM, st>>>(
+    using C = TcCfg<BN, STAGES, AR>;
+    k_loglik_tc<BN, STAGES, RESID, AR><<<plan.grid, Epi<RESID>::THREADS, C::SMEM, st>>>(
         mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits,
         ra ? ra->R : nullptr, ra ? ra->n_r : 0, ra ? ra->rsum_part : nullptr);
     return cudaGetLastError();
@@ -523,27 +589,31 @@ cudaError_t tc_init_attributes()
     cudaError_t e = cudaSuccess;
 #define SET_SMEM(kern, bytes) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-    SET_SMEM((k_loglik_tc<256, 3, false>), (TcCfg<256, 3>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, false>), (TcCfg<128, 4>::SMEM));
-    SET_SMEM((k_loglik_tc<256, 3, true>), (TcCfg<256, 3>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, true>), (TcCfg<128, 4>::SMEM));
+    SET_SMEM((k_loglik_tc<256, 3, false, false>), (TcCfg<256, 3, false>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, false, false>), (TcCfg<128, 4, false>::SMEM));
+    SET_SMEM((k_loglik_tc<256, 3, true, false>), (TcCfg<256, 3, false>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, true, false>), (TcCfg<128, 4, false>::SMEM));
+    SET_SMEM((k_loglik_tc<256, 3, false, true>), (TcCfg<256, 3, true>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, false, true>), (TcCfg<128, 4, true>::SMEM));
+    SET_SMEM((k_loglik_tc<256, 3, true, true>), (TcCfg<256, 3, true>::SMEM));
+    SET_SMEM((k_loglik_tc<128, 4, true, true>), (TcCfg<128, 4, true>::SMEM));
     SET_SMEM((k_adjoint_tc<ADJ_BN_SMALL, 3>), (AdjCfg<ADJ_BN_SMALL, 3>::SMEM));
     SET_SMEM((k_adjoint_tc<256, 3>), (AdjCfg<256, 3>::SMEM));
 #undef SET_SMEM
     return e;
 }
 
-TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms)
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN)
 {
     TcPlan pl;
-    pl.BN = (n <= 128) ? 128 : 256;
+    pl.BN = (BN == 128 || BN == 256) ? BN : ((n <= 128) ? 128 : 256);
     pl.n_tiles = (int)((n + pl.BN - 1) / pl.BN);
     pl.m_tiles = (int)(N_pad / BM);
     pl.ksteps = (p + 1 + 15) / 16;
     pl.kblocks = (pl.ksteps + 3) / 4;
     const int64_t units = (int64_t)pl.m_tiles * pl.n_tiles;
     pl.grid = (int)(units < num_sms ? units : num_sms);
-    pl.n_parts = 2 * pl.n_tiles;
+    pl.n_parts = (int)((n + 31) / 32);
     return pl;
 }
 
@@ -561,12 +631,25 @@ cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, c
                              const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
                              const ResidArgs* ra)
 {
+    // A stays resident when all its k-blocks fit (K <= 256)
+    const bool ar = plan.kblocks <= KB_RES;
+#define TC_CASE(BN_, S_, R_, AR_) \
+    return launch_tc<BN_, S_, R_, AR_>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st)
     if (ra) {
-        if (plan.BN == 256) return launch_tc<256, 3, true>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st);
-        return launch_tc<128, 4, true>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st);
+        if (plan.BN == 256) {
+            if (ar) TC_CASE(256, 3, true, true);
+            TC_CASE(256, 3, true, false);
+        }
+        if (ar) TC_CASE(128, 4, true, true);
+        TC_CASE(128, 4, true, false);
     }
-    if (plan.BN == 256) return launch_tc<256, 3, false>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, nullptr, st);
-    return launch_tc<128, 4, false>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, nullptr, st);
+    if (plan.BN == 256) {
+        if (ar) TC_CASE(256, 3, false, true);
+        TC_CASE(256, 3, false, false);
+    }
+    if (ar) TC_CASE(128, 4, false, true);
+    TC_CASE(128, 4, false, false);
+#undef TC_CASE
 }
 
 AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms)
@@ -612,11 +695,11 @@ cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT,
 }
 
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
-                               int64_t N, int p, const double* mean, const double* sd, const float* B, PriorArgs pr,
+                               int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st)
 {
-    k_grad_finish<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean, sd, B,
-                                                           pr, c, grad);
+    k_grad_finish<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd,
+                                                           B, pr, c, grad);
     return cudaGetLastError();
 }
 

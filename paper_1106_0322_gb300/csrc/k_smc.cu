@@ -1,15 +1,17 @@
 // k_smc.cu -- the per-step kernels of the SMC sampler over the prior scale (Section 4).
 //
-// Particle state: beta [N][p] FP32 (particle-major); log-likelihood ll[N] and log prior
-// lp[N] in FP64 (lp without the constant -p log(2c), which cancels in every ratio taken
-// at one scale; the change of scale is handled by the incremental weight); normalised
-// log-weights and weights (WeightArrays).
+// Particle state: beta [N][p] FP32 (particle-major); the log-likelihood and the log-prior
+// term sum as compensated FP32 pairs (llq, lpq; the log-prior without the constant
+// -p log(2c), which cancels in every ratio taken at one scale; the change of scale is
+// handled by the incremental weight in FP64); normalised log-weights and weights
+// (WeightArrays).
 //
 // Precision plan for GB300: the CUDA-core FP64 rate is a small fraction of FP32 and an
 // FP64 warp instruction costs a full warp's issue time even with one lane active. So sums
-// over markers run in FP32 with compensated (TwoSum) accumulation, and FP64 appears only
-// where one thread owns one particle (weights, log-likelihoods, log-priors, MH ratios) and
-// in the resampling cumulative sum, whose association order is specified.
+// over markers run in FP32 with compensated (TwoSum) accumulation, the Metropolis-Hastings
+// ratios are formed in FP32 from compensated pairs, and FP64 appears only in the weights
+// (incremental weight, log-sum-exp, ESS, log-evidence; one thread per particle) and in the
+// resampling cumulative sum, whose association order is specified.
 #include <cfloat>
 #include <cmath>
 
@@ -70,6 +72,20 @@ __device__ __forceinline__ float pack_coord(__nv_bfloat16* __restrict__ Arow, in
     return mean_f[j] * bt;
 }
 
+// Four consecutive coordinates j..j+3 (j a multiple of 4): two 8-byte stores per half.
+__device__ __forceinline__ float pack_coord4(__nv_bfloat16* __restrict__ Arow, int Kp, int j, float4 b, float4 l2e,
+                                             float4 mf)
+{
+    const float bt[4] = {b.x * l2e.x, b.y * l2e.y, b.z * l2e.z, b.w * l2e.w};
+    __align__(8) __nv_bfloat16 hi[4];
+    __align__(8) __nv_bfloat16 lo[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) split_bf16(bt[k], hi[k], lo[k]);
+    *reinterpret_cast<uint2*>(Arow + j) = *reinterpret_cast<const uint2*>(hi);
+    *reinterpret_cast<uint2*>(Arow + Kp + j) = *reinterpret_cast<const uint2*>(lo);
+    return mf.x * bt[0] + mf.y * bt[1] + mf.z * bt[2] + mf.w * bt[3];
+}
+
 __device__ __forceinline__ void pack_offset(__nv_bfloat16* __restrict__ Arow, int Kp, int p, float off)
 {
     __nv_bfloat16 hi, lo;
@@ -78,251 +94,335 @@ __device__ __forceinline__ void pack_offset(__nv_bfloat16* __restrict__ Arow, in
     Arow[Kp + p] = lo;
 }
 
-// ------------------------------------------------------------ RW proposal / pack
-// One warp per particle; lane l handles the 4-coordinate groups g = l, l+32, ... (one
-// Philox block of four normals each).
-__global__ void __launch_bounds__(BLOCK) k_propose_rw(const float* __restrict__ beta, float* __restrict__ beta_p,
-                                                     __nv_bfloat16* __restrict__ A, int ldA, int Kp,
-                                                     float2* __restrict__ lpt_p, const float* __restrict__ sigma,
-                                                     const float* __restrict__ l2e_over_s,
-                                                     const float* __restrict__ mean_f, int64_t N, int p, PriorArgs pr,
-                                                     const double* __restrict__ sched, int t, uint32_t m,
-                                                     const uint64_t* __restrict__ seedp, int noise)
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
+
+// ------------------------------------------------------------ Metropolis-Hastings test
+// The log-likelihood of particle i is sp_scale * (sum of the GEMM partials + ydq[i]), kept
+// as a compensated FP32 pair (s, c) in partial units; the log-prior is coef(c_t) * (sum of
+// log1p(|b|/(a c_t)) or |b|), kept as the pair of that sum. At one scale both differences
+// of the MH ratio are between nearby values, so they are formed in FP32 from the pairs:
+// s' - s is exact when the two are within a factor of two, and the c parts carry the rest.
+
+// The proposal's log-likelihood pair: the warp sums the partials, then adds y . eta.
+__device__ __forceinline__ FSum proposal_loglik(const MhState& s, int64_t i, int lane)
 {
-    const int64_t i = warp_global_id();
-    const int lane = threadIdx.x & 31;
-    if (i >= N) return;
-    const uint64_t seed = noise ? *seedp : 0ull;
-    const float ac = (float)((double)pr.a * sched[t]);
-    const float* row = beta + i * p;
-    float* rowp = beta_p + i * p;
-    __nv_bfloat16* Arow = A ? A + i * (int64_t)ldA : nullptr;
-    FSum lt;
-    float off = 0.0f;
-    const int groups = (p + 3) >> 2;
-    for (int g = lane; g < groups; g += 32) {
-        float z[4] = {0.f, 0.f, 0.f, 0.f};
-        if (noise) {
-            const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
-            z[0] = z4.x; z[1] = z4.y; z[2] = z4.z; z[3] = z4.w;
+    FSum L;
+    for (int q = lane; q < s.n_parts; q += 32) L.add(s.partial[(int64_t)q * s.ld_part + i]);
+    L = warp_sum(L);
+    const float2 yd = s.ydq[i];
+    L.add(yd.x);
+    L.add(yd.y);
+    return L;
+}
+
+// Warp-cooperative MH test of particle i's pending proposal; `extra` is the MALA
+// q-correction. Lane 0 decides with the accept uniform of move m_prev and, on acceptance,
+// moves the proposal's log-likelihood and log-prior into the current state. Returns the
+// decision on every lane.
+__device__ __forceinline__ bool mh_decide(const MhState& s, int64_t i, int lane, float coef, float extra, int t,
+                                          uint32_t m_prev, uint64_t seed, uint32_t* err)
+{
+    const FSum L = proposal_loglik(s, i, lane);
+    int accept = 0;
+    if (lane == 0) {
+        const float2 L0 = s.llq[i];
+        const float2 Q1 = s.lpt_p[i], Q0 = s.lpq[i];
+        const float dL = (L.s - L0.x) + (L.c - L0.y);
+        const float dQ = (Q1.x - Q0.x) + (Q1.y - Q0.y);
+        const float log_alpha = s.sp_scale * dL + coef * dQ + extra;
+        if (!isfinite(L.s)) atomicOr(err, DERR_NONFINITE);
+        const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m_prev),
+                                      seed_key(seed));
+        accept = logf(u01_open_f(u.x)) < log_alpha;
+        if (accept) {
+            s.llq[i] = make_float2(L.s, L.c);
+            s.lpq[i] = Q1;
         }
+    }
+    return __shfl_sync(0xffffffffu, accept, 0) != 0;
+}
+
+
+// Accepted-proposal count: per block in shared memory, one global atomic per block.
+__device__ __forceinline__ void count_block(unsigned long long* acc_count, int* blk, bool any)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && any && *blk) atomicAdd(acc_count, (unsigned long long)*blk);
+}
+
+// ------------------------------------------------------------ RW move kernel
+// One warp per particle. With DECIDE, the warp first runs the MH test of the proposal
+// left by the previous move (its log-likelihood partials are complete, the GEMM having run
+// in between) and, on acceptance, writes that proposal back as the particle's state while
+// reading it. Then it draws the next random-walk proposal beta' = beta + sigma xi from the
+// (possibly just accepted) state: beta' to beta_p, the compensated log-prior term sum to
+// lpt_p, y . eta' = beta' . v to ydq and (A != NULL) the split-BF16 GEMM row
+// [hi(bt) | lo(bt)] with bt_j = beta'_j log2(e)/s_j and the offset o = -sum_j m_j bt_j in
+// column p. noise = 0 packs beta unchanged (log-likelihood entry points, t = 0).
+// Lane l handles the 4-coordinate groups g = l, l+32, ... (one Philox block of normals).
+
+// One 4-coordinate group of a random-walk proposal (VEC: p % 4 == 0, float4 access).
+// `live` masks the memory traffic of a lane whose group lies beyond p.
+template <bool VEC>
+__device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool live, bool acc, int noise, float4 z,
+                                         float ac, int de, const float* src, float* dst, float* cur,
+                                         __nv_bfloat16* Arow, FSum& lt, float& yd, float& off)
+{
+    const int j0 = 4 * g;
+    if (VEC) {
+        if (!live) return;
+        const float4 b0 = ld4(src + j0);
+        if (acc) st4(cur + j0, b0);
+        const float4 sg = ld4(a.sigma + j0);
+        const float4 b = noise ? make_float4(fmaf(sg.x, z.x, b0.x), fmaf(sg.y, z.y, b0.y), fmaf(sg.z, z.z, b0.z),
+                                             fmaf(sg.w, z.w, b0.w))
+                               : b0;
+        st4(dst + j0, b);
+        const float4 v = ld4(a.vy + j0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            const int j = 4 * g + k;
-            if (j < p) {
-                const float b = noise ? row[j] + sigma[j] * z[k] : row[j];
-                rowp[j] = b;
-                lt.add(prior_term(b, ac, pr.de));
-                if (Arow) off += pack_coord(Arow, Kp, j, b, l2e_over_s, mean_f);
+            lt.add(prior_term(comp(b, k), ac, de));
+            yd = fmaf(comp(b, k), comp(v, k), yd);
+        }
+        if (Arow) off += pack_coord4(Arow, a.Kp, j0, b, ld4(a.l2e_over_s + j0), ld4(a.mean_f + j0));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = j0 + k;
+            if (live && j < p) {
+                const float b0 = src[j];
+                if (acc) cur[j] = b0;
+                const float b = noise ? fmaf(a.sigma[j], comp(z, k), b0) : b0;
+                dst[j] = b;
+                lt.add(prior_term(b, ac, de));
+                yd = fmaf(b, a.vy[j], yd);
+                if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
             }
         }
     }
-    lt = warp_sum(lt);
-    off = warp_sum(off);
-    if (lane == 0) {
-        lpt_p[i] = make_float2(lt.s, lt.c);
-        if (Arow) pack_offset(Arow, Kp, p, off);
-    }
 }
 
-// ------------------------------------------------------------ MALA proposal
+// The block's scale constants, formed once by thread 0: a c_t (FP64 product), 1/c_t and the
+// log-prior coefficient (FP64 instructions cost a whole warp's issue time, so not once per
+// warp).
+__device__ __forceinline__ void step_constants(PriorArgs pr, const double* sched, int t, float* sh)
+{
+    if (threadIdx.x == 0) {
+        const double c = sched[t];
+        sh[0] = (float)((double)pr.a * c);
+        sh[2] = 1.0f / (float)c;
+        sh[1] = pr.de ? -sh[2] : -(pr.a + 1.0f);
+    }
+    __syncthreads();
+}
+
+template <bool DECIDE, bool VEC>
+__global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int p, PriorArgs pr,
+                                                  const double* __restrict__ sched, int t, uint32_t m, uint32_t m_prev,
+                                                  const uint64_t* __restrict__ seedp, int noise, uint32_t* err)
+{
+    __shared__ int blk;
+    __shared__ float shk[3];
+    if (DECIDE && threadIdx.x == 0) blk = 0;
+    step_constants(pr, sched, t, shk);
+    const int64_t i = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (i < N) {
+        const uint64_t seed = (noise || DECIDE) ? *seedp : 0ull;
+        const float ac = shk[0];
+        bool acc = false;
+        if (DECIDE) {
+            acc = mh_decide(a.mh, i, lane, shk[1], 0.0f, t, m_prev, seed, err);
+            if (acc && lane == 0) atomicAdd(&blk, 1);
+        }
+        const float* src = (acc ? a.beta_p : a.beta) + i * p;
+        float* dst = a.beta_p + i * p;
+        float* cur = a.beta + i * p;
+        __nv_bfloat16* Arow = a.A ? a.A + i * (int64_t)a.ldA : nullptr;
+        FSum lt;
+        float yd = 0.0f, off = 0.0f;
+        const int groups = (p + 3) >> 2;
+        for (int g = lane; g < groups; g += 32) {
+            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (noise) z = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
+            rw_group<VEC>(a, p, g, true, acc, noise, z, ac, pr.de, src, dst, cur, Arow, lt, yd, off);
+        }
+        lt = warp_sum(lt);
+        yd = warp_sum(yd);
+        off = warp_sum(off);
+        if (lane == 0) {
+            a.lpt_p[i] = make_float2(lt.s, lt.c);
+            a.ydq[i] = make_float2(yd, 0.0f);
+            if (Arow) pack_offset(Arow, a.Kp, p, off);
+        }
+    }
+    if (DECIDE) count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+}
+
+// ------------------------------------------------------------ MALA move kernel
 // beta' = beta + (h^2/2) D grad log pi_t(beta) + h D^{1/2} xi with D = diag(D_j) and
 // h = lambda p^{-1/6} (written by the column-statistics kernel); grad log pi_t = grad l
 // (stored per particle) + the prior gradient -(a+1) sgn(beta)/(a c + |beta|) (double
 // exponential: -sgn(beta)/c). The forward density is evaluated at the proposal as
 // written (rounded to FP32): fwd = sum_j (beta'_j - beta_j - (h^2/2) D_j g_j)^2 / D_j, so
-// log q(beta'|beta) = -fwd/(2h^2) + const, the same formula as the reverse term.
-__global__ void __launch_bounds__(BLOCK) k_propose_mala(const float* __restrict__ beta, const float* __restrict__ gl,
-                                                       float* __restrict__ beta_p, __nv_bfloat16* __restrict__ A,
-                                                       int ldA, int Kp, float2* __restrict__ lpt_p,
-                                                       float2* __restrict__ fwd_out, const float* __restrict__ D,
-                                                       const float* __restrict__ h_dev,
-                                                       const float* __restrict__ l2e_over_s,
-                                                       const float* __restrict__ mean_f, int64_t N, int p, PriorArgs pr,
-                                                       const double* __restrict__ sched, int t, uint32_t m,
-                                                       const uint64_t* __restrict__ seedp)
+// log q(beta'|beta) = -fwd/(2h^2) + const, the same formula as the reverse term. With
+// DECIDE the warp first forms the reverse term of the pending proposal,
+// bwd = sum_j (beta_j - beta'_j - (h^2/2) D_j g'_j)^2 / D_j, and runs its MH test with
+// log alpha = l' + lp' - l - lp - (bwd - fwd)/(2h^2); an accepted proposal and its gradient
+// are written back as the state while being read.
+template <bool DECIDE>
+__global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
+                                                    const double* __restrict__ sched, int t, uint32_t m,
+                                                    uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
 {
+    __shared__ int blk;
+    __shared__ float shk[3];
+    if (DECIDE && threadIdx.x == 0) blk = 0;
+    step_constants(pr, sched, t, shk);
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
-    if (i >= N) return;
-    const uint64_t seed = *seedp;
-    const double c = sched[t];
-    const float ac = (float)((double)pr.a * c), a1 = pr.a + 1.0f, inv_c = (float)(1.0 / c);
-    const float h = *h_dev, h2 = 0.5f * h * h;
-    const float* row = beta + i * p;
-    const float* grow = gl + i * p;
-    float* rowp = beta_p + i * p;
-    __nv_bfloat16* Arow = A ? A + i * (int64_t)ldA : nullptr;
-    FSum lt, fw;
-    float off = 0.0f;
-    const int groups = (p + 3) >> 2;
-    for (int g = lane; g < groups; g += 32) {
-        const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
-        const float z[4] = {z4.x, z4.y, z4.z, z4.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = 4 * g + k;
-            if (j < p) {
-                const float b0 = row[j];
-                const float Dj = D[j];
-                const float drift = h2 * Dj * (grow[j] + dlogprior(b0, a1, ac, inv_c, pr.de));
-                const float b = (b0 + drift) + h * sqrtf(Dj) * z[k];
-                rowp[j] = b;
-                const float d = (b - b0) - drift;
-                fw.add(d * d / Dj);
-                lt.add(prior_term(b, ac, pr.de));
-                if (Arow) off += pack_coord(Arow, Kp, j, b, l2e_over_s, mean_f);
-            }
-        }
-    }
-    lt = warp_sum(lt);
-    fw = warp_sum(fw);
-    off = warp_sum(off);
-    if (lane == 0) {
-        lpt_p[i] = make_float2(lt.s, lt.c);
-        fwd_out[i] = make_float2(fw.s, fw.c);
-        if (Arow) pack_offset(Arow, Kp, p, off);
-    }
-}
-
-// --------------------------------------------------------------- finish / MH test
-// One thread per particle for the FP64 scalars (32 particles per warp instruction), then
-// the block's warps copy the accepted rows.
-__device__ __forceinline__ double finish_loglik(const AcceptArgs& a, int64_t i)
-{
-    FSum sp;
-    for (int s = 0; s < a.n_parts; ++s) sp.add(a.partial[(int64_t)s * a.ld_part + i]);
-    return a.sp_scale * sp.value();
-}
-
-constexpr int ACC_PER_BLOCK = 32;
-
-// Copy the accepted rows of the block's 32 particles: every thread moves 4-element chunks
-// of all rows at once, so the loads are in flight together.
-__device__ __forceinline__ void copy_accepted_rows(const unsigned char* flag, int64_t i0, int64_t N, int p,
-                                                   const float* __restrict__ src, float* __restrict__ dst,
-                                                   const float* __restrict__ src2, float* __restrict__ dst2)
-{
-    const int64_t total = (int64_t)ACC_PER_BLOCK * p;
-    for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-        const int q = (int)(e / p);
-        if (!flag[q] || i0 + q >= N) continue;
-        const int64_t off = i0 * p + e;
-        dst[off] = src[off];
-        if (src2) dst2[off] = src2[off];
-    }
-}
-
-__global__ void __launch_bounds__(BLOCK) k_accept(AcceptArgs a, int64_t N, int p, PriorArgs pr,
-                                                 const double* __restrict__ sched, int mode, int t, uint32_t m,
-                                                 const uint64_t* __restrict__ seedp, uint32_t* __restrict__ err)
-{
-    __shared__ unsigned char flag[ACC_PER_BLOCK];
-    __shared__ int nacc;
-    const int64_t i0 = (int64_t)blockIdx.x * ACC_PER_BLOCK;
-    if (threadIdx.x < 32) {
-        const int64_t i = i0 + threadIdx.x;
-        int accept = 0;
-        if (i < N) {
-            const double llp = finish_loglik(a, i);
-            const float2 q = a.lpt_p[i];
-            const double lpp = prior_coef(pr, sched[t]) * ((double)q.x + (double)q.y);
-            if (!isfinite(llp)) atomicOr(err, DERR_NONFINITE);
-            if (mode == 0) {
-                a.ll[i] = llp;
-                if (a.lp) a.lp[i] = lpp;
-                if (a.logw) a.logw[i] = llp;
-            } else {
-                const double log_alpha = (llp - a.ll[i]) + (lpp - a.lp[i]);
-                const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m),
-                                              seed_key(*seedp));
-                accept = (double)logf(u01_open_f(u.x)) < log_alpha;
-                if (accept) {
-                    a.ll[i] = llp;
-                    a.lp[i] = lpp;
-                }
-            }
-        }
-        flag[threadIdx.x] = (unsigned char)accept;
-        const int cnt = __popc(__ballot_sync(0xffffffffu, accept));
-        if (threadIdx.x == 0) {
-            nacc = cnt;
-            if (cnt && a.acc_count) atomicAdd(a.acc_count, (unsigned long long)cnt);
-        }
-    }
-    __syncthreads();
-    if (nacc == 0) return;
-    copy_accepted_rows(flag, i0, N, p, a.beta_p, a.beta, nullptr, nullptr);
-}
-
-// MH test of a MALA proposal: log alpha = l' + lp' - l - lp + log q(beta|beta') - log q(beta'|beta),
-// log q(x|z) = -sum_j (x_j - z_j - (h^2/2) D_j g_j(z))^2 / (2 h^2 D_j) + const. Accepted rows
-// move beta and its gradient.
-__global__ void __launch_bounds__(BLOCK) k_accept_mala(AcceptArgs a, float* __restrict__ gl,
-                                                      const float* __restrict__ gl_p, const float2* __restrict__ fwd,
-                                                      const float* __restrict__ D, const float* __restrict__ h_dev,
-                                                      int64_t N, int p, PriorArgs pr, const double* __restrict__ sched,
-                                                      int t, uint32_t m, const uint64_t* __restrict__ seedp,
-                                                      uint32_t* __restrict__ err)
-{
-    __shared__ unsigned char flag[ACC_PER_BLOCK];
-    __shared__ float2 bwd_sh[ACC_PER_BLOCK];
-    __shared__ int nacc;
-    const int64_t i0 = (int64_t)blockIdx.x * ACC_PER_BLOCK;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const double c = sched[t];
-    const float ac = (float)((double)pr.a * c), a1 = pr.a + 1.0f, inv_c = (float)(1.0 / c);
-    const float h = *h_dev, h2 = 0.5f * h * h;
-    // reverse-move residuals, one warp per particle
-    for (int q = w; q < ACC_PER_BLOCK; q += WARPS) {
-        const int64_t k = i0 + q;
-        FSum bwd;
-        if (k < N) {
-            const float* b0 = a.beta + k * p;
-            const float* b1 = a.beta_p + k * p;
-            const float* g1 = gl_p + k * p;
+    if (i < N) {
+        const uint64_t seed = *seedp;
+        const float ac = shk[0], a1 = pr.a + 1.0f, inv_c = shk[2];
+        const float h = *a.h, h2 = 0.5f * h * h;
+        const float* D = a.sigma;
+        bool acc = false;
+        if (DECIDE) {
+            FSum bwd;
+            const float* b0 = a.beta + i * p;
+            const float* b1 = a.beta_p + i * p;
+            const float* g1 = a.gl_p + i * p;
             for (int j = lane; j < p; j += 32) {
                 const float Dj = D[j];
                 const float drift = h2 * Dj * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
                 const float d = (b0[j] - b1[j]) - drift;
                 bwd.add(d * d / Dj);
             }
+            bwd = warp_sum(bwd);
+            const float2 fw = a.fwd[i];
+            const float extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
+            acc = mh_decide(a.mh, i, lane, shk[1], extra, t, m_prev, seed, err);
+            if (acc && lane == 0) atomicAdd(&blk, 1);
         }
-        bwd = warp_sum(bwd);
-        if (lane == 0) bwd_sh[q] = make_float2(bwd.s, bwd.c);
-    }
-    __syncthreads();
-    if (w == 0) {
-        const int64_t i = i0 + lane;
-        int accept = 0;
-        if (i < N) {
-            const double llp = finish_loglik(a, i);
-            const float2 q = a.lpt_p[i];
-            const double lpp = prior_coef(pr, c) * ((double)q.x + (double)q.y);
-            if (!isfinite(llp)) atomicOr(err, DERR_NONFINITE);
-            const float2 bw = bwd_sh[lane];
-            const float2 fw = fwd[i];
-            const double hh2 = 2.0 * (double)h * (double)h;
-            const double log_alpha = (llp - a.ll[i]) + (lpp - a.lp[i]) -
-                                     (((double)bw.x + (double)bw.y) - ((double)fw.x + (double)fw.y)) / hh2;
-            const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m),
-                                          seed_key(*seedp));
-            accept = (double)logf(u01_open_f(u.x)) < log_alpha;
-            if (accept) {
-                a.ll[i] = llp;
-                a.lp[i] = lpp;
+        const float* src = (acc ? a.beta_p : a.beta) + i * p;
+        const float* gsrc = (acc ? a.gl_p : a.gl) + i * p;
+        float* cur = a.beta + i * p;
+        float* gcur = a.gl + i * p;
+        float* dst = a.beta_p + i * p;
+        __nv_bfloat16* Arow = a.A ? a.A + i * (int64_t)a.ldA : nullptr;
+        FSum lt, fw;
+        float yd = 0.0f, off = 0.0f;
+        const int groups = (p + 3) >> 2;
+        for (int g = lane; g < groups; g += 32) {
+            const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = 4 * g + k;
+                if (j < p) {
+                    const float b0 = src[j];
+                    const float g0 = gsrc[j];
+                    if (acc) {
+                        cur[j] = b0;
+                        gcur[j] = g0;
+                    }
+                    const float Dj = D[j];
+                    const float drift = h2 * Dj * (g0 + dlogprior(b0, a1, ac, inv_c, pr.de));
+                    const float b = (b0 + drift) + h * sqrtf(Dj) * comp(z4, k);
+                    dst[j] = b;
+                    const float d = (b - b0) - drift;
+                    fw.add(d * d / Dj);
+                    lt.add(prior_term(b, ac, pr.de));
+                    yd = fmaf(b, a.vy[j], yd);
+                    if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
+                }
             }
         }
-        flag[lane] = (unsigned char)accept;
-        const int cnt = __popc(__ballot_sync(0xffffffffu, accept));
+        lt = warp_sum(lt);
+        fw = warp_sum(fw);
+        yd = warp_sum(yd);
+        off = warp_sum(off);
         if (lane == 0) {
-            nacc = cnt;
-            if (cnt && a.acc_count) atomicAdd(a.acc_count, (unsigned long long)cnt);
+            a.lpt_p[i] = make_float2(lt.s, lt.c);
+            a.fwd[i] = make_float2(fw.s, fw.c);
+            a.ydq[i] = make_float2(yd, 0.0f);
+            if (Arow) pack_offset(Arow, a.Kp, p, off);
         }
     }
-    __syncthreads();
-    if (nacc == 0) return;
-    copy_accepted_rows(flag, i0, N, p, a.beta_p, a.beta, gl_p, gl);
+    if (DECIDE) count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+}
+
+// ------------------------------------------------------------ last move of a step
+// MH test of the pending proposals (RW, or MALA with the reverse term), then accepted
+// proposals (and their gradients) are copied into the state rows, so that between steps
+// beta and gl hold the particles.
+template <bool MALA, bool VEC>
+__global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, int p, PriorArgs pr,
+                                                      const double* __restrict__ sched, int t, uint32_t m_prev,
+                                                      const uint64_t* __restrict__ seedp, uint32_t* err)
+{
+    __shared__ int blk;
+    __shared__ float shk[3];
+    if (threadIdx.x == 0) blk = 0;
+    step_constants(pr, sched, t, shk);
+    const int64_t i = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (i < N) {
+        float extra = 0.0f;
+        if (MALA) {
+            const float ac = shk[0], a1 = pr.a + 1.0f, inv_c = shk[2];
+            const float h = *a.h, h2 = 0.5f * h * h;
+            FSum bwd;
+            const float* b0 = a.beta + i * p;
+            const float* b1 = a.beta_p + i * p;
+            const float* g1 = a.gl_p + i * p;
+            for (int j = lane; j < p; j += 32) {
+                const float Dj = a.sigma[j];
+                const float drift = h2 * Dj * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
+                const float d = (b0[j] - b1[j]) - drift;
+                bwd.add(d * d / Dj);
+            }
+            bwd = warp_sum(bwd);
+            const float2 fw = a.fwd[i];
+            extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
+        }
+        const bool acc = mh_decide(a.mh, i, lane, shk[1], extra, t, m_prev, *seedp, err);
+        if (acc) {
+            if (lane == 0) atomicAdd(&blk, 1);
+            const float* src = a.beta_p + i * p;
+            float* dst = a.beta + i * p;
+            if (VEC) {
+                for (int j = 4 * lane; j < p; j += 128) st4(dst + j, ld4(src + j));
+                if (MALA)
+                    for (int j = 4 * lane; j < p; j += 128) st4(a.gl + i * p + j, ld4(a.gl_p + i * p + j));
+            } else {
+                for (int j = lane; j < p; j += 32) dst[j] = src[j];
+                if (MALA)
+                    for (int j = lane; j < p; j += 32) a.gl[i * p + j] = a.gl_p[i * p + j];
+            }
+        }
+    }
+    count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+}
+
+// ------------------------------------------------------------ log-likelihood finish
+// The packed particles' log-likelihood as the state: llq (pair), lpq = lpt_p, and in FP64
+// l = sp_scale (s + c) to logw (prior-IS weights at t = 0) and/or ll_out.
+__global__ void __launch_bounds__(BLOCK) k_finish_loglik(MhState s, int64_t N, double* __restrict__ logw,
+                                                        double* __restrict__ ll_out, uint32_t* __restrict__ err)
+{
+    const int64_t i = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const FSum L = proposal_loglik(s, i, lane);
+    if (lane != 0) return;
+    if (!isfinite(L.s)) atomicOr(err, DERR_NONFINITE);
+    s.llq[i] = make_float2(L.s, L.c);
+    s.lpq[i] = s.lpt_p[i];
+    const double l = s.sp_scale_d * ((double)L.s + (double)L.c);
+    if (logw) logw[i] = l;
+    if (ll_out) ll_out[i] = l;
 }
 
 // ------------------------------------------------------------------ reweighting
@@ -335,15 +435,22 @@ constexpr int RW_PER_BLOCK = 32;
 constexpr int RW_THREADS = 32 * RW_PER_BLOCK;
 
 __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict__ beta, double* __restrict__ logw,
-                                                   double* __restrict__ lp, int64_t N, int p, PriorArgs pr,
+                                                   float2* __restrict__ lpq, int64_t N, int p, PriorArgs pr,
                                                    const double* __restrict__ sched, int t, uint32_t* __restrict__ err)
 {
     __shared__ float4 sums[RW_PER_BLOCK];
+    __shared__ float shk[4];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RW_PER_BLOCK;
-    const double c = sched[t], cp = sched[t - 1];
-    const float k1 = (float)(cp - c), kc = (float)c, kac = (float)((double)pr.a * cp);
-    const float ac = (float)((double)pr.a * c);
+    if (threadIdx.x == 0) {  // the scale constants once per block (FP64)
+        const double c = sched[t], cp = sched[t - 1];
+        shk[0] = (float)(cp - c);
+        shk[1] = (float)c;
+        shk[2] = (float)((double)pr.a * cp);
+        shk[3] = (float)((double)pr.a * c);
+    }
+    __syncthreads();
+    const float k1 = shk[0], kc = shk[1], kac = shk[2], ac = shk[3];
     {
         const int q = w;
         const int64_t i = base + q;
@@ -362,15 +469,16 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
     __syncthreads();
     if (w == 0) {
         const int64_t i = base + lane;
+        const double c = sched[t], cp = sched[t - 1];
         if (i < N) {
             const float4 s = sums[lane];
-            const double sd = (double)s.x + (double)s.y, sn = (double)s.z + (double)s.w;
+            const double sd = (double)s.x + (double)s.y;
             const double lbase = -(double)p * log(c / cp);
             const double d = pr.de ? lbase - sd * (1.0 / c - 1.0 / cp) : lbase - ((double)pr.a + 1.0) * sd;
             const double nl = logw[i] + d;
             if (!isfinite(nl)) atomicOr(err, DERR_NONFINITE);
             logw[i] = nl;
-            lp[i] = prior_coef(pr, c) * sn;
+            lpq[i] = make_float2(s.z, s.w);
         }
     }
 }
@@ -401,7 +509,9 @@ __device__ double block_sum_f64(double v, double* sh)
 
 // Each block: (m_b, sum e^{x - m_b}, sum e^{2(x - m_b)}) over its elements. The last block
 // to finish combines the blocks in block order and publishes LSE, ESS, log Z and the flag.
-__global__ void __launch_bounds__(BLOCK) k_lse_partial(const double* __restrict__ logw, int64_t N,
+constexpr int LSE_THREADS = 128;  // one weight per thread up to 128 x LSE_BLOCKS particles
+
+__global__ void __launch_bounds__(LSE_THREADS) k_lse_partial(const double* __restrict__ logw, int64_t N,
                                                       double* __restrict__ scratch, unsigned int* __restrict__ counter,
                                                       int t, int mode, double ess_frac, double* __restrict__ ess_out,
                                                       double* __restrict__ logz_out, uint8_t* __restrict__ res_out,
@@ -409,12 +519,12 @@ __global__ void __launch_bounds__(BLOCK) k_lse_partial(const double* __restrict_
 {
     __shared__ double sh[BLOCK / 32];
     __shared__ bool last;
-    const int64_t stride = (int64_t)gridDim.x * BLOCK;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     double mx = -DBL_MAX;
-    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < N; i += stride) mx = fmax(mx, logw[i]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) mx = fmax(mx, logw[i]);
     const double mb = block_max_f64(mx, sh);
     double s1 = 0.0, s2 = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * BLOCK + threadIdx.x; i < N; i += stride) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
         const double e = exp(logw[i] - mb);
         s1 += e;
         s2 += e * e;
@@ -504,32 +614,53 @@ constexpr int RS_BLOCK = 256;  // cumulative-sum block of the specified associat
 
 // The cumulative sum C of W in the specified order: a running sum inside each 256-block
 // in index order, a running sum of the block totals, C_i = carry(block) + local_i.
-// cum holds N + ceil(N/256) + 1 doubles: C, then one carry per block, then u.
+// cum holds N + ceil(N/256) + 1 doubles: C, then one carry per block, then u. Block totals
+// pass through shared memory (RS_TOT at a time), so the sequential carry sum reads no
+// global memory.
+constexpr int RS_TOT = 4096;
+
 __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __restrict__ W, int64_t N,
                                                                double* __restrict__ cum, const int* __restrict__ flag,
                                                                int t, const uint64_t* __restrict__ seedp,
                                                                double u_override)
 {
     if (flag && *flag == 0) return;
+    __shared__ double tot[RS_TOT];
     const int tid = threadIdx.x;
     const int64_t nblk = (N + RS_BLOCK - 1) / RS_BLOCK;
     double* carry = cum + N;
-    for (int64_t b = tid; b < nblk; b += RS_THREADS) {
-        const int64_t i0 = b * RS_BLOCK, i1 = (i0 + RS_BLOCK < N) ? i0 + RS_BLOCK : N;
-        double local = 0.0;
-        for (int64_t i = i0; i < i1; ++i) {
-            local = __dadd_rn(local, W[i]);
-            cum[i] = local;
+    double run = 0.0;  // thread 0's running sum of block totals
+    for (int64_t b0 = 0; b0 < nblk; b0 += RS_TOT) {
+        const int64_t b1 = (b0 + RS_TOT < nblk) ? b0 + RS_TOT : nblk;
+        for (int64_t b = b0 + tid; b < b1; b += RS_THREADS) {
+            const int64_t i0 = b * RS_BLOCK, i1 = (i0 + RS_BLOCK < N) ? i0 + RS_BLOCK : N;
+            double local = 0.0;
+            int64_t i = i0;
+            for (; i + 8 <= i1; i += 8) {  // loads ahead of the dependent additions
+                double w[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) w[k] = W[i + k];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    local = __dadd_rn(local, w[k]);
+                    cum[i + k] = local;
+                }
+            }
+            for (; i < i1; ++i) {
+                local = __dadd_rn(local, W[i]);
+                cum[i] = local;
+            }
+            tot[b - b0] = local;
         }
+        __syncthreads();
+        if (tid == 0)
+            for (int64_t b = b0; b < b1; ++b) {
+                carry[b] = run;
+                run = __dadd_rn(run, tot[b - b0]);
+            }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
-        double c = 0.0;
-        for (int64_t b = 0; b < nblk; ++b) {
-            carry[b] = c;
-            const int64_t last = ((b + 1) * RS_BLOCK < N ? (b + 1) * RS_BLOCK : N) - 1;
-            c = __dadd_rn(c, cum[last]);
-        }
         if (seedp) {
             const uint4 u = philox4x32_10(make_uint4(0u, 0u, (uint32_t)t, TAG_RESAMPLE << 16), seed_key(*seedp));
             carry[nblk] = u01_d(u.x);
@@ -538,11 +669,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __re
         }
     }
     __syncthreads();
-    for (int64_t b = 1 + tid; b < nblk; b += RS_THREADS) {
-        const int64_t i0 = b * RS_BLOCK, i1 = (i0 + RS_BLOCK < N) ? i0 + RS_BLOCK : N;
-        const double cb = carry[b];
-        for (int64_t i = i0; i < i1; ++i) cum[i] = __dadd_rn(cb, cum[i]);
-    }
+    for (int64_t e = RS_BLOCK + tid; e < N; e += RS_THREADS) cum[e] = __dadd_rn(carry[e / RS_BLOCK], cum[e]);
 }
 
 // A_k = min{i : C_i > (k + u)/N}, clamped to N - 1. C is non-negative and non-decreasing,
@@ -569,46 +696,68 @@ __global__ void k_resample_search(const double* __restrict__ cum, int64_t N, int
     }
 }
 
-__global__ void k_gather(const int32_t* __restrict__ idx, const float* __restrict__ beta, float* __restrict__ beta_tmp,
-                         const double* __restrict__ ll, const double* __restrict__ lp, double* __restrict__ ll_tmp,
-                         double* __restrict__ lp_tmp, const float* __restrict__ g, float* __restrict__ g_tmp, int64_t N,
-                         int p, const int* __restrict__ flag)
+// Ancestor rows into the scratch buffers, one warp per new particle k: beta_tmp[k] =
+// beta[idx[k]] (and the gradient rows for MALA), with the log-likelihood and log-prior pairs.
+template <bool VEC>
+__global__ void __launch_bounds__(BLOCK) k_gather(const int32_t* __restrict__ idx, const float* __restrict__ beta,
+                                                 float* __restrict__ beta_tmp, const float2* __restrict__ llq,
+                                                 const float2* __restrict__ lpq, float2* __restrict__ llq_tmp,
+                                                 float2* __restrict__ lpq_tmp, const float* __restrict__ g,
+                                                 float* __restrict__ g_tmp, int64_t N, int p, const int* __restrict__ flag)
 {
     if (*flag == 0) return;
-    const int64_t total = N * (int64_t)p;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = e / p;
-        const int j = (int)(e - k * p);
-        const int64_t a = idx[k];
-        beta_tmp[e] = beta[a * p + j];
-        if (g) g_tmp[e] = g[a * p + j];
-        if (j == 0) {
-            ll_tmp[k] = ll[a];
-            lp_tmp[k] = lp[a];
-        }
+    const int64_t k = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
+    const int64_t a = idx[k];
+    const float* src = beta + a * p;
+    float* dst = beta_tmp + k * p;
+    if (VEC) {
+        for (int j = 4 * lane; j < p; j += 128) st4(dst + j, ld4(src + j));
+        if (g)
+            for (int j = 4 * lane; j < p; j += 128) st4(g_tmp + k * p + j, ld4(g + a * p + j));
+    } else {
+        for (int j = lane; j < p; j += 32) dst[j] = src[j];
+        if (g)
+            for (int j = lane; j < p; j += 32) g_tmp[k * p + j] = g[a * p + j];
+    }
+    if (lane == 0) {
+        llq_tmp[k] = llq[a];
+        lpq_tmp[k] = lpq[a];
     }
 }
 
-__global__ void k_copyback(float* __restrict__ beta, const float* __restrict__ beta_tmp, double* __restrict__ ll,
-                           double* __restrict__ lp, const double* __restrict__ ll_tmp, const double* __restrict__ lp_tmp,
-                           float* __restrict__ g, const float* __restrict__ g_tmp, WeightArrays w, int64_t N, int p,
-                           const int* __restrict__ flag, double lw, double wi, uint32_t wf)
+// The resampled particles back into the state, with uniform weights (log(1/N), 1/N and
+// round(2^31/N), formed on the host).
+template <bool VEC>
+__global__ void __launch_bounds__(BLOCK) k_copyback(float* __restrict__ beta, const float* __restrict__ beta_tmp,
+                                                   float2* __restrict__ llq, float2* __restrict__ lpq,
+                                                   const float2* __restrict__ llq_tmp, const float2* __restrict__ lpq_tmp,
+                                                   float* __restrict__ g, const float* __restrict__ g_tmp, WeightArrays w,
+                                                   int64_t N, int p, const int* __restrict__ flag, double lw, double wi,
+                                                   uint32_t wf)
 {
     if (*flag == 0) return;
-    const int64_t total = N * (int64_t)p;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = e / p;
-        const int j = (int)(e - k * p);
-        beta[e] = beta_tmp[e];
-        if (g) g[e] = g_tmp[e];
-        if (j == 0) {
-            ll[k] = ll_tmp[k];
-            lp[k] = lp_tmp[k];
-            w.logw[k] = lw;
-            w.W[k] = wi;
-            w.Wf[k] = (float)wi;
-            w.wfix[k] = wf;
-        }
+    const int64_t k = warp_global_id();
+    const int lane = threadIdx.x & 31;
+    if (k >= N) return;
+    const int64_t o = k * p;
+    if (VEC) {
+        for (int j = 4 * lane; j < p; j += 128) st4(beta + o + j, ld4(beta_tmp + o + j));
+        if (g)
+            for (int j = 4 * lane; j < p; j += 128) st4(g + o + j, ld4(g_tmp + o + j));
+    } else {
+        for (int j = lane; j < p; j += 32) beta[o + j] = beta_tmp[o + j];
+        if (g)
+            for (int j = lane; j < p; j += 32) g[o + j] = g_tmp[o + j];
+    }
+    if (lane == 0) {
+        llq[k] = llq_tmp[k];
+        lpq[k] = lpq_tmp[k];
+        w.logw[k] = lw;
+        w.W[k] = wi;
+        w.Wf[k] = (float)wi;
+        w.wfix[k] = wf;
     }
 }
 
@@ -981,47 +1130,65 @@ cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_propose_rw(const float* beta, float* beta_p, __nv_bfloat16* A, int ldA, int Kp, float2* lpt_p,
-                              const float* sigma, const float* l2e_over_s, const float* mean_f, int64_t N, int p,
-                              PriorArgs pr, const double* sched, int t, uint32_t m, const uint64_t* seed, int noise,
-                              cudaStream_t st)
+cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                           uint32_t m, uint32_t m_prev, const uint64_t* seed, int noise, uint32_t* err, cudaStream_t st)
 {
-    k_propose_rw<<<warps_grid(N), BLOCK, 0, st>>>(beta, beta_p, A, ldA, Kp, lpt_p, sigma, l2e_over_s, mean_f, N, p, pr,
-                                                  sched, t, m, seed, noise);
+    const bool vec = (p & 3) == 0;
+    const unsigned grid = warps_grid(N);
+    if (decide) {
+        if (vec)
+            k_move_rw<true, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+        else
+            k_move_rw<true, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+    } else {
+        if (vec)
+            k_move_rw<false, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+        else
+            k_move_rw<false, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_propose_mala(const float* beta, const float* gl, float* beta_p, __nv_bfloat16* A, int ldA, int Kp,
-                                float2* lpt_p, float2* fwd, const float* D, const float* h, const float* l2e_over_s,
-                                const float* mean_f, int64_t N, int p, PriorArgs pr, const double* sched, int t,
-                                uint32_t m, const uint64_t* seed, cudaStream_t st)
+cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                             uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
-    k_propose_mala<<<warps_grid(N), BLOCK, 0, st>>>(beta, gl, beta_p, A, ldA, Kp, lpt_p, fwd, D, h, l2e_over_s, mean_f,
-                                                    N, p, pr, sched, t, m, seed);
+    if (decide)
+        k_move_mala<true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, err);
+    else
+        k_move_mala<false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_accept(const AcceptArgs& a, int64_t N, int p, PriorArgs pr, const double* sched, int mode, int t,
-                          uint32_t m, const uint64_t* seed, uint32_t* err, cudaStream_t st)
+cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                               uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
-    k_accept<<<(unsigned)((N + ACC_PER_BLOCK - 1) / ACC_PER_BLOCK), BLOCK, 0, st>>>(a, N, p, pr, sched, mode, t, m, seed,
-                                                                                     err);
+    const bool vec = (p & 3) == 0;
+    const unsigned grid = warps_grid(N);
+    if (mala) {
+        if (vec)
+            k_move_commit<true, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
+        else
+            k_move_commit<true, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
+    } else {
+        if (vec)
+            k_move_commit<false, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
+        else
+            k_move_commit<false, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_accept_mala(const AcceptArgs& a, float* gl, const float* gl_p, const float2* fwd, const float* D,
-                               const float* h, int64_t N, int p, PriorArgs pr, const double* sched, int t, uint32_t m,
-                               const uint64_t* seed, uint32_t* err, cudaStream_t st)
+cudaError_t launch_finish_loglik(const MhState& s, int64_t N, double* logw, double* ll_out, uint32_t* err,
+                                 cudaStream_t st)
 {
-    k_accept_mala<<<(unsigned)((N + ACC_PER_BLOCK - 1) / ACC_PER_BLOCK), BLOCK, 0, st>>>(a, gl, gl_p, fwd, D, h, N, p, pr,
-                                                                                          sched, t, m, seed, err);
+    k_finish_loglik<<<warps_grid(N), BLOCK, 0, st>>>(s, N, logw, ll_out, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reweight(const float* beta, double* logw, double* lp, int64_t N, int p, PriorArgs pr,
+cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_t N, int p, PriorArgs pr,
                             const double* sched, int t, uint32_t* err, cudaStream_t st)
 {
-    k_reweight<<<(unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK), RW_THREADS, 0, st>>>(beta, logw, lp, N, p, pr, sched,
+    k_reweight<<<(unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK), RW_THREADS, 0, st>>>(beta, logw, lpq, N, p, pr, sched,
                                                                                          t, err);
     return cudaGetLastError();
 }
@@ -1030,9 +1197,9 @@ cudaError_t launch_lse_ess(const WeightArrays& w, int64_t N, double* scratch, un
                            double ess_frac, double* ess_out, double* logz_out, uint8_t* resampled_out, int* flag,
                            uint32_t* err, cudaStream_t st)
 {
-    int64_t blocks = (N + BLOCK - 1) / BLOCK;
+    int64_t blocks = (N + LSE_THREADS - 1) / LSE_THREADS;
     if (blocks > LSE_BLOCKS) blocks = LSE_BLOCKS;
-    k_lse_partial<<<(unsigned)blocks, BLOCK, 0, st>>>(w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
+    k_lse_partial<<<(unsigned)blocks, LSE_THREADS, 0, st>>>(w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
                                                       resampled_out, flag, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1062,23 +1229,33 @@ cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const double* ll, const double* lp,
-                          double* ll_tmp, double* lp_tmp, const float* g, float* g_tmp, int64_t N, int p,
+cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const float2* llq, const float2* lpq,
+                          float2* llq_tmp, float2* lpq_tmp, const float* g, float* g_tmp, int64_t N, int p,
                           const int* flag, cudaStream_t st)
 {
-    k_gather<<<elem_grid(N * p), 256, 0, st>>>(idx, beta, beta_tmp, ll, lp, ll_tmp, lp_tmp, g, g_tmp, N, p, flag);
+    if ((p & 3) == 0)
+        k_gather<true><<<warps_grid(N), BLOCK, 0, st>>>(idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
+                                                        flag);
+    else
+        k_gather<false><<<warps_grid(N), BLOCK, 0, st>>>(idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
+                                                         flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_copyback(float* beta, const float* beta_tmp, double* ll, double* lp, const double* ll_tmp,
-                            const double* lp_tmp, float* g, const float* g_tmp, const WeightArrays& w, int64_t N,
-                            int p, const int* flag, cudaStream_t st)
+cudaError_t launch_copyback(float* beta, const float* beta_tmp, float2* llq, float2* lpq, const float2* llq_tmp,
+                            const float2* lpq_tmp, float* g, const float* g_tmp, const WeightArrays& w, int64_t N, int p,
+                            const int* flag, cudaStream_t st)
 {
     // uniform weights after resampling: log(1/N), 1/N and round(2^31 / N), formed on the host
     const double wi = 1.0 / (double)N;
     const uint32_t wf = (uint32_t)std::llrint(wi * 2147483648.0);
-    k_copyback<<<elem_grid(N * p), 256, 0, st>>>(beta, beta_tmp, ll, lp, ll_tmp, lp_tmp, g, g_tmp, w, N, p, flag,
-                                                 -std::log((double)N), wi, wf);
+    const double lw = -std::log((double)N);
+    if ((p & 3) == 0)
+        k_copyback<true><<<warps_grid(N), BLOCK, 0, st>>>(beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
+                                                          flag, lw, wi, wf);
+    else
+        k_copyback<false><<<warps_grid(N), BLOCK, 0, st>>>(beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
+                                                           flag, lw, wi, wf);
     return cudaGetLastError();
 }
 

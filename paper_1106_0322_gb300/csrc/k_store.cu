@@ -59,9 +59,13 @@ __global__ void k_store_sums(const int8_t* __restrict__ G, const uint8_t* __rest
     }
 }
 
+// colf[0..p) = 1/s_j, colf[p..2p) = v_j and colf[2p..3p) = v_j log2(e) in FP32, where
+// v = X^T y is the coefficient vector of the linear half of the log-likelihood,
+// sum_i y_i eta_i = beta . v.
 __global__ void k_store_stats(int64_t n, int64_t p, const unsigned long long* __restrict__ sums,
                               double* __restrict__ mean, double* __restrict__ sd, double* __restrict__ v,
-                              float* __restrict__ l2e_over_s, float* __restrict__ mean_f, uint32_t* __restrict__ err)
+                              float* __restrict__ l2e_over_s, float* __restrict__ mean_f, float* __restrict__ colf,
+                              uint32_t* __restrict__ err)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= p) return;
@@ -78,9 +82,13 @@ __global__ void k_store_stats(int64_t n, int64_t p, const unsigned long long* __
     }
     mean[j] = m;
     sd[j] = s;
-    v[j] = (double)(nn * SY - NY * S1) / ((double)nn * s);
+    const double vj = (double)(nn * SY - NY * S1) / ((double)nn * s);
+    v[j] = vj;
     l2e_over_s[j] = (float)(LOG2E / s);
     mean_f[j] = (float)m;
+    colf[j] = (float)(1.0 / s);
+    colf[p + j] = (float)vj;
+    colf[2 * p + j] = (float)(vj * LOG2E);
 }
 
 // BF16 operand rows (g_i0..g_i,p-1, 1, 0 ... 0) of width Kp and the FP32 standardised X.
@@ -155,10 +163,10 @@ cudaError_t launch_store_sums(const int8_t* G, const uint8_t* y, int64_t n, int6
 }
 
 cudaError_t launch_store_finish(const int8_t* G, int64_t n, int64_t p, int Kp, const unsigned long long* sums,
-                                double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f,
+                                double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f, float* colf,
                                 __nv_bfloat16* Gbf, float* Xf, uint32_t* err, cudaStream_t st)
 {
-    k_store_stats<<<(unsigned)((p + 127) / 128), 128, 0, st>>>(n, p, sums, mean, sd, v, l2e_over_s, mean_f, err);
+    k_store_stats<<<(unsigned)((p + 127) / 128), 128, 0, st>>>(n, p, sums, mean, sd, v, l2e_over_s, mean_f, colf, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t total = n * (int64_t)Kp;

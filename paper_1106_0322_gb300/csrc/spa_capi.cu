@@ -2,16 +2,20 @@
 //
 // A context owns one region's genotype store and the device workspace of its sweeps.
 // spa_run enqueues the whole sweep -- init, then per scale step: reweight, log-sum-exp /
-// ESS, conditional resampling, proposal scales, M x (propose, likelihood, accept),
-// summaries -- on one stream, captures it once into a CUDA graph keyed by
+// ESS, conditional resampling, proposal scales, M x (MH test of the previous move fused with
+// the next proposal, likelihood), the last MH test with its commit, summaries -- on one stream, captures it once into a CUDA graph keyed by
 // (T, N, M, config), and replays the graph for later sweeps of the same shape. The
 // schedule and the seed live in device memory, so a replay only re-uploads them.
 // Decisions that depend on data (resample or not) are taken on the device (a flag the
 // resampling kernels read), so the host never waits inside a sweep.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -52,11 +56,14 @@ struct Workspace {
     float *beta = nullptr, *beta_p = nullptr, *scale = nullptr;
     __nv_bfloat16* A = nullptr;
     CUtensorMap mapA;
+    int BN = 0;               // n-tile width of the likelihood kernel (tuned per shape)
     float2* lpt_p = nullptr;  // compensated log-prior term sums of the proposals
-    double *ll = nullptr, *lp = nullptr, *logw = nullptr, *W = nullptr;
+    float2* ydq = nullptr;    // the proposals' linear log-likelihood term beta' . v
+    float2 *llq = nullptr, *lpq = nullptr, *llq_tmp = nullptr, *lpq_tmp = nullptr;  // MH state pairs
+    double *ll = nullptr, *logw = nullptr, *W = nullptr;  // ll: FP64 log-likelihood output of the entry points
     float* Wf = nullptr;
     uint32_t* wfix = nullptr;
-    double *ll_tmp = nullptr, *lp_tmp = nullptr, *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
+    double *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
     unsigned int* lse_counter = nullptr;
     float4* colpart = nullptr;
     float* h = nullptr;  // MALA step h = lambda p^(-1/6)
@@ -123,6 +130,7 @@ struct spa_ctx {
     unsigned long long* sums = nullptr;
     double *mean = nullptr, *sd = nullptr, *v = nullptr, *unit_c = nullptr;
     float *l2e_s = nullptr, *mean_f = nullptr, *Xf = nullptr;
+    float* colf = nullptr;  // [3p]: 1/s_j, v_j, v_j log2(e) (FP32)
     __nv_bfloat16* Gbf = nullptr;
     CUtensorMap mapB;
     int mapB_BN = 0;
@@ -138,6 +146,7 @@ struct spa_ctx {
     RunBufs rb;
     cudaGraphExec_t gexec = nullptr;
     GraphKey gkey;
+    uint64_t gen = 0;  // bumped whenever captured work may refer to stale buffers or config
     int64_t graph_launches = 0;
     int64_t last_launches = 0;
 
@@ -206,12 +215,13 @@ int read_error_word(spa_ctx* c)
 void free_workspace(Workspace& w)
 {
     dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
-    dfree(w.lpt_p); dfree(w.ll); dfree(w.lp); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix);
-    dfree(w.ll_tmp); dfree(w.lp_tmp); dfree(w.cum); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
+    dfree(w.lpt_p); dfree(w.ydq); dfree(w.llq); dfree(w.lpq); dfree(w.llq_tmp); dfree(w.lpq_tmp);
+    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
     dfree(w.lse_scratch); dfree(w.lse_counter);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
     dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
     w.N = w.N_pad = 0;
+    w.BN = 0;
 }
 
 void free_runbufs(RunBufs& r)
@@ -221,10 +231,13 @@ void free_runbufs(RunBufs& r)
     r.T = 0;
 }
 
-void drop_graph(spa_ctx* c)
+// Drop the context's own sweep graph. bump: the buffers or the config it used are about
+// to change, so graphs of batches holding this context become stale too.
+void drop_graph(spa_ctx* c, bool bump = true)
 {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
+    if (bump) ++c->gen;
     c->gkey = GraphKey();
 }
 
@@ -237,6 +250,67 @@ int ensure_mapB(spa_ctx* c, int BN)
     return SPA_OK;
 }
 
+// ----------------------------------------------------------- likelihood tile tuner
+// The n-tile width of the likelihood kernel (128 or 256 individuals) sets how evenly the
+// (particle-tile, n-tile) units spread over the SMs and how often each particle tile is
+// streamed again. Each shape (device, N_pad, n, p) is timed once per process with both
+// widths on the context's stream (3 warm-up and 10 timed launches each, CUDA events) and
+// the faster one is kept. The result does not depend on the choice: the partial sums are
+// per 32-individual chunk whatever the width.
+int tune_bn(spa_ctx* c)
+{
+    Workspace& w = c->ws;
+    if (c->n <= 128) return 128;
+    // SPA_LOGLIK_BN=128|256 fixes the width instead (reproducible profiles and comparisons)
+    if (const char* env = std::getenv("SPA_LOGLIK_BN")) {
+        const int v = std::atoi(env);
+        if (v == 128 || v == 256) return v;
+    }
+    static std::mutex mu;
+    static std::map<std::tuple<int, int64_t, int64_t, int64_t>, int> cache;
+    const auto key = std::make_tuple(c->device, w.N_pad, c->n, c->p);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    cudaStream_t st = c->stream();
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 256;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return 256;
+    }
+    int best = 256;
+    float best_ms = -1.0f;
+    for (int BN : {128, 256}) {
+        CUtensorMap mB;
+        if (!tc_make_map_B(&mB, c->Gbf, c->n, c->Kp, BN)) continue;
+        const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, BN);
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+            e = launch_loglik_tc(w.mapA, mB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+        for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+            e = launch_loglik_tc(w.mapA, mB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) continue;
+        if (best_ms < 0.0f || ms < best_ms) {
+            best_ms = ms;
+            best = BN;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = best;
+    return best;
+}
+
 int ensure_workspace(spa_ctx* c, int64_t N)
 {
     Workspace& w = c->ws;
@@ -245,7 +319,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     free_workspace(w);
     const int64_t p = c->p;
     const int64_t N_pad = round_up(N, 128);
-    const TcPlan plan = tc_plan(c->n, (int)p, N_pad, c->num_sms);
+    const TcPlan plan = tc_plan(c->n, (int)p, N_pad, c->num_sms);  // n_parts does not depend on BN
     const int64_t simt_parts = (c->n + SIMT_TILE_N - 1) / SIMT_TILE_N;
     const int64_t parts = plan.n_parts > simt_parts ? plan.n_parts : simt_parts;
     const int64_t nblk = (N + 255) / 256;
@@ -256,8 +330,8 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     WA(beta_p, N * p);
     WA(scale, p);
     WA(A, N_pad * 2 * c->Kp);
-    WA(lpt_p, N); WA(ll, N); WA(lp, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
-    WA(ll_tmp, N); WA(lp_tmp, N);
+    WA(lpt_p, N); WA(ydq, N); WA(llq, N); WA(lpq, N); WA(llq_tmp, N); WA(lpq_tmp, N);
+    WA(ll, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
     WA(cum, N + nblk + 1);
     WA(colpart, (int64_t)COLSTAT_SPLITS * p);
     WA(lambda, 1);
@@ -281,11 +355,10 @@ int ensure_workspace(spa_ctx* c, int64_t N)
         free_workspace(w);
         return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the particle operand");
     }
-    int rc = ensure_mapB(c, plan.BN);
-    if (rc != SPA_OK) return rc;
     w.N = N;
     w.N_pad = N_pad;
-    return SPA_OK;
+    w.BN = tune_bn(c);
+    return ensure_mapB(c, w.BN);
 }
 
 int ensure_adjoint_buffers(spa_ctx* c)
@@ -377,17 +450,19 @@ struct Enq {
 // gradient of the log-likelihood at the packed particles (beta_p / A) into out, on the
 // tensor cores: residual likelihood pass, C = R G, finish. Also leaves the softplus
 // partials of those particles in w.partial.
+TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, c->num_sms, c->ws.BN); }
+
 void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
 {
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
-    const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
+    const TcPlan plan = plan_of(c);
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     ResidArgs ra{w.R, a.n_r, w.rsum};
     q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra));
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st));
-    q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean, c->sd, Bsrc, c->pr,
-                            cs, out, q.st));
+    q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
+                            c->pr, cs, out, q.st));
 }
 
 // log-likelihood of the current proposals (beta_p) into the partial sums
@@ -396,68 +471,91 @@ void enq_loglik(Enq& q)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-        const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
-        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
+        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
     } else {
         q.ck(launch_loglik_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
     }
 }
 
-AcceptArgs accept_args(spa_ctx* c, unsigned long long* acc)
+// MH state of the context's particles; partial units are ln 2 * nats on the tensor-core
+// path and nats on the FP32 path.
+MhState mh_state(spa_ctx* c, unsigned long long* acc)
 {
     Workspace& w = c->ws;
-    AcceptArgs a;
+    const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
+    MhState m;
+    m.llq = w.llq;
+    m.lpq = w.lpq;
+    m.lpt_p = w.lpt_p;
+    m.ydq = w.ydq;
+    m.partial = w.partial;
+    m.n_parts = tc ? plan_of(c).n_parts : (int)((c->n + SIMT_TILE_N - 1) / SIMT_TILE_N);
+    m.ld_part = w.N_pad;
+    m.sp_scale_d = tc ? LN2 : 1.0;
+    m.sp_scale = (float)m.sp_scale_d;
+    m.acc_count = acc;
+    return m;
+}
+
+MoveArgs move_args(spa_ctx* c, unsigned long long* acc)
+{
+    Workspace& w = c->ws;
+    const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
+    MoveArgs a;
     a.beta = w.beta;
     a.beta_p = w.beta_p;
-    a.ll = w.ll;
-    a.lp = w.lp;
+    a.A = tc ? w.A : nullptr;
+    a.ldA = 2 * c->Kp;
+    a.Kp = c->Kp;
     a.lpt_p = w.lpt_p;
-    a.partial = w.partial;
-    if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-        a.n_parts = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms).n_parts;
-        a.sp_scale = LN2;
-    } else {
-        a.n_parts = (int)((c->n + SIMT_TILE_N - 1) / SIMT_TILE_N);
-        a.sp_scale = 1.0;
-    }
-    a.ld_part = w.N_pad;
-    a.logw = nullptr;
-    a.acc_count = acc;
+    a.ydq = w.ydq;
+    a.sigma = w.scale;
+    a.l2e_over_s = c->l2e_s;
+    a.mean_f = c->mean_f;
+    a.vy = c->colf + (tc ? 2 : 1) * c->p;
+    a.mh = mh_state(c, acc);
+    a.gl = w.gl;
+    a.gl_p = w.gl_p;
+    a.fwd = w.fwd;
+    a.h = w.h;
     return a;
 }
 
-void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
+// The proposals' log-likelihood partials (and, for MALA, their gradients into gl_p).
+void enq_proposal_likelihood(Enq& q, bool mala)
 {
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
-    const bool tc = c->cfg.precision == SPA_PREC_SPLIT_BF16;
-    const AcceptArgs a = accept_args(c, acc);
-    if (c->cfg.move_kind == SPA_MOVE_MALA) {
-        for (int mm = 0; mm < M; ++mm) {
-            const uint32_t m = m0 + (uint32_t)mm;
-            q.ck(launch_propose_mala(w.beta, w.gl, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.fwd,
-                                     w.scale, w.h, c->l2e_s, c->mean_f, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
-                                     c->rb.seed, q.st));
-            if (tc) {
-                enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
-            } else {
-                enq_loglik(q);
-                q.ck(launch_grad_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.eta, w.gl_p, nullptr, c->pr, 0.0,
-                                      q.st));
-                ++q.launches;  // the plain adjoint is two kernels
-            }
-            q.ck(launch_accept_mala(a, w.gl, w.gl_p, w.fwd, w.scale, w.h, w.N, (int)c->p, c->pr, c->rb.sched, t, m,
-                                    c->rb.seed, c->d_err, q.st));
-        }
-        return;
+    if (!mala) {
+        enq_loglik(q);
+    } else if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
+    } else {
+        enq_loglik(q);
+        q.ck(launch_grad_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.eta, w.gl_p, nullptr, c->pr, 0.0, q.st));
+        ++q.launches;  // the plain adjoint is two kernels
     }
+}
+
+// M moves at step t with move indices m0 .. m0+M-1: the MH test of move m runs inside the
+// proposal kernel of move m+1, the last one in the commit kernel.
+void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
+{
+    if (M <= 0) return;
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
+    const MoveArgs a = move_args(c, acc);
+    const int p = (int)c->p;
     for (int mm = 0; mm < M; ++mm) {
         const uint32_t m = m0 + (uint32_t)mm;
-        q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
-                               c->mean_f, w.N, (int)c->p, c->pr, c->rb.sched, t, m, c->rb.seed, 1, q.st));
-        enq_loglik(q);
-        q.ck(launch_accept(a, w.N, (int)c->p, c->pr, c->rb.sched, 1, t, m, c->rb.seed, c->d_err, q.st));
+        if (mala)
+            q.ck(launch_move_mala(a, mm > 0, w.N, p, c->pr, c->rb.sched, t, m, m - 1u, c->rb.seed, c->d_err, q.st));
+        else
+            q.ck(launch_move_rw(a, mm > 0, w.N, p, c->pr, c->rb.sched, t, m, m - 1u, c->rb.seed, 1, c->d_err, q.st));
+        enq_proposal_likelihood(q, mala);
     }
+    q.ck(launch_move_commit(a, mala, w.N, p, c->pr, c->rb.sched, t, m0 + (uint32_t)(M - 1), c->rb.seed, c->d_err, q.st));
 }
 
 void enq_resample(Enq& q, int t)
@@ -467,11 +565,11 @@ void enq_resample(Enq& q, int t)
     q.ck(launch_resample_index(w.W, w.N, w.cum, w.idx, w.flag, t, c->rb.seed, 0.0, q.st));
     ++q.launches;  // scan + search
     const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
-    q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr,
+    q.ck(launch_gather(w.idx, w.beta, w.beta_p, w.llq, w.lpq, w.llq_tmp, w.lpq_tmp, mala ? w.gl : nullptr,
                        mala ? w.gl_p : nullptr, w.N, (int)c->p, w.flag, q.st));
     WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
-    q.ck(launch_copyback(w.beta, w.beta_p, w.ll, w.lp, w.ll_tmp, w.lp_tmp, mala ? w.gl : nullptr, mala ? w.gl_p : nullptr,
-                         wa, w.N, (int)c->p, w.flag, q.st));
+    q.ck(launch_copyback(w.beta, w.beta_p, w.llq, w.lpq, w.llq_tmp, w.lpq_tmp, mala ? w.gl : nullptr,
+                         mala ? w.gl_p : nullptr, wa, w.N, (int)c->p, w.flag, q.st));
 }
 
 void enq_colstats(Enq& q, int t)
@@ -509,8 +607,8 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
     // t = 0: prior draws, their log-likelihoods, importance weights
     q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
-    q.ck(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
-                           c->mean_f, w.N, p, c->pr, r.sched, 0, 0u, r.seed, 0, q.st));
+    const MoveArgs a0 = move_args(c, nullptr);
+    q.ck(launch_move_rw(a0, false, w.N, p, c->pr, r.sched, 0, 0u, 0u, r.seed, 0, c->d_err, q.st));
     if (mala && tc) {
         enq_grad_tc(q, w.gl, w.beta, 0.0, w.N);  // also leaves the softplus partials of the draws
     } else {
@@ -520,9 +618,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
             ++q.launches;
         }
     }
-    AcceptArgs a0 = accept_args(c, nullptr);
-    a0.logw = w.logw;
-    q.ck(launch_accept(a0, w.N, p, c->pr, r.sched, 0, 0, 0u, r.seed, c->d_err, q.st));
+    q.ck(launch_finish_loglik(a0.mh, w.N, w.logw, nullptr, c->d_err, q.st));
     const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
     q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
                         c->d_err, q.st));
@@ -542,7 +638,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     }
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0) {
-            q.ck(launch_reweight(w.beta, w.logw, w.lp, w.N, p, c->pr, r.sched, (int)t, c->d_err, q.st));
+            q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.sched, (int)t, c->d_err, q.st));
             q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
                                 c->d_err, q.st));
             ++q.launches;
@@ -584,8 +680,8 @@ int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
     CK(cudaMemsetAsync(c->sums, 0, sizeof(unsigned long long) * (size_t)(3 * p + 1), st), "memset sums");
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st), "memset err");
     CK(launch_store_sums(c->G, c->y, n, p, c->sums, c->d_err, st), "store sums");
-    CK(launch_store_finish(c->G, n, p, c->Kp, c->sums, c->mean, c->sd, c->v, c->l2e_s, c->mean_f, c->Gbf, c->Xf, c->d_err,
-                           st),
+    CK(launch_store_finish(c->G, n, p, c->Kp, c->sums, c->mean, c->sd, c->v, c->l2e_s, c->mean_f, c->colf, c->Gbf, c->Xf,
+                           c->d_err, st),
        "store pack");
     CK(launch_store_pack_t(c->G, c->y, n, p, c->n_r, c->GT, c->yv, st), "store pack transposed");
     CK(launch_store_ybits(c->y, n, c->ywords, c->ybits, st), "store y bits");
@@ -599,10 +695,114 @@ void destroy(spa_ctx* c)
     free_workspace(c->ws);
     free_runbufs(c->rb);
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
-    dfree(c->l2e_s); dfree(c->mean_f); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
+    dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
     dfree(c->ybits);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ batches
+struct spa_batch {
+    std::vector<spa_ctx*> ctxs;
+    std::vector<uint64_t> gens, seeds;
+    std::vector<int64_t> T, per_ctx_launches;
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+};
+
+namespace {
+
+void batch_free(spa_batch* b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaEvent_t ev : b->joins)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->st) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+// Prepare every context (buffers, schedule, seed), then capture all sweeps into one graph:
+// the batch stream forks to each context's stream, each context enqueues its sweep there,
+// and the batch stream joins them all.
+int batch_build(spa_batch* b, spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args)
+{
+    for (int32_t r = 0; r < R; ++r) {
+        spa_ctx* c = ctxs[r];
+        const int64_t T = args->T[r], N = args->N[r];
+        const int32_t M = args->moves_per_step[r];
+        const double* sched = args->schedules[r];
+        auto bad = [&](const char* what) {
+            set_thread_error_str("region " + std::to_string(r) + ": " + what);
+            return SPA_EINVAL;
+        };
+        if (!sched) return bad("schedule is NULL");
+        if (T < 1 || T > (int64_t)1 << 24) return bad("T out of range");
+        if (N < 1 || N > (int64_t)1 << 22) return bad("N out of range");
+        if (M < 0 || M > 65535) return bad("moves_per_step out of range");
+        for (int64_t t = 0; t < T; ++t)
+            if (!(sched[t] > 0.0) || !std::isfinite(sched[t])) return bad("schedule values must be finite and > 0");
+        int rc = validate_config(c, c->cfg);
+        if (rc == SPA_OK) rc = ensure_workspace(c, N);
+        if (rc == SPA_OK) rc = ensure_runbufs(c, T);
+        if (rc == SPA_OK && c->cfg.move_kind == SPA_MOVE_MALA) rc = ensure_mala_buffers(c);
+        if (rc == SPA_OK) {
+            cudaError_t e = cudaMemcpyAsync(c->rb.sched, sched, sizeof(double) * (size_t)T, cudaMemcpyHostToDevice,
+                                            c->stream());
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream());
+            if (e != cudaSuccess) rc = cuda_fail(c, e, "copy schedule");
+        }
+        if (rc != SPA_OK) {
+            set_thread_error_str("region " + std::to_string(r) + ": " + c->err);
+            return rc;
+        }
+        b->ctxs.push_back(c);
+        b->T.push_back(T);
+        b->seeds.push_back(args->seeds[r]);
+    }
+    auto cuda_err = [&](cudaError_t e, const char* what) {
+        set_thread_error_str(std::string("batch: ") + what + ": " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA;
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    b->joins.assign((size_t)R, nullptr);
+    for (int32_t r = 0; r < R && e == cudaSuccess; ++r) e = cudaEventCreateWithFlags(&b->joins[r], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_err(e, "stream and events");
+    e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(e, "begin capture");
+    cudaError_t ee = cudaEventRecord(b->fork, b->st);
+    b->launches = 0;
+    for (int32_t r = 0; r < R && ee == cudaSuccess; ++r) {
+        spa_ctx* c = b->ctxs[r];
+        ee = cudaStreamWaitEvent(c->stream(), b->fork, 0);
+        if (ee != cudaSuccess) break;
+        const int64_t n = enqueue_sweep(c, b->T[r], args->moves_per_step[r], &ee);
+        b->per_ctx_launches.push_back(n);
+        b->launches += n;
+        if (ee == cudaSuccess) ee = cudaEventRecord(b->joins[r], c->stream());
+        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(b->st, b->joins[r], 0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(b->st, &g);
+    if (ee != cudaSuccess || ec != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_err(ee != cudaSuccess ? ee : ec, "capture");
+    }
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_err(e, "graph instantiate");
+    }
+    for (int32_t r = 0; r < R; ++r) b->gens.push_back(b->ctxs[r]->gen);
+    return SPA_OK;
 }
 
 }  // namespace
@@ -661,7 +861,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     CA(y, n);
     CA(sums, 3 * p + 1);
     CA(mean, p); CA(sd, p); CA(v, p); CA(unit_c, 1);
-    CA(l2e_s, p); CA(mean_f, p);
+    CA(l2e_s, p); CA(mean_f, p); CA(colf, 3 * p);
     CA(Xf, n * p);
     CA(Gbf, n * c->Kp);
     c->n_r = round_up(n, 64);
@@ -727,6 +927,8 @@ const char* spa_last_error(const spa_ctx* c)
 
 int64_t spa_last_launch_count(const spa_ctx* c) { return c ? c->last_launches : 0; }
 
+int spa_loglik_tile_width(const spa_ctx* c) { return (c && c->ws.N > 0) ? c->ws.BN : 0; }
+
 static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int64_t T, int64_t N, int32_t M,
                       uint64_t seed)
 {
@@ -759,7 +961,7 @@ static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int
     key.M = M;
     key.cfg = c->cfg;
     if (!c->gexec || !(key == c->gkey)) {
-        drop_graph(c);
+        drop_graph(c, false);  // buffers and config were settled above
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t ee = cudaSuccess;
@@ -836,43 +1038,87 @@ int spa_sync(spa_ctx* c)
     return read_error_word(c);
 }
 
-int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_result* outs)
+int spa_batch_create(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_batch** out)
 {
-    if (!ctxs || !args || R < 0) return fail(nullptr, SPA_EINVAL, "bad batch arguments");
+    if (!out) return fail(nullptr, SPA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || !args || R < 1 || !args->schedules || !args->T || !args->N || !args->moves_per_step || !args->seeds)
+        return fail(nullptr, SPA_EINVAL, "bad batch arguments");
     for (int32_t r = 0; r < R; ++r) {
-        spa_ctx* c = ctxs[r];
-        int rc = run_common(c, args->schedules[r], false, args->T[r], args->N[r], args->moves_per_step[r], args->seeds[r]);
-        if (rc != SPA_OK) {
-            set_thread_error_str(c ? c->err : std::string("NULL context"));
-            return rc;
-        }
+        if (!ctxs[r]) return fail(nullptr, SPA_EINVAL, "NULL context in batch");
+        for (int32_t q = 0; q < r; ++q)
+            if (ctxs[q] == ctxs[r]) return fail(nullptr, SPA_EINVAL, "a context appears twice in the batch");
     }
-    for (int32_t r = 0; r < R; ++r) {
-        spa_ctx* c = ctxs[r];
-        cudaStream_t st = c->stream();
-        const int64_t T = args->T[r], p = c->p;
+    spa_batch* b = new (std::nothrow) spa_batch();
+    if (!b) return fail(nullptr, SPA_ENOMEM, "host allocation");
+    int rc = batch_build(b, ctxs, R, args);
+    if (rc != SPA_OK) {
+        batch_free(b);
+        return rc;
+    }
+    *out = b;
+    return SPA_OK;
+}
+
+int spa_batch_run(spa_batch* b, const uint64_t* seeds, spa_result* outs)
+{
+    if (!b || !b->exec) return fail(nullptr, SPA_EINVAL, "batch is NULL");
+    const int32_t R = (int32_t)b->ctxs.size();
+    for (int32_t r = 0; r < R; ++r)
+        if (b->ctxs[r]->gen != b->gens[r])
+            return fail(nullptr, SPA_EINVAL, "a context's workspace or config changed since the batch was created");
+    if (seeds)
+        for (int32_t r = 0; r < R; ++r) b->seeds[r] = seeds[r];
+    cudaStream_t st = b->st;
+    cudaError_t e = cudaSuccess;
+    for (int32_t r = 0; r < R && e == cudaSuccess; ++r)
+        e = cudaMemcpyAsync(b->ctxs[r]->rb.seed, &b->seeds[r], sizeof(uint64_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st);
+    for (int32_t r = 0; r < R && e == cudaSuccess && outs; ++r) {
+        spa_ctx* c = b->ctxs[r];
+        const RunBufs& rb = c->rb;
+        const int64_t T = b->T[r], p = c->p;
         const int nq = c->cfg.n_quantiles, nd = c->cfg.n_deltas;
-        RunBufs& rb = c->rb;
-        spa_result* out = outs ? &outs[r] : nullptr;
-        if (out) {
-            auto d2h = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
-                return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
-            };
-            CK(d2h(out->mean, rb.mean, sizeof(double) * (size_t)(T * p)), "copy mean");
-            CK(d2h(out->quantile, rb.quant, sizeof(double) * (size_t)(T * p * nq)), "copy quantiles");
-            CK(d2h(out->conc, rb.conc, sizeof(double) * (size_t)(T * p * nd)), "copy concentrations");
-            CK(d2h(out->ess, rb.ess, sizeof(double) * (size_t)T), "copy ess");
-            CK(d2h(out->log_z_inc, rb.logz, sizeof(double) * (size_t)T), "copy log z");
-            CK(d2h(out->accept_rate, rb.accrate, sizeof(double) * (size_t)T), "copy acceptance");
-            CK(d2h(out->resampled, rb.res, (size_t)T), "copy resampled");
-        }
-        int rc = read_error_word(c);
+        spa_result* o = &outs[r];
+        auto d2h = [&](void* dst, const void* src, size_t bytes) {
+            if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st);
+        };
+        d2h(o->mean, rb.mean, sizeof(double) * (size_t)(T * p));
+        d2h(o->quantile, rb.quant, sizeof(double) * (size_t)(T * p * nq));
+        d2h(o->conc, rb.conc, sizeof(double) * (size_t)(T * p * nd));
+        d2h(o->ess, rb.ess, sizeof(double) * (size_t)T);
+        d2h(o->log_z_inc, rb.logz, sizeof(double) * (size_t)T);
+        d2h(o->accept_rate, rb.accrate, sizeof(double) * (size_t)T);
+        d2h(o->resampled, rb.res, (size_t)T);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(nullptr, e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA,
+                                      std::string("batch run: ") + cudaGetErrorString(e));
+    for (int32_t r = 0; r < R; ++r) {
+        spa_ctx* c = b->ctxs[r];
+        c->last_launches = b->per_ctx_launches[r];
+        const int rc = read_error_word(c);
         if (rc != SPA_OK) {
-            set_thread_error_str(c->err);
+            set_thread_error_str("region " + std::to_string(r) + ": " + c->err);
             return rc;
         }
     }
     return SPA_OK;
+}
+
+int64_t spa_batch_launch_count(const spa_batch* b) { return b ? b->launches : 0; }
+
+void spa_batch_destroy(spa_batch* b) { batch_free(b); }
+
+int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, spa_result* outs)
+{
+    if (R == 0 && ctxs && args) return SPA_OK;
+    spa_batch* b = nullptr;
+    int rc = spa_batch_create(ctxs, R, args, &b);
+    if (rc != SPA_OK) return rc;
+    rc = spa_batch_run(b, nullptr, outs);
+    spa_batch_destroy(b);
+    return rc;
 }
 
 // ------------------------------------------------------------ per-step entry points
@@ -890,19 +1136,15 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
     CK(cudaMemcpyAsync(w.beta, B, sizeof(float) * (size_t)(N * p), B_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        st),
        "copy B");
-    CK(launch_propose_rw(w.beta, w.beta_p, tc ? w.A : nullptr, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s,
-                         c->mean_f, N, (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st),
-       "pack");
+    const MoveArgs a = move_args(c, nullptr);
+    CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_c, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
     if (tc) {
-        const TcPlan plan = tc_plan(c->n, (int)p, w.N_pad, c->num_sms);
-        CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st), "loglik tc");
+        CK(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+           "loglik tc");
     } else {
         CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
     }
-    AcceptArgs a = accept_args(c, nullptr);
-    a.ll = ll_dev ? ll : w.ll;
-    a.lp = nullptr;
-    CK(launch_accept(a, N, (int)p, c->pr, c->unit_c, 0, 0, 0u, nullptr, c->d_err, st), "finish loglik");
+    CK(launch_finish_loglik(a.mh, N, nullptr, ll_dev ? ll : w.ll, c->d_err, st), "finish loglik");
     if (!ll_dev) CK(cudaMemcpyAsync(ll, w.ll, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st), "copy ll");
     if (st != c->stream()) CK(cudaStreamSynchronize(st), "sync");
     return read_error_word(c);
@@ -916,8 +1158,7 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
     Workspace& w = c->ws;
     for (int32_t k = 0; k < reps; ++k) {
         if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-            const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms);
-            CK(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+            CK(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
                "loglik tc");
         } else {
             CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");
@@ -961,13 +1202,10 @@ static int grad_impl(spa_ctx* c, const float* B, bool dev, int64_t N, double cs,
         Enq q;
         q.c = c;
         q.st = st;
-        q.ck(launch_propose_rw(w.beta, w.beta_p, w.A, 2 * c->Kp, c->Kp, w.lpt_p, w.scale, c->l2e_s, c->mean_f, N,
-                               (int)p, c->pr, c->unit_c, 0, 0u, nullptr, 0, st));
+        const MoveArgs a = move_args(c, nullptr);
+        q.ck(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_c, 0, 0u, 0u, nullptr, 0, c->d_err, st));
         enq_grad_tc(q, dev ? grad : w.grad, w.beta, cs, N);
-        AcceptArgs a = accept_args(c, nullptr);
-        a.ll = (dev && ll) ? ll : w.ll;
-        a.lp = nullptr;
-        q.ck(launch_accept(a, N, (int)p, c->pr, c->unit_c, 0, 0, 0u, nullptr, c->d_err, st));
+        q.ck(launch_finish_loglik(a.mh, N, nullptr, (dev && ll) ? ll : w.ll, c->d_err, st));
         if (q.e != cudaSuccess) return cuda_fail(c, q.e, "gradient (tensor cores)");
         if (!dev) {
             CK(cudaMemcpyAsync(grad, w.grad, sizeof(float) * (size_t)(N * p), cudaMemcpyDeviceToHost, st), "copy grad");
@@ -1085,7 +1323,7 @@ int spa_incr_weight(double nu, double c_prev, double c_new, const float* B, int6
     Scratch s;
     float* dB = s.get<float>(N * p);
     double* dW = s.get<double>(N);
-    double* dL = s.get<double>(N);
+    float2* dL = s.get<float2>(N);
     double* dS = s.get<double>(2);
     uint32_t* dE = s.get<uint32_t>(1);
     if (!dB || !dW || !dL || !dS || !dE) return fail(nullptr, SPA_ENOMEM, "device allocation");

@@ -27,7 +27,7 @@ cudaError_t launch_store_sums(const int8_t* G, const uint8_t* y, int64_t n, int6
 // FP32 constants; the BF16 GEMM operand [n][Kp] = (g_i0..g_i,p-1, 1, 0...); the FP32
 // standardised X [n][p].
 cudaError_t launch_store_finish(const int8_t* G, int64_t n, int64_t p, int Kp, const unsigned long long* sums,
-                                double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f,
+                                double* mean, double* sd, double* v, float* l2e_over_s, float* mean_f, float* colf,
                                 __nv_bfloat16* Gbf, float* Xf, uint32_t* err, cudaStream_t st);
 
 cudaError_t launch_store_pack_t(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, int64_t n_r,
@@ -56,51 +56,70 @@ struct WeightArrays {
 cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const double* sched, int t0,
                               const uint64_t* seed, cudaStream_t st);
 
-// Random-walk proposal (noise = 1) or plain packing of beta (noise = 0): writes beta_p, the
-// compensated sum of the proposal's log-prior terms (log1p(|b|/(a c)), or |b| for the double
-// exponential) to lpt_p, and (A != NULL) the split-BF16 GEMM row [hi(bt) | lo(bt)] with
-// bt_j = beta'_j log2(e)/s_j and the offset o = -sum_j m_j bt_j in column p.
-cudaError_t launch_propose_rw(const float* beta, float* beta_p, __nv_bfloat16* A, int ldA, int Kp, float2* lpt_p,
-                              const float* sigma, const float* l2e_over_s, const float* mean_f, int64_t N, int p,
-                              PriorArgs pr, const double* sched, int t, uint32_t m, const uint64_t* seed, int noise,
-                              cudaStream_t st);
-
-// Finish log-likelihoods from the GEMM partial sums (l = sp_scale * sum of partials) and
-// log-priors from lpt_p (without the constant -p log(2c), which cancels at a fixed scale),
-// then store them (mode 0) or run the Metropolis-Hastings test (mode 1).
-struct AcceptArgs {
-    float* beta;
-    const float* beta_p;
-    double* ll;
-    double* lp;
-    const float2* lpt_p;
-    const float* partial;
+// ------------------------------------------------------------- moves
+// A move is a proposal for every particle (beta' in beta_p, its GEMM row in A), the GEMM
+// for the proposals' log-likelihood partials, and the Metropolis-Hastings test. The test of
+// move m runs at the start of move m+1's proposal kernel (the accepted proposal is written
+// back as the state while it is read), and the last move of a step ends with a commit
+// kernel, so that between steps beta (and gl) hold the particles.
+//
+// Log-likelihoods and log-priors in the MH test are compensated FP32 pairs (s, c), value
+// s + c: llq in partial units (ln 2 * nats for the tensor-core path, nats for the FP32
+// path) and lpq = sum_j log1p(|b_j|/(a c_t)) (Gt) or sum_j |b_j| (double exponential) at
+// the current scale; log alpha = sp_scale (l' - l) + coef(c_t) (q' - q) with
+// coef = -(a+1) or -1/c, formed in FP32 from the pairs.
+struct MhState {
+    float2* llq;               // current log-likelihood pair (partial units)
+    float2* lpq;               // current log-prior term sum pair at c_t
+    const float2* lpt_p;       // proposal's log-prior term sum pair
+    const float2* ydq;         // proposal's linear term y . eta (partial units)
+    const float* partial;      // proposal's softplus partials [n_parts][ld_part]
     int n_parts;
     int64_t ld_part;
-    double sp_scale;
-    double* logw;                    // mode 0: logw = ll (prior-IS weights); may be NULL
-    unsigned long long* acc_count;  // mode 1: accepted-proposal counter; may be NULL
+    float sp_scale;            // natural-log units per partial unit
+    double sp_scale_d;         // the same in FP64 (for the log-weights)
+    unsigned long long* acc_count;
 };
-cudaError_t launch_accept(const AcceptArgs& a, int64_t N, int p, PriorArgs pr, const double* sched, int mode, int t,
-                          uint32_t m, const uint64_t* seed, uint32_t* err, cudaStream_t st);
 
-// MALA proposal (needs grad l at beta in gl, D_j from launch_colstats kind 1, lambda on the
-// device) and its MH test with the Langevin q-correction; accepted rows move beta and gl.
-// h = lambda p^{-1/6} comes from launch_colstats (h_out). fwd receives the compensated sum
-// of (beta' - beta - drift)^2 / D per particle.
-cudaError_t launch_propose_mala(const float* beta, const float* gl, float* beta_p, __nv_bfloat16* A, int ldA, int Kp,
-                                float2* lpt_p, float2* fwd, const float* D, const float* h, const float* l2e_over_s,
-                                const float* mean_f, int64_t N, int p, PriorArgs pr, const double* sched, int t,
-                                uint32_t m, const uint64_t* seed, cudaStream_t st);
-cudaError_t launch_accept_mala(const AcceptArgs& a, float* gl, const float* gl_p, const float2* fwd, const float* D,
-                               const float* h, int64_t N, int p, PriorArgs pr, const double* sched, int t, uint32_t m,
-                               const uint64_t* seed, uint32_t* err, cudaStream_t st);
+struct MoveArgs {
+    float* beta;                 // particle states
+    float* beta_p;               // proposals
+    __nv_bfloat16* A;            // GEMM rows, NULL on the FP32 path
+    int ldA, Kp;
+    float2* lpt_p;
+    float2* ydq;
+    const float* sigma;          // RW: per-coordinate step; MALA: D_j
+    const float* l2e_over_s;
+    const float* mean_f;
+    const float* vy;             // v_j in partial units (y . eta = beta . v)
+    MhState mh;
+    // MALA only
+    float* gl;                   // grad l of the states
+    const float* gl_p;           // grad l of the proposals
+    float2* fwd;                 // forward-move residual sum of the proposals
+    const float* h;              // step size
+};
+
+// Random-walk move (decide: MH test of the pending proposal first; noise = 0: pack beta
+// unchanged, for the log-likelihood entry points and t = 0).
+cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                           uint32_t m, uint32_t m_prev, const uint64_t* seed, int noise, uint32_t* err, cudaStream_t st);
+// MALA move: needs grad l of the states in gl, D_j (sigma) and h from launch_colstats kind 1.
+cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                             uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st);
+// MH test of the pending proposals, then accepted rows (and gradients) into the state.
+cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+                               uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st);
+// The packed particles' log-likelihoods as the state (llq, lpq), and in FP64 to logw
+// (prior-IS weights) and/or ll_out; either may be NULL.
+cudaError_t launch_finish_loglik(const MhState& s, int64_t N, double* logw, double* ll_out, uint32_t* err,
+                                 cudaStream_t st);
 // lambda *= exp(acceptance - 0.574) (MALA step adaptation) and a device scalar store.
 cudaError_t launch_adapt_lambda(double* lam, const unsigned long long* acc, double denom, cudaStream_t st);
 cudaError_t launch_set_f64(double* ptr, double v, cudaStream_t st);
 
-// logw += log p(beta | c_t) - log p(beta | c_{t-1}); lp refreshed at c_t (without -p log(2c)).
-cudaError_t launch_reweight(const float* beta, double* logw, double* lp, int64_t N, int p, PriorArgs pr,
+// logw += log p(beta | c_t) - log p(beta | c_{t-1}); the log-prior pair lpq refreshed at c_t.
+cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_t N, int p, PriorArgs pr,
                             const double* sched, int t, uint32_t* err, cudaStream_t st);
 
 // Log-sum-exp and ESS of logw (per-CTA partial (max, sum e, sum e^2) combined in block order
@@ -122,12 +141,12 @@ cudaError_t launch_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* resa
 // *flag == 0. cum holds N + ceil(N/256) + 1 doubles.
 cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32_t* idx, const int* flag,
                                   int t, const uint64_t* seed, double u_override, cudaStream_t st);
-cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const double* ll,
-                          const double* lp, double* ll_tmp, double* lp_tmp, const float* g, float* g_tmp,
-                          int64_t N, int p, const int* flag, cudaStream_t st);
-cudaError_t launch_copyback(float* beta, const float* beta_tmp, double* ll, double* lp, const double* ll_tmp,
-                            const double* lp_tmp, float* g, const float* g_tmp, const WeightArrays& w, int64_t N,
-                            int p, const int* flag, cudaStream_t st);
+cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const float2* llq, const float2* lpq,
+                          float2* llq_tmp, float2* lpq_tmp, const float* g, float* g_tmp, int64_t N, int p,
+                          const int* flag, cudaStream_t st);
+cudaError_t launch_copyback(float* beta, const float* beta_tmp, float2* llq, float2* lpq, const float2* llq_tmp,
+                            const float2* lpq_tmp, float* g, const float* g_tmp, const WeightArrays& w, int64_t N, int p,
+                            const int* flag, cudaStream_t st);
 
 // Weighted column moments -> per-coordinate proposal scales. kind 0 (RW):
 // sigma_j = lam/sqrt(p) max(sd_j, floor c); kind 1 (MALA): D_j = max(var_j, (floor c)^2).
@@ -163,9 +182,9 @@ cudaError_t launch_prior_logpdf(PriorArgs pr, double c, const float* beta, int64
                                 cudaStream_t st);
 
 // ------------------------------------------------------------ likelihood
-// tcgen05 split-BF16 GEMM with the fused log-likelihood reduction: partial[(nt*2 + h)*N_pad + i]
-// receives the sum over the h-th half of n-tile nt of y_r eta2 - log2(1 + 2^eta2), eta2 =
-// eta log2(e), so that l = ln(2) * (sum of the partials).
+// tcgen05 split-BF16 GEMM with the fused softplus reduction: partial[c * N_pad + i] receives
+// -sum over the 32-individual chunk c of log2(1 + 2^eta2), eta2 = eta log2(e), so that
+// l = ln(2) * (sum of the partials + beta . v log2(e)) with v = X^T y.
 struct TcPlan {
     int BN;          // individuals per n-tile (128 or 256)
     int n_tiles;     // ceil(n / BN)
@@ -173,9 +192,10 @@ struct TcPlan {
     int kblocks;     // active 64-wide k-blocks of each half
     int ksteps;      // active 16-wide k-steps of each half: ceil((p+1)/16)
     int grid;        // persistent CTAs
-    int n_parts;     // partial sums per particle = 2 * n_tiles
+    int n_parts;     // partial sums per particle = ceil(n / 32), whatever BN
 };
-TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms);
+// BN = 128 or 256 picks the n-tile width (the tuner's choice); 0 picks by the size of n.
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN = 0);
 // Opt the tensor-core kernels into their dynamic shared memory (once per device, before any capture).
 cudaError_t tc_init_attributes();
 bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp);
@@ -204,11 +224,11 @@ bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p, float* gpart,
                               int64_t N_pad, uint32_t* err, cudaStream_t st);
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
-                               int64_t N, int p, const double* mean, const double* sd, const float* B, PriorArgs pr,
+                               int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st);
 
-// Plain FP32 SIMT path: partial[nt * N_pad + i] = sum over 64-individual tile nt of
-// y_r eta_r - softplus(eta_r) (natural units).
+// Plain FP32 SIMT path: partial[nt * N_pad + i] = -sum over 64-individual tile nt of
+// softplus(eta_r) (natural units; the linear half beta . v is added by the move kernels).
 constexpr int SIMT_TILE_N = 64;
 cudaError_t launch_loglik_simt(const float* beta_p, const float* Xf, const uint8_t* y, int64_t N, int64_t n, int p,
                                float* partial, int64_t N_pad, cudaStream_t st);
