@@ -136,23 +136,39 @@ def profile_traffic(workload: str):
     return e.get("dram_bytes_per_launch")
 
 
+def oracle_sample_shape(w, region, sched, cfg, seconds_target):
+    """(particles, steps) of a bounded oracle sample of about seconds_target: calibrated on one
+    step with at most 512 particles, then full N if one step fits, else fewer particles."""
+    import oracle
+
+    n0 = min(w["N"], 512)
+    t0 = time.perf_counter()
+    oracle.run(region.G, region.y, w["nu"], sched[:1], n0, w["M"], seed=1, cfg=cfg)
+    per_particle_step = (time.perf_counter() - t0) / n0
+    full_step = per_particle_step * w["N"]
+    if full_step <= seconds_target:
+        return w["N"], max(1, min(w["T"], int(seconds_target / max(full_step, 1e-4))))
+    return max(64, int(seconds_target / max(per_particle_step, 1e-9))), 1
+
+
+def oracle_gmac(w, Ns, steps):
+    return Ns * w["n"] * w["p"] * (steps * w["M"] + 1) / 1e9
+
+
 def cpu_oracle_sample(w, region, sched, seconds_target=15.0, seed=1):
-    """Time the FP64 oracle on a bounded prefix of the sweep (init + the first steps)."""
+    """Time the FP64 oracle on a bounded prefix of the sweep (init + the first steps; fewer
+    particles when one step at full N would take longer than the target)."""
     import oracle
 
     threads = oracle.max_threads()
-    # calibrate on one step, then take as many steps as fit in ~seconds_target
+    cfg = oracle.make_config(move=w["move"])
+    Ns, steps = oracle_sample_shape(w, region, sched, cfg, seconds_target)
     t0 = time.perf_counter()
-    oracle.run(region.G, region.y, w["nu"], sched[:1], w["N"], w["M"], seed=seed)
-    one = time.perf_counter() - t0
-    steps = max(1, min(w["T"], int(seconds_target / max(one, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.run(region.G, region.y, w["nu"], sched[:steps], w["N"], w["M"], seed=seed)
+    oracle.run(region.G, region.y, w["nu"], sched[:steps], Ns, w["M"], seed=seed, cfg=cfg)
     dt = time.perf_counter() - t0
-    gmac = w["N"] * w["n"] * w["p"] * (steps * w["M"] + 1) / 1e9
-    return {"value": gmac / dt, "unit": "GMAC/s", "cores": threads, "kind": "oracle",
+    return {"value": oracle_gmac(w, Ns, steps) / dt, "unit": "GMAC/s", "cores": threads, "kind": "oracle",
             "sample": f"first {steps} of {w['T']} scale steps (init + {steps * w['M']} moves) of the same "
-                      f"workload, full N, {dt:.1f} s on {threads} threads"}
+                      f"workload with {Ns} of {w['N']} particles, {dt:.1f} s on {threads} threads"}
 
 
 def reference_arm(args, w):
@@ -165,25 +181,23 @@ def reference_arm(args, w):
 
     oracle.build()
     region = synth.workload_region(w["name"])
-    sched = synth.geometric_schedule(w["T"])
-    t0 = time.perf_counter()
-    oracle.run(region.G, region.y, w["nu"], sched[:1], w["N"], w["M"], seed=1)
-    one = time.perf_counter() - t0
+    sched = synth.workload_schedule(w["name"])
+    cfg = oracle.make_config(move=w["move"])
     budget = 150.0 / max(1, args.steps + args.warmup)
-    steps_per = max(1, min(w["T"], int(budget / max(one, 1e-3))))
-    gmac = w["N"] * w["n"] * w["p"] * (steps_per * w["M"] + 1) / 1e9
+    Ns, steps_per = oracle_sample_shape(w, region, sched, cfg, budget)
+    gmac = oracle_gmac(w, Ns, steps_per)
     for k in range(args.warmup):
-        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], w["N"], w["M"], seed=100 + k)
+        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], Ns, w["M"], seed=100 + k, cfg=cfg)
     times = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], w["N"], w["M"], seed=200 + k)
+        oracle.run(region.G, region.y, w["nu"], sched[:steps_per], Ns, w["M"], seed=200 + k, cfg=cfg)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = gmac * args.steps / tot
     threads = oracle.max_threads()
     sample = (f"each step: first {steps_per} of {w['T']} scale steps (init + {steps_per * w['M']} moves) of the "
-              f"workload at full N, FP64, {threads} threads")
+              f"workload with {Ns} of {w['N']} particles, FP64, {threads} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GMAC/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
@@ -272,6 +286,54 @@ def batched_bench(args):
     return 0
 
 
+def loglik_roofline(reg, w, args, stream):
+    """The likelihood kernel timed alone with CUDA events (200 launches on the sweep's
+    stream, in the sweep's launch configuration), against the measured BF16 peak."""
+    import torch
+
+    reps = 200
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reg.loglik_repeat(w["N"], 5, stream.cuda_stream)
+    e0.record(stream)
+    reg.loglik_repeat(w["N"], reps, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    reg.sync()
+    kern_ms = e0.elapsed_time(e1) / reps
+    peaks, peak_src = measured_peaks()
+    flop = 2.0 * w["N"] * w["n"] * w["p"]
+    achieved = flop / (kern_ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops_sustained" if args.precision == "split_bf16" else "bf16_tflops")
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": profile_traffic(args.workload),
+                "kernel": "k_loglik_tc" if args.precision == "split_bf16" else "k_eta_tile",
+                "tile_bn": reg.loglik_tile_width(),
+                "launch_ms": kern_ms, "peak_source": f"{peak_src}: bf16 sustained (kernel inside a long step)",
+                "algorithmic_flop_per_launch": flop}
+    return roofline
+
+
+SFU_OPS_PER_CLK_PER_SM = 16  # MUFU (ex2, lg2, rcp, ...) results per clock per SM
+
+
+def site_roofline(w, ms_per_step, clocks):
+    """The single-coordinate cycle is bound by the SFU: every trial update needs one ex2 per
+    individual. Achieved = N M p n T ex2 / sweep time, against SMs x 16 per clock x the
+    maximum SM clock (a derived peak: the measured peaks cover copies and GEMMs only)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * SFU_OPS_PER_CLK_PER_SM * mhz * 1e6 / 1e9
+    ops = w["N"] * w["M"] * w["p"] * w["n"] * w["T"]
+    achieved = ops / (ms_per_step / 1e3) / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (SFU ex2)", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_move_site",
+            "peak_source": f"derived: {sms} SMs x {SFU_OPS_PER_CLK_PER_SM} SFU results/clk x {mhz:.0f} MHz",
+            "algorithmic_ops_per_sweep": ops, "note": "whole-sweep rate (the cycle kernel dominates the sweep)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -318,14 +380,15 @@ def main():
     import paper_1106_0322_gb300 as spa
 
     region = synth.workload_region(args.workload)
-    sched_h = synth.geometric_schedule(w["T"])
+    sched_h = synth.workload_schedule(args.workload)
     sched_d = torch.tensor(sched_h, dtype=torch.float64, device=dev)
     # A dedicated stream: the library runs on it and the events are recorded on it (the
     # legacy default stream has handle 0, which the library reads as "its own stream").
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
-    cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream)
+    init = dict(init="resample_move", burn_in_steps=w["burn_in"]) if w.get("burn_in") else {}
+    cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream, **init)
     reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
     T, p = w["T"], w["p"]
     out_d = {
@@ -385,32 +448,16 @@ def main():
     assert np.all(np.isfinite(out_d["mean"].cpu().numpy()))
 
     # ----------------------------------- dominant kernel: the likelihood GEMM + epilogue
-    reps = 200
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reg.loglik_repeat(w["N"], 5, stream.cuda_stream)
-    e0.record(stream)
-    reg.loglik_repeat(w["N"], reps, stream.cuda_stream)
-    e1.record(stream)
-    e1.synchronize()
-    reg.sync()
-    kern_ms = e0.elapsed_time(e1) / reps
-    peaks, peak_src = measured_peaks()
-    flop = 2.0 * w["N"] * w["n"] * w["p"]
-    achieved = flop / (kern_ms / 1e3) / 1e12
-    peak = peaks.get("bf16_tflops_sustained" if args.precision == "split_bf16" else "bf16_tflops")
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": profile_traffic(args.workload),
-                "kernel": "k_loglik_tc" if args.precision == "split_bf16" else "k_eta_tile",
-                "tile_bn": reg.loglik_tile_width(),
-                "launch_ms": kern_ms, "peak_source": f"{peak_src}: bf16 sustained (kernel inside a long step)",
-                "algorithmic_flop_per_launch": flop}
+    if w["move"] == "site":
+        roofline = site_roofline(w, ms_per_step, clocks)
+    else:
+        roofline = loglik_roofline(reg, w, args, stream)
 
     # --------------------------------- plain FP32 comparator sweep on the same workload
     plain = None
-    if args.precision == "split_bf16" and rank == 0:
+    if args.precision == "split_bf16" and rank == 0 and w["move"] != "site":
         reg32 = spa.Region(region.G, region.y, w["nu"],
-                           config=spa.make_config(move=w["move"], precision="fp32", stream=stream.cuda_stream))
+                           config=spa.make_config(move=w["move"], precision="fp32", stream=stream.cuda_stream, **init))
         reg32.run_device(sched_d, w["N"], w["M"], 7, out_d)
         reg32.sync()
         flush.zero_()
@@ -429,7 +476,8 @@ def main():
     if not args.no_e2e:
         G_pin = torch.from_numpy(region.G).pin_memory()
         y_pin = torch.from_numpy(region.y).pin_memory()
-        ereg = spa.Region(region.G, region.y, w["nu"], config=spa.make_config(move=w["move"], precision=args.precision))
+        ereg = spa.Region(region.G, region.y, w["nu"],
+                          config=spa.make_config(move=w["move"], precision=args.precision, **init))
         ereg.run(sched_h, w["N"], w["M"], 1)  # builds the graph once, as a long-lived context does
         t_e2e = 0.0
         ksteps = max(2, min(args.steps, 5))

@@ -45,6 +45,10 @@ extern "C" {
 /* ------------------------------------------------------------------ configuration */
 #define SPA_MOVE_RW 0       /* joint random-walk Metropolis-Hastings */
 #define SPA_MOVE_MALA 1     /* Metropolis-adjusted Langevin, driven by the adjoint kernel */
+#define SPA_MOVE_SITE 2     /* the paper's own kernel (Section 4.1, "Further details"): per move,
+                               a cycle of single-coordinate random-walk Metropolis updates
+                               j = 1..p with proposal sd site_sd, each an O(n) update of X beta;
+                               runs on CUDA cores (FP32), the precision field is ignored */
 
 #define SPA_PREC_SPLIT_BF16 0 /* tcgen05: X exact in BF16, beta = hi + lo BF16, FP32 accumulate */
 #define SPA_PREC_FP32 1       /* plain FP32 SIMT (FFMA) comparator path */
@@ -56,7 +60,7 @@ extern "C" {
 #define SPA_MAX_DELTAS 8
 
 typedef struct spa_config {
-    int32_t move_kind;       /* SPA_MOVE_RW (default) or SPA_MOVE_MALA */
+    int32_t move_kind;       /* SPA_MOVE_RW (default), SPA_MOVE_MALA or SPA_MOVE_SITE */
     int32_t precision;       /* SPA_PREC_SPLIT_BF16 (default) or SPA_PREC_FP32 */
     int32_t init_mode;       /* SPA_INIT_PRIOR_IS (default) or SPA_INIT_RESAMPLE_MOVE */
     int32_t burn_in_steps;   /* blocks of M moves at c_1 for SPA_INIT_RESAMPLE_MOVE (default 0) */
@@ -68,6 +72,7 @@ typedef struct spa_config {
     double rw_scale;         /* RW: sigma_j = rw_scale/sqrt(p) * max(sd_W(beta_j), sd_floor*c) (2.38) */
     double mala_h;           /* MALA: initial lambda in h = lambda * p^(-1/6) (1.65) */
     double sd_floor;         /* floor of the proposal scale relative to c (default 1e-3) */
+    double site_sd;          /* SITE: proposal sd of one coordinate (0.5: the paper's variance 0.25) */
     void* stream;            /* cudaStream_t to run on; NULL: the context's own stream */
 } spa_config;
 
@@ -191,6 +196,25 @@ int spa_loglik_tile_width(const spa_ctx* ctx);
  * uses. No host synchronisation; for timing the kernel with events on `stream`.
  * SPA_EINVAL if no workspace of N particles exists. */
 int spa_loglik_repeat(spa_ctx* ctx, int64_t N, int32_t reps, void* stream);
+
+/* Scale-marginalised summaries (Section 4, eq. all_particles). With a uniform prior on
+ * log b and a log-spaced schedule (as spa_run's geometric schedules are), the particle
+ * systems of all steps mix with weights proportional to Z_t / Z_1, each estimated by the
+ * running product of the Z_t / Z_{t-1} increments:
+ *   post_c[t] = exp(L_t - max L) / sum_s exp(L_s - max L),  L_t = sum_{s=1..t} log_z_inc[s]
+ * (log_z_inc[0] is common to every L_t and does not enter), which is also the posterior of
+ * the scale on the schedule's grid. mean_out[j] = sum_t post_c[t] mean[t][j] and
+ * conc_out[j][d] = sum_t post_c[t] conc[t][j][d] are the mixture's means and V(Delta).
+ * Inputs are one sweep's spa_result arrays: log_z_inc [T], mean [T][p], conc [T][p][D]
+ * (D = the config's n_deltas, 0..SPA_MAX_DELTAS; conc and conc_out may be NULL when
+ * D = 0). Outputs: post_c [T], mean_out [p], conc_out [p][D]. All FP64, formed on the GPU.
+ * spa_marginal takes host pointers and blocks; spa_marginal_device takes device pointers and
+ * only enqueues on `stream`. Errors: SPA_EINVAL (NULL pointers, T or p < 1, D out of
+ * range), SPA_ENOMEM, SPA_ECUDA. */
+int spa_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p, int32_t D,
+                 double* post_c, double* mean_out, double* conc_out);
+int spa_marginal_device(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
+                        int32_t D, double* post_c, double* mean_out, double* conc_out, void* stream);
 
 /* ------------------------------------------------------- per-step entry points */
 

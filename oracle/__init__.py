@@ -51,6 +51,7 @@ class OrConfig(C.Structure):
         ("rw_scale", C.c_double),
         ("mala_h", C.c_double),
         ("sd_floor", C.c_double),
+        ("site_sd", C.c_double),
         ("n_threads", C.c_int32),
     ]
 
@@ -103,6 +104,9 @@ def _load():
                                C.c_int64, C.c_int64, C.c_int32, C.c_uint64, P(OrConfig), P(OrResult)]
         lib.or_run.restype = C.c_int
         lib.or_max_threads.restype = C.c_int
+        lib.or_marginal.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_int64, C.c_int64, C.c_int,
+                                    P(C.c_double), P(C.c_double), P(C.c_double)]
+        lib.or_marginal.restype = C.c_int
         _lib = lib
         return lib
 
@@ -218,12 +222,30 @@ def max_threads() -> int:
     return int(_load().or_max_threads())
 
 
+def marginal(log_z_inc, mean, conc) -> dict:
+    """Scale-marginalised summaries (Section 4, eq. all_particles) from a sweep's per-step
+    outputs: log_z_inc [T], mean [T, p], conc [T, p, D]. Returns post_c [T] (the weights
+    Z_t/Z_1 normalised), mean [p] and conc [p, D] of the mixture over scales."""
+    lz = np.ascontiguousarray(log_z_inc, dtype=np.float64)
+    m = np.ascontiguousarray(mean, dtype=np.float64)
+    c = np.ascontiguousarray(conc, dtype=np.float64)
+    T, p = m.shape
+    D = c.shape[2] if c.ndim == 3 else 0
+    post = np.zeros(T)
+    mo = np.zeros(p)
+    co = np.zeros((p, max(D, 1)))
+    if _load().or_marginal(_p(lz, C.c_double), _p(m, C.c_double), _p(c, C.c_double), T, p, D, _p(post, C.c_double),
+                           _p(mo, C.c_double), _p(co, C.c_double)) != 0:
+        raise ValueError("or_marginal: bad sizes")
+    return {"post_c": post, "mean": mo, "conc": co[:, :D]}
+
+
 def make_config(move: str = "rw", init: str = "prior_is", burn_in_steps: int = 0,
                 quantiles=(0.05, 0.5, 0.95), deltas=(0.05, 0.1), ess_frac: float = 0.75,
                 rw_scale: float = 2.38, mala_h: float = 1.65, sd_floor: float = 1e-3,
-                n_threads: int = 0) -> OrConfig:
+                site_sd: float = 0.5, n_threads: int = 0) -> OrConfig:
     cfg = OrConfig()
-    cfg.move_kind = {"rw": 0, "mala": 1}[move]
+    cfg.move_kind = {"rw": 0, "mala": 1, "site": 2}[move]
     cfg.init_mode = {"prior_is": 0, "mcmc": 1}[init]
     cfg.burn_in_steps = burn_in_steps
     cfg.n_quantiles = len(quantiles)
@@ -236,6 +258,7 @@ def make_config(move: str = "rw", init: str = "prior_is", burn_in_steps: int = 0
     cfg.rw_scale = rw_scale
     cfg.mala_h = mala_h
     cfg.sd_floor = sd_floor
+    cfg.site_sd = site_sd
     cfg.n_threads = n_threads
     return cfg
 

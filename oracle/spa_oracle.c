@@ -25,6 +25,9 @@
  *   or_weighted_quantile  pinned: brute-force definition on small inputs
  *   or_run                pinned: p <= 2 grid quadrature of every pi_t (posterior
  *                         means, quantiles, concentrations) and of Z_t / Z_1
+ *   or_marginal           pinned: equal evidence gives the plain average, one dominant
+ *                         step gives its summary, shift invariance of log Z, and the
+ *                         p <= 2 quadrature of the scale-marginalised posterior
  *   The paper's own SPA curves cannot pin anything: its figures and data are absent.
  */
 #include <math.h>
@@ -71,7 +74,7 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
  *   move normals       (j/4, particle, t, 2<<16 | m)  Box-Muller pairs (u0,u1), (u2,u3)
  *   MH uniform         (0,   particle, t, 3<<16 | m)  u0
  *   resampling uniform (0,   0,        t, 4<<16)      u0                                   */
-enum { OR_TAG_INIT = 1, OR_TAG_NORMAL = 2, OR_TAG_ACCEPT = 3, OR_TAG_RESAMPLE = 4 };
+enum { OR_TAG_INIT = 1, OR_TAG_NORMAL = 2, OR_TAG_ACCEPT = 3, OR_TAG_RESAMPLE = 4, OR_TAG_SITE = 5 };
 
 static void or_draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t out[4])
 {
@@ -401,7 +404,8 @@ int or_weighted_quantile(const double* vals, const double* W, int64_t N, const d
 /* The SMC sampler over the prior scale (Section 4).                          */
 /* ------------------------------------------------------------------------- */
 typedef struct {
-    int32_t move_kind;      /* 0: joint random-walk Metropolis; 1: MALA */
+    int32_t move_kind;      /* 0: joint random-walk Metropolis; 1: MALA; 2: the paper's cycle
+                               of single-coordinate random-walk updates */
     int32_t init_mode;      /* 0: prior importance sampling at c_1; 1: the same, then an
                                unconditional resample and burn-in moves at c_1 */
     int32_t burn_in_steps;  /* init_mode 1: blocks of M moves run before step 1's statistics */
@@ -414,6 +418,7 @@ typedef struct {
     double mala_h;          /* MALA: h = lambda_t * p^(-1/6), lambda_0 = mala_h, then
                                lambda_{t+1} = lambda_t * exp(acceptance_t - 0.574) */
     double sd_floor;
+    double site_sd;         /* single-coordinate moves: proposal sd (0.5, variance 0.25) */
     int32_t n_threads;      /* OpenMP threads; <= 0 keeps the runtime default */
 } or_config;
 
@@ -458,11 +463,61 @@ static void or_col_moments(const or_state* s, const double* W, double* mu, doubl
     }
 }
 
+/* The paper's own kernel (Section 4.1, "Further details"): a cycle of single-  */
+/* coordinate random-walk Metropolis updates, j = 1..p in order, each proposing  */
+/* beta_j' = beta_j + site_sd * xi, the cycle repeated M times. eta = X beta is   */
+/* carried along and changed by x_.j * delta when an update is accepted, so one  */
+/* update costs O(n). The normal is Box-Muller's cosine branch on the first two  */
+/* words of the Philox block (j, particle, t, TAG_SITE << 16 | m); the third word */
+/* is the update's uniform. Returns the number of accepted coordinate updates.   */
+static int64_t or_site_moves(or_state* s, double c, uint32_t t, uint32_t m0, int32_t M, const or_config* cfg)
+{
+    const int64_t p = s->p, n = s->n, N = s->N;
+    int64_t accepted = 0;
+#pragma omp parallel reduction(+ : accepted)
+    {
+        double* eta = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < N; ++i) {
+            double* b = s->beta + i * p;
+            or_loglik_x(s->X, s->y, n, p, b, eta);
+            for (int32_t mm = 0; mm < M; ++mm) {
+                const uint32_t m = m0 + (uint32_t)mm;
+                for (int64_t j = 0; j < p; ++j) {
+                    uint32_t u[4];
+                    or_draw(s->seed, (uint32_t)j, (uint32_t)i, t, ((uint32_t)OR_TAG_SITE << 16) | m, u);
+                    const double z = sqrt(-2.0 * log(or_u01_open(u[0]))) *
+                                     cos(6.283185307179586476925286766559 * or_u01_open(u[1]));
+                    const double delta = cfg->site_sd * z;
+                    const double bn = b[j] + delta;
+                    double dl = 0.0;
+                    for (int64_t r = 0; r < n; ++r) {
+                        const double x = s->X[r * p + j];
+                        const double e0 = eta[r], e1 = e0 + x * delta;
+                        dl += (double)s->y[r] * x * delta - (or_softplus(e1) - or_softplus(e0));
+                    }
+                    const double dlp = or_logprior1(s->a, c, bn) - or_logprior1(s->a, c, b[j]);
+                    if (log(or_u01_open(u[2])) < dl + dlp) {
+                        b[j] = bn;
+                        for (int64_t r = 0; r < n; ++r) eta[r] += s->X[r * p + j] * delta;
+                        ++accepted;
+                    }
+                }
+            }
+            s->ll[i] = or_loglik_x(s->X, s->y, n, p, b, eta);
+            s->lp[i] = or_logprior(s->a, c, b, p);
+        }
+        free(eta);
+    }
+    return accepted;
+}
+
 /* M moves of an MCMC kernel with invariant distribution pi_t (Section 4.1)  */
 /* applied to every particle; returns the number of accepted proposals.      */
 static int64_t or_moves(or_state* s, double c, uint32_t t, uint32_t m0, int32_t M, const double* W,
                         const or_config* cfg, double lam)
 {
+    if (s->move_kind == 2) return or_site_moves(s, c, t, m0, M, cfg);
     const int64_t p = s->p, n = s->n, N = s->N;
     double* mu = (double*)malloc(sizeof(double) * (size_t)p);
     double* var = (double*)malloc(sizeof(double) * (size_t)p);
@@ -642,6 +697,7 @@ int or_run(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, co
            int64_t T, int64_t N, int32_t M, uint64_t seed, const or_config* cfg, or_result* r)
 {
     if (n < 1 || p < 1 || N < 1 || T < 1 || M < 0 || !(a > 0.0)) return -1;
+    if (cfg->move_kind < 0 || cfg->move_kind > 2) return -1;
     for (int64_t t = 0; t < T; ++t)
         if (!(sched[t] > 0.0) || isinf(sched[t])) return -1;
 #ifdef _OPENMP
@@ -724,7 +780,9 @@ int or_run(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, co
             break;
         }
         int64_t acc = or_moves(&s, c, (uint32_t)t, (t == 0) ? m_base : 0u, M, W, cfg, lam);
-        double rate = (M > 0) ? (double)acc / ((double)M * (double)N) : 0.0;
+        /* the acceptance rate per proposal: per coordinate update for the cycle kernel */
+        const double props = (double)M * (double)N * (cfg->move_kind == 2 ? (double)p : 1.0);
+        double rate = (M > 0) ? (double)acc / props : 0.0;
         if (r->accept_rate) r->accept_rate[t] = rate;
         if (cfg->move_kind == 1 && M > 0) lam *= exp(rate - 0.574);
         or_summaries(&s, W, cfg, t, r);
@@ -733,6 +791,45 @@ int or_run(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, co
     if (r->final_logw) memcpy(r->final_logw, logw, sizeof(double) * (size_t)N);
     free(X); free(s.beta); free(s.ll); free(s.lp); free(s.gl); free(logw); free(W);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Scale-marginalised summaries (Section 4, eq. all_particles): with a uniform   */
+/* prior on log b and the log-spaced schedule, the particle systems of all steps */
+/* are mixed with weights Z_t / Z_1, each estimated by the running product of    */
+/* the Z_t / Z_{t-1} estimates. Step t's weight is                               */
+/*   w_t = exp(L_t - max L) / sum_s exp(L_s - max L),  L_t = sum_{s=1..t} inc_s   */
+/* (inc_0, the t = 0 evidence, is common to every L_t and is left out). Mixture  */
+/* means and concentrations are the w-weighted averages of the per-step ones;    */
+/* post_c[t] = w_t is the posterior of the scale on the schedule's grid.         */
+/* ------------------------------------------------------------------------- */
+int or_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p, int D,
+                double* post_c, double* mean_out, double* conc_out)
+{
+    if (T < 1 || p < 1 || D < 0) return -1;
+    double* L = (double*)malloc(sizeof(double) * (size_t)T);
+    if (!L) return -1;
+    double acc = 0.0, m = -INFINITY;
+    for (int64_t t = 0; t < T; ++t) {
+        if (t > 0) acc += log_z_inc[t];
+        L[t] = acc;
+        if (L[t] > m) m = L[t];
+    }
+    double s = 0.0;
+    for (int64_t t = 0; t < T; ++t) s += exp(L[t] - m);
+    for (int64_t t = 0; t < T; ++t) post_c[t] = exp(L[t] - m) / s;
+    for (int64_t j = 0; j < p; ++j) {
+        double mm = 0.0;
+        for (int64_t t = 0; t < T; ++t) mm += post_c[t] * mean[t * p + j];
+        mean_out[j] = mm;
+        for (int d = 0; d < D; ++d) {
+            double cc = 0.0;
+            for (int64_t t = 0; t < T; ++t) cc += post_c[t] * conc[(t * p + j) * D + d];
+            conc_out[j * D + d] = cc;
+        }
+    }
+    free(L);
+    return 0;
 }
 
 int or_max_threads(void)

@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 SPA_OK, SPA_EINVAL, SPA_ENOMEM, SPA_ECUDA, SPA_ETIMEOUT, SPA_ENUMERIC, SPA_EUNSUPPORTED = range(7)
-MOVE_RW, MOVE_MALA = 0, 1
+MOVE_RW, MOVE_MALA, MOVE_SITE = 0, 1, 2
 PREC_SPLIT_BF16, PREC_FP32 = 0, 1
 INIT_PRIOR_IS, INIT_RESAMPLE_MOVE = 0, 1
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ENUMERIC", 6: "EUNSUPPORTED"}
@@ -47,6 +47,7 @@ class Config(C.Structure):
         ("rw_scale", C.c_double),
         ("mala_h", C.c_double),
         ("sd_floor", C.c_double),
+        ("site_sd", C.c_double),
         ("stream", C.c_void_p),
     ]
 
@@ -95,6 +96,10 @@ _SIGS = {
     "spa_incr_weight": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_int64, C.c_int64,
                                   C.c_void_p]),
     "spa_lse_ess": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "spa_marginal": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p,
+                               C.c_void_p, C.c_void_p]),
+    "spa_marginal_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spa_summaries": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p,
                                 C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "spa_philox4x32_10": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
@@ -150,9 +155,9 @@ def default_config() -> Config:
 
 def make_config(move: str = "rw", precision: str = "split_bf16", init: str = "prior_is", burn_in_steps: int = 0,
                 quantiles=(0.05, 0.5, 0.95), deltas=(0.05, 0.1), ess_frac: float = 0.75, rw_scale: float = 2.38,
-                mala_h: float = 1.65, sd_floor: float = 1e-3, stream: int = 0) -> Config:
+                mala_h: float = 1.65, sd_floor: float = 1e-3, site_sd: float = 0.5, stream: int = 0) -> Config:
     cfg = default_config()
-    cfg.move_kind = {"rw": MOVE_RW, "mala": MOVE_MALA}[move]
+    cfg.move_kind = {"rw": MOVE_RW, "mala": MOVE_MALA, "site": MOVE_SITE}[move]
     cfg.precision = {"split_bf16": PREC_SPLIT_BF16, "fp32": PREC_FP32}[precision]
     cfg.init_mode = {"prior_is": INIT_PRIOR_IS, "resample_move": INIT_RESAMPLE_MOVE, "mcmc": INIT_RESAMPLE_MOVE}[init]
     cfg.burn_in_steps = burn_in_steps
@@ -166,6 +171,7 @@ def make_config(move: str = "rw", precision: str = "split_bf16", init: str = "pr
     cfg.rw_scale = rw_scale
     cfg.mala_h = mala_h
     cfg.sd_floor = sd_floor
+    cfg.site_sd = site_sd
     cfg.stream = stream or None
     return cfg
 
@@ -361,6 +367,22 @@ class Batch:
 
 
 # ------------------------------------------------------------ context-free calls
+def marginal(result: dict) -> dict:
+    """spa_marginal on one sweep's outputs (a dict from Region.run): the posterior over the
+    schedule's scales, post_c [T], and the scale-marginalised mean [p] and conc [p, D]."""
+    lz = np.ascontiguousarray(result["log_z_inc"], dtype=np.float64)
+    m = np.ascontiguousarray(result["mean"], dtype=np.float64)
+    c = np.ascontiguousarray(result["conc"], dtype=np.float64)
+    T, p = m.shape
+    D = c.shape[2] if c.ndim == 3 else 0
+    post = np.zeros(T)
+    mo = np.zeros(p)
+    co = np.zeros((p, max(D, 1)))
+    _check(load().spa_marginal(_ptr(lz), _ptr(m), _ptr(c) if D else None, T, p, D, _ptr(post), _ptr(mo),
+                               _ptr(co) if D else None))
+    return {"post_c": post, "mean": mo, "conc": co[:, :D]}
+
+
 def resample_systematic(W, u: float) -> np.ndarray:
     W = np.ascontiguousarray(W, dtype=np.float64)
     idx = np.zeros(W.size, np.int32)

@@ -64,7 +64,9 @@ struct TcCfg {
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
 };
 
-// Sum over the first `valid` of 32 columns of softplus2(eta2) = log2(1 + 2^eta2).
+// Sum over the first `valid` of 32 columns of softplus2(eta2) = log2(1 + 2^eta2): 32
+// independent ex2/lg2 pairs, then a tree. (Folding the logarithms into one of a running
+// product was measured slower: the epilogue is latency-bound, and the product is a chain.)
 __device__ __forceinline__ float sum_sp2_32(const uint32_t (&r)[32], int valid)
 {
     float t[32];
@@ -103,11 +105,11 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         const float x = v[k];
+        const bool ok = k < valid;
         const float e = ex2_approx(-fabsf(x));
         const float onepe = 1.0f + e;
         const float inv = rcp_approx(onepe);
         const float sig = (x >= 0.0f) ? inv : e * inv;
-        const bool ok = k < valid;
         const bool yk = (ybits >> k) & 1u;
         sp[k] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
         const float r = ok ? (yk ? 1.0f : 0.0f) - sig : 0.0f;

@@ -353,6 +353,102 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
     if (DECIDE) count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
 }
 
+// ------------------------------------------------- single-coordinate update cycle
+// The paper's own kernel (Section 4.1, "Further details"): a cycle of single-coordinate
+// random-walk Metropolis updates, j = 0..p-1 in order, each proposing beta_j' = beta_j +
+// sd * xi, repeated M times per step. One warp per particle, one launch per step.
+// eta2 = log2(e) X beta lives in shared memory (computed from X^T at the start of the step)
+// and changes by x_.j delta when an update is accepted, so an update costs O(n):
+//   delta l = delta v_j - ln 2 * sum_i [softplus2(eta2_i + x2_ij delta) - softplus2(eta2_i)]
+// with the linear half from v = X^T y. softplus2 = max(eta2, 0) + log2(1 + 2^-|eta2|); the
+// max parts are summed as differences, the log parts as the base-2 logarithm of the
+// product of their factors (each in [1, 2], SITE_CHUNK per product), and each lane keeps
+// that log for its individuals at the current state, so a trial needs one ex2 per
+// individual. The normal is Box-Muller's cosine branch on words 0 and 1 of the Philox
+// block (j, particle, t, TAG_SITE << 16 | m), word 2 the update's uniform.
+constexpr int SITE_CHUNK = 64;
+
+// Per-lane: sum over the lane's individuals r = lane + 32k of max(eta2', 0) - max(eta2, 0)
+// (dm) and log2 of the product of (1 + 2^-|eta2'|) (returned), eta2' = eta2 + x2 delta.
+__device__ __forceinline__ float site_trial(const float* __restrict__ eta, const float* __restrict__ xr, int n,
+                                            int lane, float delta, float& dm)
+{
+    float lq = 0.0f, d = 0.0f;
+    for (int k0 = 0; 32 * k0 < n; k0 += SITE_CHUNK) {
+        float prod = 1.0f;
+        const int r1 = min(n, 32 * (k0 + SITE_CHUNK));
+        for (int r = lane + 32 * k0; r < r1; r += 32) {
+            const float e0 = eta[r];
+            const float e1 = fmaf(xr[r], delta, e0);
+            d += fmaxf(e1, 0.0f) - fmaxf(e0, 0.0f);
+            prod = fmaf(prod, ex2_approx(-fabsf(e1)), prod);
+        }
+        lq += lg2_approx(prod);
+    }
+    dm = d;
+    return lq;
+}
+
+__global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, const double* __restrict__ sched, int t,
+                            uint32_t m0, int M, const uint64_t* __restrict__ seedp)
+{
+    extern __shared__ float site_sm[];
+    __shared__ float shk[3];
+    __shared__ int blk;
+    const int wpc = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) blk = 0;
+    step_constants(pr, sched, t, shk);
+    float* eta = site_sm + (size_t)w * (size_t)(n + p);
+    float* brow = eta + n;
+    const int64_t i = (int64_t)blockIdx.x * wpc + w;
+    if (i < N) {
+        const uint64_t seed = *seedp;
+        const float ac = shk[0], coef = shk[1];
+        float* bg = a.beta + i * p;
+        for (int j = lane; j < p; j += 32) brow[j] = bg[j];
+        for (int r = lane; r < n; r += 32) eta[r] = 0.0f;
+        __syncwarp();
+        for (int j = 0; j < p; ++j) {  // eta2 = X2 beta, marker by marker (coalesced rows of X^T)
+            const float bj = brow[j];
+            const float* xr = a.XT2 + (size_t)j * n;
+            for (int r = lane; r < n; r += 32) eta[r] = fmaf(xr[r], bj, eta[r]);
+        }
+        float dm;
+        float lq = site_trial(eta, a.XT2, n, lane, 0.0f, dm);  // delta = 0: the current state
+        int nacc = 0;
+        for (int mm = 0; mm < M; ++mm) {
+            const uint32_t m = m0 + (uint32_t)mm;
+            for (int j = 0; j < p; ++j) {
+                const uint4 u = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)i, (uint32_t)t, (TAG_SITE << 16) | m),
+                                              seed_key(seed));
+                float sn, cs;
+                sincospif(2.0f * u01_open_f(u.y), &sn, &cs);
+                const float delta = a.sd * (sqrtf(-2.0f * logf(u01_open_f(u.x))) * cs);
+                const float* xr = a.XT2 + (size_t)j * n;
+                const float lq1 = site_trial(eta, xr, n, lane, delta, dm);
+                const float dsp = warp_sum(dm + (lq1 - lq));
+                const float b0 = brow[j], b1 = b0 + delta;
+                const float dlp = coef * (prior_term(b1, ac, pr.de) - prior_term(b0, ac, pr.de));
+                const float dl = fmaf(delta, a.vy[j], -0.69314718f * dsp);
+                int acc = logf(u01_open_f(u.z)) < dl + dlp;
+                acc = __shfl_sync(0xffffffffu, acc, 0);
+                if (acc) {
+                    for (int r = lane; r < n; r += 32) eta[r] = fmaf(xr[r], delta, eta[r]);
+                    lq = lq1;
+                    if (lane == 0) brow[j] = b1;
+                    ++nacc;
+                }
+                __syncwarp();
+            }
+        }
+        for (int j = lane; j < p; j += 32) bg[j] = brow[j];
+        if (lane == 0 && nacc) atomicAdd(&blk, nacc);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && blk && a.acc_count) atomicAdd(a.acc_count, (unsigned long long)blk);
+}
+
 // ------------------------------------------------------------ last move of a step
 // MH test of the pending proposals (RW, or MALA with the reverse term), then accepted
 // proposals (and their gradients) are copied into the state rows, so that between steps
@@ -864,13 +960,15 @@ __device__ __forceinline__ float key_float(uint32_t k)
 
 // First bin of hist[0..nbins) (weights) at which *below + the cumulative weight reaches
 // target; one warp. Adds the weight of the bins before it to *below. Returns -1 if no bin
-// reaches the target.
+// reaches the target. Lane l owns bins l*per .. l*per+per-1 and sums them starting at a
+// lane-dependent offset, so the 32 lanes hit 32 different shared-memory banks.
 __device__ int warp_find_bin(const uint32_t* hist, int nbins, unsigned long long target, unsigned long long* below)
 {
     const int lane = threadIdx.x & 31;
     const int per = nbins / 32;
+    const uint32_t* mine_p = hist + lane * per;
     unsigned long long mine = 0;
-    for (int k = 0; k < per; ++k) mine += hist[lane * per + k];
+    for (int k = 0; k < per; ++k) mine += mine_p[(k + lane) & (per - 1)];
     unsigned long long incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -901,60 +999,69 @@ __device__ int warp_find_bin(const uint32_t* hist, int nbins, unsigned long long
     return bin;
 }
 
-__device__ void block_fsum_store(FSum v, float* shs, float* shc, double* out)
+// keysT[j][i] = float_key(beta[i][j]): the particles' values marker-major as
+// order-preserving integer keys, so each summaries CTA streams its marker's column with
+// coalesced loads. 32 x 32 tiles through shared memory.
+__global__ void k_keys_transpose(const float* __restrict__ beta, int64_t N, int p, uint32_t* __restrict__ keysT)
 {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) {
-        shs[w] = v.s;
-        shc[w] = v.c;
+    __shared__ uint32_t tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32;
+    const int j0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r;
+        const int j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < N && j < p) ? float_key(beta[i * p + j]) : 0u;
     }
     __syncthreads();
-    if (threadIdx.x == 0 && out) {
-        FSum r;
-        for (int k = 0; k < SUM_THREADS / 32; ++k) {
-            r.add(shs[k]);
-            r.c += shc[k];
-        }
-        *out = r.value();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int j = j0 + r;
+        const int64_t i = i0 + threadIdx.x;
+        if (i < N && j < p) keysT[(int64_t)j * N + i] = tile[threadIdx.x][r];
     }
 }
 
-__global__ void __launch_bounds__(SUM_THREADS, 1) k_summaries(const float* __restrict__ beta, const float* __restrict__ Wf,
+constexpr int SUM_SUB = 4;     // sub-histograms of the first radix digit (by warp % 4)
+constexpr int SUM_BINS = 2048;  // bins of an 11-bit digit
+
+// Per coordinate j (one CTA): the weighted mean and the concentrations (compensated FP32
+// sums), and the weighted quantiles by an exact radix select on the fixed-point weights
+// round(W 2^31) over the order-preserving integer keys of the values: digits of 11, 11 and
+// 10 bits from the top. The first digit's histogram is built while the values are loaded,
+// in SUM_SUB copies that are merged before the search (particles cluster in a few
+// top-digit bins, and one copy per warp group spreads their atomics).
+__global__ void __launch_bounds__(SUM_THREADS, 1) k_summaries(const uint32_t* __restrict__ keysT, const float* __restrict__ Wf,
                                                                const uint32_t* __restrict__ wfix, int64_t N, int p,
                                                                SummaryArgs sa, int t, double* __restrict__ mean,
                                                                double* __restrict__ quant, double* __restrict__ conc,
                                                                int staged)
 {
     extern __shared__ uint32_t sm[];
-    __shared__ float shs[SUM_THREADS / 32], shc[SUM_THREADS / 32];
+    __shared__ float red_s[SUM_THREADS / 32][9], red_c[SUM_THREADS / 32][9];
     __shared__ unsigned long long shu[SUM_THREADS / 32];
     __shared__ uint32_t shk[SUM_THREADS / 32];
     __shared__ int bins[8][3];
     __shared__ unsigned long long below[8];
-    __shared__ double conc_sh[8];
     const int j = blockIdx.x;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int nq = sa.nq, nd = sa.nd;
+    const int nq = (quant && sa.nq > 0) ? sa.nq : 0, nd = sa.nd;
     uint32_t* keys = sm;
     uint32_t* wts = sm + (staged ? N : 0);
-    uint32_t* hist = sm + (staged ? 2 * N : 0);  // (nq or 1) * 2048 words
-    float dthr[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-        float f = (float)sa.delta[d];
-        if ((double)f < sa.delta[d]) f = nextafterf(f, INFINITY);
-        dthr[d] = f;
+    uint32_t* hist = sm + (staged ? 2 * N : 0);  // max(SUM_SUB, nq) * SUM_BINS words
+    if (nq > 0) {
+        for (int e = tid; e < SUM_SUB * SUM_BINS; e += SUM_THREADS) hist[e] = 0u;
+        if (tid < 8) below[tid] = 0ull;
+        __syncthreads();
     }
-    // ---- pass 0: stage keys and weights; mean, concentrations, maximum key, total weight
+    uint32_t* hsub = hist + (w & (SUM_SUB - 1)) * SUM_BINS;
+    // ---- load: stage keys and weights; mean, concentrations, top-digit histogram
     FSum msum;
     FSum cs[8];
     uint32_t kmax = 0;
     unsigned long long tot = 0;
+    const uint32_t* kcol = keysT + (int64_t)j * N;
     for (int64_t i = tid; i < N; i += SUM_THREADS) {
-        const float b = beta[i * p + j];
-        const uint32_t k = float_key(b);
+        const uint32_t k = kcol[i];
+        const float b = key_float(k);
         const uint32_t wv = wfix[i];
         const float wf = Wf[i];
         if (staged) {
@@ -964,68 +1071,97 @@ __global__ void __launch_bounds__(SUM_THREADS, 1) k_summaries(const float* __res
         msum.add(wf * b);
 #pragma unroll
         for (int d = 0; d < 8; ++d)
-            if (d < nd && fabsf(b) < dthr[d]) cs[d].add(wf);
+            if (d < nd && fabsf(b) < sa.dthr[d]) cs[d].add(wf);
         kmax = k > kmax ? k : kmax;
         tot += wv;
+        if (nq > 0 && wv != 0u) atomicAdd(&hsub[k >> 21], wv);
     }
-    double mval = 0.0;
-    block_fsum_store(msum, shs, shc, &mval);
-    if (tid == 0 && mean) mean[(int64_t)t * p + j] = mval;
-    for (int d = 0; d < nd; ++d) {
-        block_fsum_store(cs[d], shs, shc, &conc_sh[d]);
-        if (tid == 0 && conc) conc[((int64_t)t * p + j) * nd + d] = 1.0 - conc_sh[d];
-    }
-    if (!quant || nq == 0) return;
-    {
+    // ---- one block reduction for every scalar
+    msum = warp_sum(msum);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        uint32_t v = kmax;
+    for (int d = 0; d < 8; ++d)
+        if (d < nd) cs[d] = warp_sum(cs[d]);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-        __syncthreads();
-        if (lane == 0) {
-            shu[w] = tot;
-            shk[w] = v;
-        }
-        __syncthreads();
-        tot = 0;
-        uint32_t r = 0;
-        for (int k = 0; k < SUM_THREADS / 32; ++k) {
-            tot += shu[k];
-            r = max(r, shk[k]);
-        }
-        kmax = r;
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
     }
-    if (tid < 8) below[tid] = 0ull;
-    // ---- radix passes: (shift, bits) = (21, 11), (10, 11), (0, 10)
+    if (lane == 0) {
+        red_s[w][0] = msum.s;
+        red_c[w][0] = msum.c;
+#pragma unroll
+        for (int d = 0; d < 8; ++d)
+            if (d < nd) {
+                red_s[w][1 + d] = cs[d].s;
+                red_c[w][1 + d] = cs[d].c;
+            }
+        shu[w] = tot;
+        shk[w] = kmax;
+    }
+    __syncthreads();
+    if (w == 0) {
+        // lane v < 1 + nd finishes scalar v: the mean (v = 0) or concentration v - 1
+        if (lane < 1 + nd) {
+            FSum r;
+            for (int k = 0; k < SUM_THREADS / 32; ++k) {
+                r.add(red_s[k][lane]);
+                r.c += red_c[k][lane];
+            }
+            const double val = (double)r.s + (double)r.c;
+            if (lane == 0) {
+                if (mean) mean[(int64_t)t * p + j] = val;
+            } else if (conc) {
+                conc[((int64_t)t * p + j) * nd + (lane - 1)] = 1.0 - val;
+            }
+        }
+    }
+    if (nq == 0) return;
+    tot = 0;
+    kmax = 0;
+    for (int k = 0; k < SUM_THREADS / 32; ++k) {
+        tot += shu[k];
+        kmax = max(kmax, shk[k]);
+    }
+    // merge the top-digit copies into copy 0
+    for (int b = tid; b < SUM_BINS; b += SUM_THREADS) {
+        uint32_t v = hist[b];
+#pragma unroll
+        for (int s2 = 1; s2 < SUM_SUB; ++s2) v += hist[s2 * SUM_BINS + b];
+        hist[b] = v;
+    }
+    __syncthreads();
+    // ---- digit searches: the top digit on the merged histogram, then bits 10..20 and 0..9
+    // of the keys that share the selected prefix, one histogram per quantile level
     for (int pass = 0; pass < 3; ++pass) {
         const int bits = (pass == 2) ? 10 : 11;
         const int shift = (pass == 0) ? 21 : ((pass == 1) ? 10 : 0);
         const int nb = 1 << bits;
-        const int nh = (pass == 0) ? 1 : nq;  // the first histogram is shared by every level
-        for (int e = tid; e < nh * nb; e += SUM_THREADS) hist[e] = 0u;
-        __syncthreads();
-        for (int64_t i = tid; i < N; i += SUM_THREADS) {
-            const uint32_t k = staged ? keys[i] : float_key(beta[i * p + j]);
-            const uint32_t wv = staged ? wts[i] : wfix[i];
-            if (wv == 0u) continue;
-            const uint32_t dig = (k >> shift) & (uint32_t)(nb - 1);
-            if (pass == 0) {
-                atomicAdd(&hist[dig], wv);
-            } else {
-                const uint32_t pre = k >> (shift + bits);
-                for (int q = 0; q < nq; ++q) {
-                    if (bins[q][0] < 0) continue;
-                    const uint32_t want =
-                        (pass == 1) ? (uint32_t)bins[q][0] : (((uint32_t)bins[q][0] << 11) | (uint32_t)bins[q][1]);
-                    if (pre == want) atomicAdd(&hist[q * nb + dig], wv);
-                }
+        if (pass > 0) {
+            uint32_t want[8];
+            bool on[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                on[q] = q < nq && bins[q][0] >= 0;
+                want[q] = on[q] ? ((pass == 1) ? (uint32_t)bins[q][0] : (((uint32_t)bins[q][0] << 11) | (uint32_t)bins[q][1]))
+                                : 0u;
             }
+            for (int e = tid; e < nq * nb; e += SUM_THREADS) hist[e] = 0u;
+            __syncthreads();
+            for (int64_t i = tid; i < N; i += SUM_THREADS) {
+                const uint32_t k = staged ? keys[i] : kcol[i];
+                const uint32_t wv = staged ? wts[i] : wfix[i];
+                if (wv == 0u) continue;
+                const uint32_t dig = (k >> shift) & (uint32_t)(nb - 1);
+                const uint32_t pre = k >> (shift + bits);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (on[q] && pre == want[q]) atomicAdd(&hist[q * nb + dig], wv);
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (w < nq) {
             const int q = w;
-            const unsigned long long target = (unsigned long long)ceil(sa.q[q] * 2147483648.0);
+            const unsigned long long target = sa.target[q];
             int b = -1;
             if (tot >= target && (pass == 0 || bins[q][0] >= 0)) {
                 unsigned long long bl = below[q];
@@ -1049,6 +1185,46 @@ __global__ void __launch_bounds__(SUM_THREADS, 1) k_summaries(const float* __res
         else
             key = ((uint32_t)bins[q][0] << 21) | ((uint32_t)bins[q][1] << 10) | (uint32_t)bins[q][2];
         quant[((int64_t)t * p + j) * nq + q] = (double)key_float(key);
+    }
+}
+
+// ------------------------------------------------ scale-marginalised summaries
+// Section 4, eq. all_particles: with a uniform prior on log b over the log-spaced
+// schedule, the particle systems of all steps mix with weights Z_t / Z_1, each the running
+// product of the Z_t / Z_{t-1} estimates: w_t = exp(L_t - max L) / sum_s exp(L_s - max L),
+// L_t = sum_{s=1..t} inc_s (the t = 0 evidence is common to every L_t). One thread, in
+// step order (T is a few hundred).
+__global__ void k_marginal_weights(const double* __restrict__ log_z_inc, int64_t T, double* __restrict__ post_c)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double acc = 0.0, m = -DBL_MAX;
+    for (int64_t t = 0; t < T; ++t) {
+        if (t > 0) acc += log_z_inc[t];
+        post_c[t] = acc;
+        m = fmax(m, acc);
+    }
+    double s = 0.0;
+    for (int64_t t = 0; t < T; ++t) s += exp(post_c[t] - m);
+    for (int64_t t = 0; t < T; ++t) post_c[t] = exp(post_c[t] - m) / s;
+}
+
+// Mixture of the per-step summaries: thread (j, v) sums w_t * mean[t][j] (v = 0) or
+// w_t * conc[t][j][v - 1] over t in order.
+__global__ void k_marginal_apply(const double* __restrict__ post_c, const double* __restrict__ mean,
+                                 const double* __restrict__ conc, int64_t T, int64_t p, int D,
+                                 double* __restrict__ mean_out, double* __restrict__ conc_out)
+{
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p * (1 + D)) return;
+    const int64_t j = e / (1 + D);
+    const int v = (int)(e - j * (1 + D));
+    double acc = 0.0;
+    if (v == 0) {
+        for (int64_t t = 0; t < T; ++t) acc += post_c[t] * mean[t * p + j];
+        mean_out[j] = acc;
+    } else {
+        for (int64_t t = 0; t < T; ++t) acc += post_c[t] * conc[(t * p + j) * D + (v - 1)];
+        conc_out[j * D + (v - 1)] = acc;
     }
 }
 
@@ -1120,7 +1296,10 @@ static unsigned elem_grid(int64_t total)
 
 cudaError_t smc_init_attributes()
 {
-    return cudaFuncSetAttribute(k_summaries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SUM_STAGED_MAX);
+    cudaError_t e = cudaFuncSetAttribute(k_summaries, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SUM_STAGED_MAX);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_move_site, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SITE_SMEM_MAX);
+    return e;
 }
 
 cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const double* sched, int t0,
@@ -1175,6 +1354,25 @@ cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, P
         else
             k_move_commit<false, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
     }
+    return cudaGetLastError();
+}
+
+int site_warps_per_block(int64_t n, int p)
+{
+    const int64_t per = (n + p) * (int64_t)sizeof(float);
+    int64_t w = (int64_t)SITE_SMEM_MAX / (per > 0 ? per : 1);
+    if (w > 8) w = 8;
+    return (int)w;
+}
+
+cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const double* sched, int t,
+                             uint32_t m0, int M, const uint64_t* seed, cudaStream_t st)
+{
+    if (M <= 0) return cudaSuccess;
+    const int wpc = site_warps_per_block(n, p);
+    if (wpc < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)wpc * (size_t)(n + p) * sizeof(float);
+    k_move_site<<<(unsigned)((N + wpc - 1) / wpc), 32 * wpc, smem, st>>>(a, N, p, (int)n, pr, sched, t, m0, M, seed);
     return cudaGetLastError();
 }
 
@@ -1275,14 +1473,39 @@ cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p
 }
 
 cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p,
-                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, cudaStream_t st)
+                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
+                             cudaStream_t st)
 {
-    const int nh = s.nq > 1 ? s.nq : 1;
-    const size_t hist_bytes = (size_t)nh * 2048 * sizeof(uint32_t);
+    k_keys_transpose<<<dim3((unsigned)((N + 31) / 32), (unsigned)((p + 31) / 32)), dim3(32, 8), 0, st>>>(beta, N, p,
+                                                                                                      keysT);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    SummaryArgs a = s;
+    // host-side constants: the smallest float >= Delta (the open interval |b| < Delta tested
+    // in FP32) and the fixed-point quantile targets ceil(q 2^31)
+    for (int d = 0; d < 8; ++d) {
+        float f = (float)a.delta[d];
+        if ((double)f < a.delta[d]) f = std::nextafter(f, INFINITY);
+        a.dthr[d] = f;
+    }
+    for (int q = 0; q < 8; ++q) a.target[q] = (unsigned long long)std::ceil(a.q[q] * 2147483648.0);
+    const int nh = (quant && s.nq > 0) ? (s.nq > SUM_SUB ? s.nq : SUM_SUB) : 0;
+    const size_t hist_bytes = (size_t)nh * SUM_BINS * sizeof(uint32_t);
     const size_t staged_bytes = (size_t)N * 2 * sizeof(uint32_t) + hist_bytes;
     const int staged = staged_bytes <= SUM_STAGED_MAX ? 1 : 0;
     const size_t bytes = staged ? staged_bytes : hist_bytes;
-    k_summaries<<<(unsigned)p, SUM_THREADS, bytes, st>>>(beta, Wf, wfix, N, p, s, t, mean, quant, conc, staged);
+    k_summaries<<<(unsigned)p, SUM_THREADS, bytes, st>>>(keysT, Wf, wfix, N, p, a, t, mean, quant, conc, staged);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
+                            int D, double* post_c, double* mean_out, double* conc_out, cudaStream_t st)
+{
+    k_marginal_weights<<<1, 32, 0, st>>>(log_z_inc, T, post_c);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t work = p * (1 + D);
+    k_marginal_apply<<<(unsigned)((work + 127) / 128), 128, 0, st>>>(post_c, mean, conc, T, p, D, mean_out, conc_out);
     return cudaGetLastError();
 }
 

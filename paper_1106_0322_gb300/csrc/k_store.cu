@@ -124,6 +124,23 @@ __global__ void k_store_pack_t(const int8_t* __restrict__ G, const uint8_t* __re
     }
 }
 
+// XT2[j][i] = x_ij log2(e): the standardised genotypes marker-major, for the
+// single-coordinate kernel's coalesced column reads. 32 x 32 tiles through shared memory.
+__global__ void k_store_xt2(const float* __restrict__ Xf, int64_t n, int64_t p, float* __restrict__ XT2)
+{
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r, j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < n && j < p) ? Xf[i * p + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t j = j0 + r, i = i0 + threadIdx.x;
+        if (i < n && j < p) XT2[j * n + i] = (float)((double)tile[threadIdx.x][r] * LOG2E);
+    }
+}
+
 __global__ void k_store_ybits(const uint8_t* __restrict__ y, int64_t n, int64_t words, uint32_t* __restrict__ ybits)
 {
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,6 +154,13 @@ __global__ void k_store_ybits(const uint8_t* __restrict__ y, int64_t n, int64_t 
 }
 
 }  // namespace
+
+cudaError_t launch_store_xt2(const float* Xf, int64_t n, int64_t p, float* XT2, cudaStream_t st)
+{
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((p + 31) / 32));
+    k_store_xt2<<<grid, dim3(32, 8), 0, st>>>(Xf, n, p, XT2);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_store_ybits(const uint8_t* y, int64_t n, int64_t words, uint32_t* ybits, cudaStream_t st)
 {

@@ -64,6 +64,7 @@ struct Workspace {
     float* Wf = nullptr;
     uint32_t* wfix = nullptr;
     double *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
+    uint32_t* keysT = nullptr;  // [p][N] order-preserving keys of beta for the summaries
     unsigned int* lse_counter = nullptr;
     float4* colpart = nullptr;
     float* h = nullptr;  // MALA step h = lambda p^(-1/6)
@@ -136,6 +137,7 @@ struct spa_ctx {
     int mapB_BN = 0;
     __nv_bfloat16* GT = nullptr;  // [p][n_r] for the adjoint
     float* yv = nullptr;
+    float* XT2 = nullptr;  // [p][n] X^T log2(e) for the single-coordinate kernel
     uint32_t* ybits = nullptr;  // y as a bitmask, one word per 32 individuals
     int64_t ywords = 0;
     int64_t n_r = 0;
@@ -216,7 +218,7 @@ void free_workspace(Workspace& w)
 {
     dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
     dfree(w.lpt_p); dfree(w.ydq); dfree(w.llq); dfree(w.lpq); dfree(w.llq_tmp); dfree(w.lpq_tmp);
-    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
+    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.keysT); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
     dfree(w.lse_scratch); dfree(w.lse_counter);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
     dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
@@ -332,6 +334,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     WA(A, N_pad * 2 * c->Kp);
     WA(lpt_p, N); WA(ydq, N); WA(llq, N); WA(lpq, N); WA(llq_tmp, N); WA(lpq_tmp, N);
     WA(ll, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
+    WA(keysT, N * p);
     WA(cum, N + nblk + 1);
     WA(colpart, (int64_t)COLSTAT_SPLITS * p);
     WA(lambda, 1);
@@ -544,6 +547,11 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     if (M <= 0) return;
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
+    if (c->cfg.move_kind == SPA_MOVE_SITE) {  // all M cycles in one launch
+        const SiteArgs sa{w.beta, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
+        q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.sched, t, m0, M, c->rb.seed, q.st));
+        return;
+    }
     const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
     const MoveArgs a = move_args(c, acc);
     const int p = (int)c->p;
@@ -593,7 +601,9 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     const bool tc = cfg.precision == SPA_PREC_SPLIT_BF16;
     const bool mala = cfg.move_kind == SPA_MOVE_MALA;
     const int p = (int)c->p;
-    const double denom = (double)w.N * (double)M;
+    const bool site = cfg.move_kind == SPA_MOVE_SITE;
+    // acceptance is per proposal: per coordinate update for the single-coordinate cycle
+    const double denom = (double)w.N * (double)M * (site ? (double)p : 1.0);
     SummaryArgs sa;
     sa.nq = cfg.n_quantiles;
     sa.nd = cfg.n_deltas;
@@ -629,7 +639,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
         for (int b = 0; b < cfg.burn_in_steps; ++b) {
             unsigned long long* scratch = r.acc + T;
             if (q.e == cudaSuccess) q.e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), q.st);
-            enq_colstats(q, 0);
+            if (!site) enq_colstats(q, 0);
             enq_moves(q, 0, m_base, M, scratch);
             if (mala) q.ck(launch_adapt_lambda(w.lambda, scratch, denom, q.st));
             m_base += (uint32_t)M;
@@ -644,9 +654,10 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
             ++q.launches;
         }
         enq_resample(q, (int)t);
-        enq_colstats(q, (int)t);
+        if (!site) enq_colstats(q, (int)t);
         enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
-        q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, q.st));
+        q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
+        ++q.launches;  // the key transpose and the summaries
         if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
     }
     q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
@@ -656,7 +667,13 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
 
 int validate_config(spa_ctx* c, const spa_config& k)
 {
-    if (k.move_kind != SPA_MOVE_RW && k.move_kind != SPA_MOVE_MALA) return fail(c, SPA_EINVAL, "move_kind");
+    if (k.move_kind != SPA_MOVE_RW && k.move_kind != SPA_MOVE_MALA && k.move_kind != SPA_MOVE_SITE)
+        return fail(c, SPA_EINVAL, "move_kind");
+    if (k.move_kind == SPA_MOVE_SITE) {
+        if (!(k.site_sd > 0.0) || !std::isfinite(k.site_sd)) return fail(c, SPA_EINVAL, "site_sd must be finite and > 0");
+        if (c && site_warps_per_block(c->n, (int)c->p) < 1)
+            return fail(c, SPA_EINVAL, "n + p too large for the single-coordinate kernel's shared memory");
+    }
     if (k.precision != SPA_PREC_SPLIT_BF16 && k.precision != SPA_PREC_FP32) return fail(c, SPA_EINVAL, "precision");
     if (k.init_mode != SPA_INIT_PRIOR_IS && k.init_mode != SPA_INIT_RESAMPLE_MOVE) return fail(c, SPA_EINVAL, "init_mode");
     if (k.burn_in_steps < 0) return fail(c, SPA_EINVAL, "burn_in_steps");
@@ -685,6 +702,7 @@ int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
        "store pack");
     CK(launch_store_pack_t(c->G, c->y, n, p, c->n_r, c->GT, c->yv, st), "store pack transposed");
     CK(launch_store_ybits(c->y, n, c->ywords, c->ybits, st), "store y bits");
+    CK(launch_store_xt2(c->Xf, n, p, c->XT2, st), "store X transposed");
     return read_error_word(c);
 }
 
@@ -696,7 +714,7 @@ void destroy(spa_ctx* c)
     free_runbufs(c->rb);
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
-    dfree(c->ybits);
+    dfree(c->ybits); dfree(c->XT2);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -829,6 +847,7 @@ void spa_config_default(spa_config* k)
     k->rw_scale = 2.38;
     k->mala_h = 1.65;
     k->sd_floor = 1e-3;
+    k->site_sd = 0.5;
     k->stream = nullptr;
 }
 
@@ -867,6 +886,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     c->n_r = round_up(n, 64);
     CA(GT, p * c->n_r);
     CA(yv, n);
+    CA(XT2, n * p);
     c->ywords = round_up(n, 256) / 32;
     CA(ybits, c->ywords);
     CA(d_err, 1);
@@ -1338,6 +1358,47 @@ int spa_incr_weight(double nu, double c_prev, double c_new, const float* B, int6
     return finish_free(e, "incremental weight");
 }
 
+int spa_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p, int32_t D,
+                 double* post_c, double* mean_out, double* conc_out)
+{
+    if (!log_z_inc || !mean || !post_c || !mean_out || T < 1 || p < 1 || D < 0 || D > SPA_MAX_DELTAS ||
+        (D > 0 && (!conc || !conc_out)))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    Scratch s;
+    double* dZ = s.get<double>(T);
+    double* dM = s.get<double>(T * p);
+    double* dC = s.get<double>(T * p * (D > 0 ? D : 1));
+    double* dP = s.get<double>(T);
+    double* dMo = s.get<double>(p);
+    double* dCo = s.get<double>(p * (D > 0 ? D : 1));
+    if (!dZ || !dM || !dC || !dP || !dMo || !dCo) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    cudaStream_t st = cudaStreamPerThread;
+    cudaError_t e = cudaMemcpyAsync(dZ, log_z_inc, sizeof(double) * (size_t)T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dM, mean, sizeof(double) * (size_t)(T * p), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && D > 0)
+        e = cudaMemcpyAsync(dC, conc, sizeof(double) * (size_t)(T * p * D), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_marginal(dZ, dM, dC, T, p, D, dP, dMo, dCo, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(post_c, dP, sizeof(double) * (size_t)T, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mean_out, dMo, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && D > 0)
+        e = cudaMemcpyAsync(conc_out, dCo, sizeof(double) * (size_t)(p * D), cudaMemcpyDeviceToHost, st);
+    return finish_free(e, "marginal");
+}
+
+int spa_marginal_device(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
+                        int32_t D, double* post_c, double* mean_out, double* conc_out, void* stream)
+{
+    if (!log_z_inc || !mean || !post_c || !mean_out || T < 1 || p < 1 || D < 0 || D > SPA_MAX_DELTAS ||
+        (D > 0 && (!conc || !conc_out)))
+        return fail(nullptr, SPA_EINVAL, "bad arguments");
+    if (check_device(nullptr) != SPA_OK) return SPA_EUNSUPPORTED;
+    const cudaError_t e = launch_marginal(log_z_inc, mean, conc, T, p, D, post_c, mean_out, conc_out,
+                                          static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return fail(nullptr, SPA_ECUDA, std::string("marginal: ") + cudaGetErrorString(e));
+    return SPA_OK;
+}
+
 int spa_lse_ess(const double* logw, int64_t N, double* lse, double* ess)
 {
     if (!logw || N < 1) return fail(nullptr, SPA_EINVAL, "bad arguments");
@@ -1391,12 +1452,13 @@ int spa_summaries(const float* B, const double* W, int64_t N, int64_t p, const d
     double* dM = s.get<double>(p);
     double* dQ = s.get<double>(p * (nq ? nq : 1));
     double* dC = s.get<double>(p * (nd ? nd : 1));
-    if (!dB || !dW || !dWf || !dFix || !dM || !dQ || !dC) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    uint32_t* dK = s.get<uint32_t>(N * p);
+    if (!dB || !dW || !dWf || !dFix || !dM || !dQ || !dC || !dK) return fail(nullptr, SPA_ENOMEM, "device allocation");
     cudaStream_t st = cudaStreamPerThread;
     cudaError_t e = cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(N * p), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dW, W, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_weight_forms(dW, N, dWf, dFix, st);
-    if (e == cudaSuccess) e = launch_summaries(dB, dWf, dFix, N, (int)p, sa, 0, dM, nq ? dQ : nullptr, dC, st);
+    if (e == cudaSuccess) e = launch_summaries(dB, dWf, dFix, N, (int)p, sa, 0, dM, nq ? dQ : nullptr, dC, dK, st);
     if (e == cudaSuccess && mean) e = cudaMemcpyAsync(mean, dM, sizeof(double) * (size_t)p, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && quant && nq)
         e = cudaMemcpyAsync(quant, dQ, sizeof(double) * (size_t)(p * nq), cudaMemcpyDeviceToHost, st);

@@ -27,7 +27,7 @@ enum : uint32_t {
     DERR_ESS = 8u,        // ESS < 1 (all weights non-finite)
 };
 
-constexpr uint32_t TAG_INIT = 1u, TAG_NORMAL = 2u, TAG_ACCEPT = 3u, TAG_RESAMPLE = 4u;
+constexpr uint32_t TAG_INIT = 1u, TAG_NORMAL = 2u, TAG_ACCEPT = 3u, TAG_RESAMPLE = 4u, TAG_SITE = 5u;
 
 // ---------------------------------------------------------------------- Philox
 __device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k)

@@ -32,6 +32,8 @@ cudaError_t launch_store_finish(const int8_t* G, int64_t n, int64_t p, int Kp, c
 
 cudaError_t launch_store_pack_t(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, int64_t n_r,
                                 __nv_bfloat16* GT, float* yv, cudaStream_t st);
+// XT2 [p][n] = X^T log2(e) (single-coordinate moves).
+cudaError_t launch_store_xt2(const float* Xf, int64_t n, int64_t p, float* XT2, cudaStream_t st);
 // y as a bitmask: bit (i % 32) of word i / 32 is y_i; words cover `words` * 32 individuals.
 cudaError_t launch_store_ybits(const uint8_t* y, int64_t n, int64_t words, uint32_t* ybits, cudaStream_t st);
 
@@ -100,6 +102,20 @@ struct MoveArgs {
     const float* h;              // step size
 };
 
+// The paper's single-coordinate cycle (move kind 2): M cycles over j = 0..p-1 per launch.
+struct SiteArgs {
+    float* beta;                      // particle states [N][p], updated in place
+    const float* XT2;                 // [p][n] standardised genotypes times log2(e)
+    const float* vy;                  // v = X^T y (nats)
+    float sd;                         // proposal standard deviation
+    unsigned long long* acc_count;   // accepted coordinate updates (may be NULL)
+};
+constexpr size_t SITE_SMEM_MAX = 220 * 1024;  // eta2 and beta rows of a block's particles
+// Particles per block (one warp each) for n individuals and p markers; 0 if one does not fit.
+int site_warps_per_block(int64_t n, int p);
+cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const double* sched, int t,
+                             uint32_t m0, int M, const uint64_t* seed, cudaStream_t st);
+
 // Random-walk move (decide: MH test of the pending proposal first; noise = 0: pack beta
 // unchanged, for the log-likelihood entry points and t = 0).
 cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
@@ -162,9 +178,18 @@ struct SummaryArgs {
     double q[8];
     int nd;
     double delta[8];
+    // filled by launch_summaries: the smallest float >= delta[d], and ceil(q 2^31)
+    float dthr[8];
+    unsigned long long target[8];
 };
+// keysT: N * p words of scratch (the transposed keys; two kernels).
 cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p,
-                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, cudaStream_t st);
+                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
+                             cudaStream_t st);
+
+// Scale-marginalised summaries (mixture over the steps with weights Z_t / Z_1).
+cudaError_t launch_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
+                            int D, double* post_c, double* mean_out, double* conc_out, cudaStream_t st);
 
 cudaError_t launch_accept_rate(const unsigned long long* acc_count, int T, double denom, double* rate,
                                cudaStream_t st);

@@ -154,12 +154,31 @@ WORKLOADS = {
                         N=16384, T=200, M=10, move="rw", seed=1002),
     "mala": dict(n=2000, p=200, rho=0.95, causal_beta=(0.3, 0.5, -0.4), nu=2.0,
                  N=8192, T=200, M=5, move="mala", seed=1003),
+    # The paper's own settings (Section 4.1, "Further details"): its single-coordinate
+    # cycle (M = 5 cycles per step), its schedules b_t = b_1 0.98^(t-1) run from diffuse to
+    # sparse, started by MCMC at the first scale (resample-move burn-in), on synthetic data
+    # of its two data sets' shapes (n = 500 / p = 50 with a = 1 and T = 450; the 18q region,
+    # n = 1859 / p = 184, with a = 4, b_1 = 1 and T = 250).
+    "paper-small": dict(n=500, p=50, rho=0.95, causal_beta=PAPER_CAUSAL_BETA, nu=1.0,
+                        N=8192, T=450, M=5, move="site", seed=1005, schedule=("paper", 2.0), burn_in=10),
+    "paper-18q": dict(n=1859, p=184, rho=0.95, causal_beta=PAPER_CAUSAL_BETA, nu=4.0,
+                      N=8192, T=250, M=5, move="site", seed=1006, schedule=("paper", 1.0), burn_in=10),
 }
 
 
 def workload_region(name: str) -> Region:
     w = WORKLOADS[name]
     return make_region(w["n"], w["p"], w["rho"], w["causal_beta"], w["seed"])
+
+
+def workload_schedule(name: str) -> np.ndarray:
+    """The workload's scale schedule c_t: geometric over log c in [-8, 0], sparse to
+    diffuse, or the paper's b_t = b_1 0.98^(t-1) (as c_t = b_t / a) when it names one."""
+    w = WORKLOADS[name]
+    sch = w.get("schedule")
+    if sch and sch[0] == "paper":
+        return paper_schedule(sch[1], w["T"], w["nu"])
+    return geometric_schedule(w["T"])
 
 
 def batched_regions(R: int = 64, seed: int = 1004):

@@ -199,3 +199,72 @@ def split_bound_local(G, B):
     from tests.test_gpu_parity import split_bound
 
     return split_bound(G, B, B.shape[1])
+
+
+def test_marginal_matches_oracle(spa):
+    rng = np.random.default_rng(9)
+    T, p, D = 37, 11, 2
+    res = {"log_z_inc": rng.normal(0, 3, T), "mean": rng.normal(0, 1, (T, p)), "conc": rng.uniform(0, 1, (T, p, D))}
+    g = spa.marginal(res)
+    o = oracle.marginal(res["log_z_inc"], res["mean"], res["conc"])
+    for k in ("post_c", "mean", "conc"):
+        assert np.allclose(g[k], o[k], rtol=1e-12, atol=1e-300), k
+
+
+def test_sweep_marginal_matches_quadrature(spa):
+    """The scale-marginalised posterior (Section 4, eq. all_particles) of GPU sweeps against
+    grid quadrature of sum_t Z(c_t) pi_{c_t} / sum_t Z(c_t), p = 1, a = 1."""
+    reg = synth.make_region(200, 1, 0.9, (0.6,), seed=2025)
+    sched = synth.geometric_schedule(16, -6.0, 0.0, sparse_to_diffuse=True)
+    runs = _gpu_runs(spa, reg, 1.0, sched, 2048, 4, spa.make_config(), list(range(300, 300 + R)))
+    post = Posterior(reg.G, reg.y, 1.0, sched)
+    lz = np.array([post.log_z(c) for c in sched])
+    w = np.exp(lz - lz.max())
+    w /= w.sum()
+    truth_mean = np.array([w @ np.array([post.mean(c)[0] for c in sched])])
+    truth_conc = np.array([w @ np.array([post.conc(c, 0.1)[0] for c in sched])])
+    margs = [spa.marginal(r) for r in runs]
+    _check(_zscores([m["mean"] for m in margs], truth_mean, 2e-4), "marginal mean")
+    _check(_zscores([m["conc"][:, 1] for m in margs], truth_conc, 2e-3), "marginal V(0.1)")
+    _check(_zscores([m["post_c"] for m in margs], w, 2e-3), "p(c | X, y)")
+
+
+# ------------------------------------------------ the paper's single-coordinate cycle
+def test_site_sweep_matches_oracle(spa):
+    """Move kind SITE (Section 4.1): M cycles of p single-coordinate random-walk updates,
+    GPU against the oracle in distribution (R seeds each)."""
+    reg = synth.make_region(400, 12, 0.95, (0.4, -0.3), seed=1101)
+    sched = synth.geometric_schedule(8, -5.0, 0.0)
+    g = _gpu_runs(spa, reg, 1.0, sched, 512, 2, spa.make_config(move="site"), list(range(1, R + 1)))
+    ocfg = oracle.make_config(move="site")
+    o = [oracle.run(reg.G, reg.y, 1.0, sched, 512, 2, seed=700 + s, cfg=ocfg) for s in range(R)]
+    _check(_two_sample_z([r["mean"] for r in g], [r["mean"] for r in o], 2e-4), "mean")
+    _check(_two_sample_z([r["conc"] for r in g], [r["conc"] for r in o], 2e-3), "conc")
+    _check(_two_sample_z([r["accept_rate"] for r in g], [r["accept_rate"] for r in o], 2e-3), "acceptance")
+    for r in g:
+        assert np.all((r["accept_rate"] > 0.0) & (r["accept_rate"] < 1.0))
+
+
+def test_site_same_seed_first_step_agrees(spa):
+    """Both sides draw the same Philox blocks for every coordinate update, so with one seed
+    the first step's accept decisions coincide except near ties and the means agree closely."""
+    reg = synth.make_region(300, 6, 0.9, (0.5,), seed=1102)
+    sched = synth.geometric_schedule(3, -3.0, 0.0)
+    with spa.Region(reg.G, reg.y, 1.0, config=spa.make_config(move="site")) as r:
+        g = r.run(sched, 256, 1, 11)
+    o = oracle.run(reg.G, reg.y, 1.0, sched, 256, 1, seed=11, cfg=oracle.make_config(move="site"))
+    assert abs(g["accept_rate"][0] - o["accept_rate"][0]) < 0.01
+    assert np.max(np.abs(g["mean"][0] - o["mean"][0])) < 5e-3
+
+
+@pytest.mark.parametrize("p,a,direction,lo", [(1, 1.0, "s2d", -6.0), (2, 4.0, "d2s", -4.5)])
+def test_site_sweep_matches_quadrature(spa, p, a, direction, lo):
+    reg = synth.make_region(200, p, 0.9, (0.6,) * p, seed=2024 + p)
+    sched = synth.geometric_schedule(16, lo, 0.0, sparse_to_diffuse=(direction == "s2d"))
+    init = "prior_is" if direction == "s2d" else "resample_move"
+    cfg = spa.make_config(move="site", init=init, burn_in_steps=25)
+    runs = _gpu_runs(spa, reg, a, sched, 2048, 4, cfg, list(range(100, 100 + R)))
+    post = Posterior(reg.G, reg.y, a, sched)
+    _check(_zscores([r["mean"] for r in runs], np.array([post.mean(c) for c in sched]), 2e-4), "mean")
+    _check(_zscores(np.stack([np.cumsum(r["log_z_inc"]) for r in runs]), np.array([post.log_z(c) for c in sched]),
+                    2e-3), "log Z")

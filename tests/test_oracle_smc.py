@@ -55,7 +55,8 @@ def _runs(reg, a, sched, N, M, move="rw", init="prior_is", burn=0):
 # below log c ~ -4.5 (32 seeds: bias 0.06 at log c = -6, 0.018 at -5, none resolvable at
 # -4.4): a property of the algorithm at this budget, so the quadrature pin stops there.
 SWEEPS = [(1, 1.0, "rw", "s2d", 0.9, -6.0), (2, 4.0, "rw", "d2s", 0.9, -4.5), (2, 2.0, "mala", "d2s", 0.9, -6.0),
-          (1, math.inf, "rw", "d2s", 0.9, -6.0), (2, 1.0, "rw", "d2s", 0.9, -6.0)]
+          (1, math.inf, "rw", "d2s", 0.9, -6.0), (2, 1.0, "rw", "d2s", 0.9, -6.0),
+          (2, 4.0, "site", "d2s", 0.9, -4.5), (1, 1.0, "site", "s2d", 0.9, -6.0)]
 
 
 @pytest.mark.parametrize("p,a,move,direction,rho,lo", SWEEPS)
@@ -86,7 +87,7 @@ def test_smc_sweep_matches_quadrature(p, a, move, direction, rho, lo):
         _check(_zscores(F, np.array(q_levels)[None, :], 2e-3), "quantiles")
 
 
-@pytest.mark.parametrize("move,a", [("rw", 1.0), ("mala", 4.0)])
+@pytest.mark.parametrize("move,a", [("rw", 1.0), ("mala", 4.0), ("site", 2.0)])
 def test_fixed_scale_mcmc_matches_quadrature(move, a):
     # Section 4.2: MCMC at a fixed scale, started with burn-in from prior draws.
     reg = synth.make_region(200, 2, 0.9, (0.5, -0.4), seed=77)
