@@ -334,6 +334,76 @@ def site_roofline(w, ms_per_step, clocks):
             "algorithmic_ops_per_sweep": ops, "note": "whole-sweep rate (the cycle kernel dominates the sweep)"}
 
 
+def matched_error(args):
+    """Split-BF16 against plain FP32 at matched posterior-mean error on one workload.
+
+    Gold: the mean over 16 seeds of the FP32 path at 4N. For each path and particle count
+    N' in {N/4, N/2, N, 2N}: 8 seeds, the RMSE over (t, j) of each seed's posterior means
+    against the gold, averaged over seeds, and the sweep's device time. The split path's
+    time at the FP32 path's error at N is interpolated in log-log (error ~ N'^-1/2)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    import paper_1106_0322_gb300 as spa
+    from paper_1106_0322_gb300 import synth
+
+    w = dict(synth.WORKLOADS[args.workload])
+    region = synth.workload_region(args.workload)
+    sched = synth.workload_schedule(args.workload)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    T, p = w["T"], w["p"]
+
+    def runs(precision, N, seeds):
+        cfg = spa.make_config(move=w["move"], precision=precision, stream=stream.cuda_stream)
+        reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
+        out = {"mean": torch.empty((T, p), dtype=torch.float64, device=dev)}
+        means, ms = [], []
+        reg.run_device(torch.tensor(sched, device=dev), N, w["M"], 1, out)  # graph + workspace
+        for s in seeds:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reg.run_device(torch.tensor(sched, device=dev), N, w["M"], s, out)
+            e1.record(stream)
+            e1.synchronize()
+            reg.sync()
+            ms.append(e0.elapsed_time(e1))
+            means.append(out["mean"].cpu().numpy().copy())
+        reg.close()
+        return np.array(means), float(np.median(ms))
+
+    N = w["N"]
+    gold_means, _ = runs("fp32", 4 * N, list(range(9000, 9016)))
+    gold = gold_means.mean(axis=0)
+    table = {}
+    for prec in ("split_bf16", "fp32"):
+        rows = []
+        for f in (0.25, 0.5, 1.0, 2.0):
+            Nf = int(N * f)
+            m, ms = runs(prec, Nf, list(range(100, 108)))
+            rmse = float(np.mean([np.sqrt(np.mean((mi - gold) ** 2)) for mi in m]))
+            rows.append({"N": Nf, "rmse": rmse, "ms": ms})
+        table[prec] = rows
+    target = next(r for r in table["fp32"] if r["N"] == N)
+    sp = table["split_bf16"]
+    le = np.log([r["rmse"] for r in sp])
+    lt = np.log([r["ms"] for r in sp])
+    order = np.argsort(le)
+    t_at = float(np.exp(np.interp(np.log(target["rmse"]), le[order], lt[order])))
+    line = {"metric": "SPA sweep wall time at matched posterior-mean error (split-BF16 vs plain FP32)",
+            "workload": workload_desc(dict(w, name=args.workload)),
+            "gold": "mean of 16 seeds of the FP32 path at 4N",
+            "fp32_at_N": target, "split_bf16_ms_at_matched_error": t_at,
+            "speedup_at_matched_error": target["ms"] / t_at, "table": table}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,12 +414,16 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--matched-error", action="store_true",
+                    help="split-BF16 vs plain FP32 wall time at matched posterior-mean error (one JSON line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
 
     from paper_1106_0322_gb300 import synth
 
+    if args.matched_error:
+        return matched_error(args)
     if args.workload == "batched":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no reference-arm sample; "

@@ -979,23 +979,36 @@ __device__ int warp_find_bin(const uint32_t* hist, int nbins, unsigned long long
     const unsigned int hit = __ballot_sync(0xffffffffu, base + incl >= target);
     if (hit == 0u) return -1;
     const int L = __ffs(hit) - 1;
+    // inside lane L's range: the whole warp scans its `per` bins, `per / 32` per lane
+    const unsigned long long start = __shfl_sync(0xffffffffu, base + incl - mine, L);
+    const int sub = per / 32;  // bins per lane (per is a multiple of 32)
+    const uint32_t* rng = hist + L * per + lane * sub;
+    unsigned long long part = 0;
+    for (int k = 0; k < sub; ++k) part += rng[k];
+    unsigned long long inc2 = part;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, inc2, o);
+        if (lane >= o) inc2 += v;
+    }
+    const unsigned int hit2 = __ballot_sync(0xffffffffu, start + inc2 >= target);
+    const int L2 = __ffs(hit2) - 1;  // lane L's total reaches the target, so some lane does
     int bin = -1;
-    unsigned long long add = 0;
-    if (lane == L) {
-        unsigned long long cum = base + incl - mine;
-        for (int k = 0; k < per; ++k) {
-            const unsigned long long h = hist[L * per + k];
+    unsigned long long cum = 0;
+    if (lane == L2) {
+        cum = start + inc2 - part;
+        for (int k = 0; k < sub; ++k) {
+            const unsigned long long h = rng[k];
             if (cum + h >= target) {
-                bin = L * per + k;
+                bin = L * per + L2 * sub + k;
                 break;
             }
             cum += h;
         }
-        add = cum - base;
     }
-    bin = __shfl_sync(0xffffffffu, bin, L);
-    add = __shfl_sync(0xffffffffu, add, L);
-    if (bin >= 0) *below = base + add;
+    bin = __shfl_sync(0xffffffffu, bin, L2);
+    cum = __shfl_sync(0xffffffffu, cum, L2);
+    if (bin >= 0) *below = cum;
     return bin;
 }
 
@@ -1029,7 +1042,7 @@ constexpr int SUM_BINS = 2048;  // bins of an 11-bit digit
 // 10 bits from the top. The first digit's histogram is built while the values are loaded,
 // in SUM_SUB copies that are merged before the search (particles cluster in a few
 // top-digit bins, and one copy per warp group spreads their atomics).
-__global__ void __launch_bounds__(SUM_THREADS, 1) k_summaries(const uint32_t* __restrict__ keysT, const float* __restrict__ Wf,
+__global__ void __launch_bounds__(SUM_THREADS, 2) k_summaries(const uint32_t* __restrict__ keysT, const float* __restrict__ Wf,
                                                                const uint32_t* __restrict__ wfix, int64_t N, int p,
                                                                SummaryArgs sa, int t, double* __restrict__ mean,
                                                                double* __restrict__ quant, double* __restrict__ conc,
