@@ -73,6 +73,8 @@ typedef struct spa_config {
     double mala_h;           /* MALA: initial lambda in h = lambda * p^(-1/6) (1.65) */
     double sd_floor;         /* floor of the proposal scale relative to c (default 1e-3) */
     double site_sd;          /* SITE: proposal sd of one coordinate (0.5: the paper's variance 0.25) */
+    int32_t map_path;        /* nonzero: record each step's particle of highest posterior density,
+                                for spa_map_path after the run (default 0) */
     void* stream;            /* cudaStream_t to run on; NULL: the context's own stream */
 } spa_config;
 
@@ -215,6 +217,29 @@ int spa_marginal(const double* log_z_inc, const double* mean, const double* conc
                  double* post_c, double* mean_out, double* conc_out);
 int spa_marginal_device(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
                         int32_t D, double* post_c, double* mean_out, double* conc_out, void* stream);
+
+/* MAP estimates by EM (Section 2.1). The scale-mixture representation makes each EM step
+ * a weighted-L1 logistic regression, beta <- argmax l(beta) - sum_j w_j |beta_j| with
+ * w_j = (a+1)/(a c + |beta_j|) (double exponential: 1/c), iterated until no coordinate
+ * moves by more than tol (or max_em steps). The inner problem is solved on the GPU by
+ * proximal-gradient steps with momentum and restarts, in FP32, to a tenth of tol.
+ *
+ * spa_map: S independent solves at scale c > 0 from beta0 [S][p] (host, FP32); beta_out
+ * [S][p] receives the modes and logpost [S] (may be NULL) l + log p at them (FP64, the
+ * constant -p log 2c included). Blocks until done.
+ *
+ * spa_map_path (Section 4.1): after a spa_run / spa_run_device of T steps with
+ * config.map_path set, at each step t the EM starts from the step's particle of highest
+ * posterior density and (t > 0) from the previous step's MAP, and the mode with the higher
+ * log posterior is kept: map_out [T][p] (host, FP32), logpost [T] (host, may be NULL).
+ * One thread block walks the steps in order. Blocks until done.
+ *
+ * Errors: SPA_EINVAL (NULL arguments, S or T < 1, c <= 0, max_em < 1, tol <= 0, no recorded
+ * run of T steps with map_path, or n + 5p too large for one block's shared memory),
+ * SPA_ENOMEM, SPA_ECUDA. */
+int spa_map(spa_ctx* ctx, const float* beta0, int32_t S, double c, int32_t max_em, double tol, float* beta_out,
+            double* logpost);
+int spa_map_path(spa_ctx* ctx, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost);
 
 /* ------------------------------------------------------- per-step entry points */
 

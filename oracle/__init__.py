@@ -107,6 +107,9 @@ def _load():
         lib.or_marginal.argtypes = [P(C.c_double), P(C.c_double), P(C.c_double), C.c_int64, C.c_int64, C.c_int,
                                     P(C.c_double), P(C.c_double), P(C.c_double)]
         lib.or_marginal.restype = C.c_int
+        lib.or_map.argtypes = [P(C.c_int8), P(C.c_uint8), C.c_int64, C.c_int64, C.c_double, C.c_double, P(C.c_double),
+                               C.c_int32, C.c_double, P(C.c_double), P(C.c_double)]
+        lib.or_map.restype = C.c_int
         _lib = lib
         return lib
 
@@ -220,6 +223,20 @@ def weighted_quantile(vals, W, qs) -> np.ndarray:
 
 def max_threads() -> int:
     return int(_load().or_max_threads())
+
+
+def map_em(G, y, a: float, c: float, beta0, max_em: int = 500, tol: float = 1e-10):
+    """MAP by EM from beta0 (Section 2.1): returns (mode, log l + log p at the mode)."""
+    G = np.ascontiguousarray(G, dtype=np.int8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    b0 = np.ascontiguousarray(beta0, dtype=np.float64)
+    n, p = G.shape
+    out = np.zeros(p)
+    lp = C.c_double(0.0)
+    if _load().or_map(_p(G, C.c_int8), _p(y, C.c_uint8), n, p, float(a), float(c), _p(b0, C.c_double), int(max_em),
+                      float(tol), _p(out, C.c_double), C.byref(lp)) != 0:
+        raise ValueError("or_map: bad input")
+    return out, lp.value
 
 
 def marginal(log_z_inc, mean, conc) -> dict:

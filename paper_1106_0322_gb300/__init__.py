@@ -48,6 +48,7 @@ class Config(C.Structure):
         ("mala_h", C.c_double),
         ("sd_floor", C.c_double),
         ("site_sd", C.c_double),
+        ("map_path", C.c_int32),
         ("stream", C.c_void_p),
     ]
 
@@ -84,6 +85,9 @@ _SIGS = {
     "spa_batch_destroy": (None, [C.c_void_p]),
     "spa_last_launch_count": (C.c_int64, [C.c_void_p]),
     "spa_loglik_tile_width": (C.c_int, [C.c_void_p]),
+    "spa_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
+                          C.c_void_p]),
+    "spa_map_path": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
     "spa_loglik_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "spa_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_loglik_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -155,7 +159,8 @@ def default_config() -> Config:
 
 def make_config(move: str = "rw", precision: str = "split_bf16", init: str = "prior_is", burn_in_steps: int = 0,
                 quantiles=(0.05, 0.5, 0.95), deltas=(0.05, 0.1), ess_frac: float = 0.75, rw_scale: float = 2.38,
-                mala_h: float = 1.65, sd_floor: float = 1e-3, site_sd: float = 0.5, stream: int = 0) -> Config:
+                mala_h: float = 1.65, sd_floor: float = 1e-3, site_sd: float = 0.5, map_path: bool = False,
+                stream: int = 0) -> Config:
     cfg = default_config()
     cfg.move_kind = {"rw": MOVE_RW, "mala": MOVE_MALA, "site": MOVE_SITE}[move]
     cfg.precision = {"split_bf16": PREC_SPLIT_BF16, "fp32": PREC_FP32}[precision]
@@ -172,6 +177,7 @@ def make_config(move: str = "rw", precision: str = "split_bf16", init: str = "pr
     cfg.mala_h = mala_h
     cfg.sd_floor = sd_floor
     cfg.site_sd = site_sd
+    cfg.map_path = 1 if map_path else 0
     cfg.stream = stream or None
     return cfg
 
@@ -251,6 +257,24 @@ class Region:
 
     def last_launch_count(self) -> int:
         return int(load().spa_last_launch_count(self._h))
+
+    def map(self, beta0, c: float, max_em: int = 200, tol: float = 1e-5):
+        """MAP by EM (Section 2.1) from each row of beta0 [S, p] at scale c: (modes [S, p],
+        log posteriors [S])."""
+        b0 = np.ascontiguousarray(np.atleast_2d(beta0), dtype=np.float32)
+        S = b0.shape[0]
+        out = np.zeros_like(b0)
+        lp = np.zeros(S)
+        _check(load().spa_map(self._h, _ptr(b0), S, float(c), int(max_em), float(tol), _ptr(out), _ptr(lp)), self._h)
+        return out, lp
+
+    def map_path(self, T: int, max_em: int = 200, tol: float = 1e-5):
+        """The MAP path (Section 4.1) of the last run (config map_path=True): (map [T, p],
+        log posteriors [T])."""
+        out = np.zeros((T, self.p), np.float32)
+        lp = np.zeros(T)
+        _check(load().spa_map_path(self._h, int(T), int(max_em), float(tol), _ptr(out), _ptr(lp)), self._h)
+        return out, lp
 
     def loglik_tile_width(self) -> int:
         """n-tile width of the tensor-core likelihood kernel (0 before the first run)."""

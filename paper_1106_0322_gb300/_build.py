@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libspa.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["k_store.cu", "k_smc.cu", "k_loglik_tc.cu", "k_loglik_simt.cu", "spa_capi.cu", "spa_noalloc.cu"]
+SOURCES = ["k_store.cu", "k_smc.cu", "k_loglik_tc.cu", "k_loglik_simt.cu", "k_map.cu", "spa_capi.cu", "spa_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -190,6 +190,10 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // everything above is independent of the previous kernel; what follows reads A and
+    // writes the partials the previous kernel may still be reading
+    grid_dependency_wait();
+    grid_launch_dependents();
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
@@ -578,10 +582,21 @@ cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const Tc
                       cudaStream_t st)
 {
     using C = TcCfg<BN, STAGES, AR>;
-    k_loglik_tc<BN, STAGES, RESID, AR><<<plan.grid, Epi<RESID>::THREADS, C::SMEM, st>>>(
-        mapA, mapB, plan.n_tiles, plan.m_tiles, plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits,
-        ra ? ra->R : nullptr, ra ? ra->n_r : 0, ra ? ra->rsum_part : nullptr);
-    return cudaGetLastError();
+    // programmatic dependent launch: the prologue (barriers, TMEM, descriptor prefetch)
+    // overlaps the previous kernel's tail; the kernel waits for it before touching data
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.grid);
+    cfg.blockDim = dim3(Epi<RESID>::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, mapA, mapB, plan.n_tiles, plan.m_tiles,
+                              plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
+                              ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr);
 }
 
 }  // namespace

@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
     __shared__ float shk[3];
     if (DECIDE && threadIdx.x == 0) blk = 0;
     step_constants(pr, sched, t, shk);
+    grid_dependency_wait();  // the previous kernel (the likelihood GEMM) has finished
+    grid_launch_dependents();
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
     if (i < N) {
@@ -444,6 +446,25 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
         }
         for (int j = lane; j < p; j += 32) bg[j] = brow[j];
         if (lane == 0 && nacc) atomicAdd(&blk, nacc);
+        // the MH state at the end of the step, in the units the move kernels keep it:
+        // l = beta . v - ln 2 (sum_i max(eta2_i, 0) + sum of the lanes' log products), and the
+        // log-prior term sum
+        if (a.llq) {
+            float mx = 0.0f, yd = 0.0f;
+            FSum lt;
+            for (int r = lane; r < n; r += 32) mx += fmaxf(eta[r], 0.0f);
+            for (int j = lane; j < p; j += 32) {
+                yd = fmaf(brow[j], a.vy[j], yd);
+                lt.add(prior_term(brow[j], ac, pr.de));
+            }
+            const float sp2 = warp_sum(mx + lq);
+            yd = warp_sum(yd);
+            lt = warp_sum(lt);
+            if (lane == 0) {
+                a.llq[i] = make_float2((yd - 0.69314718f * sp2) * a.inv_sp_scale, 0.0f);
+                a.lpq[i] = make_float2(lt.s, lt.c);
+            }
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && blk && a.acc_count) atomicAdd(a.acc_count, (unsigned long long)blk);
@@ -462,6 +483,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
     __shared__ float shk[3];
     if (threadIdx.x == 0) blk = 0;
     step_constants(pr, sched, t, shk);
+    grid_dependency_wait();
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
     if (i < N) {
@@ -1299,6 +1321,26 @@ __global__ void k_prior_logpdf(PriorArgs pr, double c, const float* beta, int64_
 }  // namespace
 
 // ======================================================================= launchers
+// Launch configuration with programmatic stream serialization (programmatic dependent
+// launch): the kernel may be scheduled while its predecessor drains and waits for it with
+// grid_dependency_wait before reading anything the predecessor wrote.
+static cudaLaunchConfig_t pdl_config(unsigned grid, unsigned block, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    return cfg;
+}
+static void pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&attr)[1])
+{
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+}
+
 static unsigned warps_grid(int64_t N) { return (unsigned)((N + WARPS - 1) / WARPS); }
 static unsigned elem_grid(int64_t total)
 {
@@ -1327,11 +1369,13 @@ cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, Pri
 {
     const bool vec = (p & 3) == 0;
     const unsigned grid = warps_grid(N);
-    if (decide) {
+    if (decide) {  // follows the likelihood GEMM: programmatic dependent launch
+        cudaLaunchConfig_t cfg = pdl_config(grid, BLOCK, st);
+        cudaLaunchAttribute attr[1];
+        pdl_attr(cfg, attr);
         if (vec)
-            k_move_rw<true, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
-        else
-            k_move_rw<true, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+            return cudaLaunchKernelEx(&cfg, k_move_rw<true, true>, a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+        return cudaLaunchKernelEx(&cfg, k_move_rw<true, false>, a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
     } else {
         if (vec)
             k_move_rw<false, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
@@ -1355,19 +1399,15 @@ cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, P
                                uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
     const bool vec = (p & 3) == 0;
-    const unsigned grid = warps_grid(N);
+    cudaLaunchConfig_t cfg = pdl_config(warps_grid(N), BLOCK, st);  // follows the likelihood GEMM
+    cudaLaunchAttribute attr[1];
+    pdl_attr(cfg, attr);
     if (mala) {
-        if (vec)
-            k_move_commit<true, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
-        else
-            k_move_commit<true, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
-    } else {
-        if (vec)
-            k_move_commit<false, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
-        else
-            k_move_commit<false, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m_prev, seed, err);
+        if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<true, true>, a, N, p, pr, sched, t, m_prev, seed, err);
+        return cudaLaunchKernelEx(&cfg, k_move_commit<true, false>, a, N, p, pr, sched, t, m_prev, seed, err);
     }
-    return cudaGetLastError();
+    if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<false, true>, a, N, p, pr, sched, t, m_prev, seed, err);
+    return cudaLaunchKernelEx(&cfg, k_move_commit<false, false>, a, N, p, pr, sched, t, m_prev, seed, err);
 }
 
 int site_warps_per_block(int64_t n, int p)

@@ -92,6 +92,7 @@ struct RunBufs {
     unsigned long long* acc = nullptr;
     uint8_t* res = nullptr;
     uint64_t* seed = nullptr;
+    float* best = nullptr;  // [T][p] each step's particle of highest posterior density (map_path)
 };
 
 struct GraphKey {
@@ -151,6 +152,9 @@ struct spa_ctx {
     uint64_t gen = 0;  // bumped whenever captured work may refer to stale buffers or config
     int64_t graph_launches = 0;
     int64_t last_launches = 0;
+    int64_t best_T = 0;        // steps recorded in rb.best by the last run (0: none)
+    float* lip = nullptr;      // ||X||_2^2 / 4 for the MAP solver
+    bool lip_ok = false;
 
     cudaStream_t stream() const { return cfg.stream ? static_cast<cudaStream_t>(cfg.stream) : own_stream; }
 };
@@ -188,6 +192,7 @@ int check_device(spa_ctx* c)
         return fail(c, SPA_EUNSUPPORTED, "the library is built for sm_103a (compute capability 10.x)");
     CK(tc_init_attributes(), "tensor-core kernel attributes");
     CK(smc_init_attributes(), "summaries kernel attributes");
+    CK(map_init_attributes(), "MAP kernel attributes");
     if (c) {
         c->device = dev;
         c->num_sms = prop.multiProcessorCount;
@@ -229,7 +234,7 @@ void free_workspace(Workspace& w)
 void free_runbufs(RunBufs& r)
 {
     dfree(r.sched); dfree(r.mean); dfree(r.quant); dfree(r.conc); dfree(r.ess); dfree(r.logz); dfree(r.accrate);
-    dfree(r.acc); dfree(r.res); dfree(r.seed);
+    dfree(r.acc); dfree(r.res); dfree(r.seed); dfree(r.best);
     r.T = 0;
 }
 
@@ -426,6 +431,7 @@ int ensure_runbufs(spa_ctx* c, int64_t T)
     RA(acc, T + 1);
     RA(res, T);
     RA(seed, 1);
+    RA(best, T * p);
 #undef RA
     if (e != cudaSuccess) {
         free_runbufs(r);
@@ -548,7 +554,8 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     if (c->cfg.move_kind == SPA_MOVE_SITE) {  // all M cycles in one launch
-        const SiteArgs sa{w.beta, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
+        const float inv_sp = c->cfg.precision == SPA_PREC_SPLIT_BF16 ? (float)LOG2E : 1.0f;
+        const SiteArgs sa{w.beta, w.llq, w.lpq, inv_sp, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
         q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.sched, t, m0, M, c->rb.seed, q.st));
         return;
     }
@@ -658,6 +665,8 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
         enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
         q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
         ++q.launches;  // the key transpose and the summaries
+        if (cfg.map_path)
+            q.ck(launch_best_particle(mh_state(c, nullptr), w.beta, w.N, p, c->pr, r.sched, (int)t, r.best, q.st));
         if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
     }
     q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
@@ -703,6 +712,7 @@ int upload_data(spa_ctx* c, const int8_t* G, const uint8_t* y)
     CK(launch_store_pack_t(c->G, c->y, n, p, c->n_r, c->GT, c->yv, st), "store pack transposed");
     CK(launch_store_ybits(c->y, n, c->ywords, c->ybits, st), "store y bits");
     CK(launch_store_xt2(c->Xf, n, p, c->XT2, st), "store X transposed");
+    c->lip_ok = false;  // new data: the MAP solver's curvature bound is recomputed on demand
     return read_error_word(c);
 }
 
@@ -714,7 +724,7 @@ void destroy(spa_ctx* c)
     free_runbufs(c->rb);
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
-    dfree(c->ybits); dfree(c->XT2);
+    dfree(c->ybits); dfree(c->XT2); dfree(c->lip);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -848,6 +858,7 @@ void spa_config_default(spa_config* k)
     k->mala_h = 1.65;
     k->sd_floor = 1e-3;
     k->site_sd = 0.5;
+    k->map_path = 0;
     k->stream = nullptr;
 }
 
@@ -887,6 +898,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     CA(GT, p * c->n_r);
     CA(yv, n);
     CA(XT2, n * p);
+    CA(lip, 1);
     c->ywords = round_up(n, 256) / 32;
     CA(ybits, c->ywords);
     CA(d_err, 1);
@@ -1003,6 +1015,7 @@ static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int
     }
     CK(cudaGraphLaunch(c->gexec, st), "graph launch");
     c->last_launches = c->graph_launches;
+    c->best_T = c->cfg.map_path ? T : 0;
     return SPA_OK;
 }
 
@@ -1117,6 +1130,7 @@ int spa_batch_run(spa_batch* b, const uint64_t* seeds, spa_result* outs)
     for (int32_t r = 0; r < R; ++r) {
         spa_ctx* c = b->ctxs[r];
         c->last_launches = b->per_ctx_launches[r];
+        c->best_T = c->cfg.map_path ? b->T[r] : 0;
         const int rc = read_error_word(c);
         if (rc != SPA_OK) {
             set_thread_error_str("region " + std::to_string(r) + ": " + c->err);
@@ -1185,6 +1199,73 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
         }
     }
     return SPA_OK;
+}
+
+static MapData map_data(spa_ctx* c)
+{
+    return MapData{c->Xf, c->XT2, c->y, c->n, (int)c->p, c->lip, c->pr};
+}
+
+static int ensure_lipschitz(spa_ctx* c, cudaStream_t st)
+{
+    if (c->lip_ok) return SPA_OK;
+    CK(launch_map_lipschitz(map_data(c), c->lip, st), "MAP curvature bound");
+    CK(cudaStreamSynchronize(st), "sync");
+    c->lip_ok = true;
+    return SPA_OK;
+}
+
+int spa_map(spa_ctx* c, const float* beta0, int32_t S, double cs, int32_t max_em, double tol, float* beta_out,
+            double* logpost)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!beta0 || !beta_out || S < 1 || !(cs > 0.0) || !std::isfinite(cs) || max_em < 1 || !(tol > 0.0))
+        return fail(c, SPA_EINVAL, "bad arguments");
+    if (!map_fits(c->n, (int)c->p)) return fail(c, SPA_EINVAL, "n + 5p too large for the MAP solver's shared memory");
+    cudaStream_t st = c->stream();
+    int rc = ensure_lipschitz(c, st);
+    if (rc != SPA_OK) return rc;
+    const int64_t p = c->p;
+    float *d0 = nullptr, *d1 = nullptr;
+    double* dl = nullptr;
+    cudaError_t e = dalloc(&d0, (size_t)(S * p));
+    if (e == cudaSuccess) e = dalloc(&d1, (size_t)(S * p));
+    if (e == cudaSuccess) e = dalloc(&dl, (size_t)S);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d0, beta0, sizeof(float) * (size_t)(S * p), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_map(map_data(c), d0, S, cs, max_em, (float)tol, d1, dl, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(beta_out, d1, sizeof(float) * (size_t)(S * p), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && logpost) e = cudaMemcpyAsync(logpost, dl, sizeof(double) * (size_t)S, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d0);
+    dfree(d1);
+    dfree(dl);
+    if (e != cudaSuccess) return cuda_fail(c, e, "MAP");
+    return read_error_word(c);
+}
+
+int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!map_out || T < 1 || max_em < 1 || !(tol > 0.0)) return fail(c, SPA_EINVAL, "bad arguments");
+    if (c->best_T != T || c->rb.T != T || !c->rb.best)
+        return fail(c, SPA_EINVAL, "no recorded run of T steps with config.map_path set");
+    if (!map_fits(c->n, (int)c->p)) return fail(c, SPA_EINVAL, "n + 5p too large for the MAP solver's shared memory");
+    cudaStream_t st = c->stream();
+    int rc = ensure_lipschitz(c, st);
+    if (rc != SPA_OK) return rc;
+    const int64_t p = c->p;
+    float* dm = nullptr;
+    double* dl = nullptr;
+    cudaError_t e = dalloc(&dm, (size_t)(T * p));
+    if (e == cudaSuccess) e = dalloc(&dl, (size_t)T);
+    if (e == cudaSuccess) e = launch_map_path(map_data(c), c->rb.best, c->rb.sched, (int)T, max_em, (float)tol, dm, dl, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(map_out, dm, sizeof(float) * (size_t)(T * p), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && logpost) e = cudaMemcpyAsync(logpost, dl, sizeof(double) * (size_t)T, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(dm);
+    dfree(dl);
+    if (e != cudaSuccess) return cuda_fail(c, e, "MAP path");
+    return read_error_word(c);
 }
 
 int spa_loglik(spa_ctx* c, const float* B, int64_t N, double* ll_out)

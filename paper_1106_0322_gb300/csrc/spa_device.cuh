@@ -129,6 +129,14 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start before its predecessor finishes; this waits until the predecessor grid has
+// completed and its memory is visible (a no-op for kernels launched without the attribute).
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel's blocks be scheduled once every block of this grid has passed here
+// (they still wait for this grid's completion before reading its results).
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
     uint64_t t;

@@ -105,6 +105,9 @@ struct MoveArgs {
 // The paper's single-coordinate cycle (move kind 2): M cycles over j = 0..p-1 per launch.
 struct SiteArgs {
     float* beta;                      // particle states [N][p], updated in place
+    float2* llq;                      // at the end of the step: log-likelihood (partial units)
+    float2* lpq;                      //   and log-prior term sum pair, as the MH state keeps them
+    float inv_sp_scale;               // partial units per nat
     const float* XT2;                 // [p][n] standardised genotypes times log2(e)
     const float* vy;                  // v = X^T y (nats)
     float sd;                         // proposal standard deviation
@@ -205,6 +208,31 @@ cudaError_t launch_prior_sample(uint64_t seed, PriorArgs pr, double c, int64_t N
                                 cudaStream_t st);
 cudaError_t launch_prior_logpdf(PriorArgs pr, double c, const float* beta, int64_t k, double* out,
                                 cudaStream_t st);
+
+// ------------------------------------------------------------ MAP by EM
+// Section 2.1 (EM with weighted-L1 logistic steps), Section 4.1 (the MAP path).
+struct MapData {
+    const float* Xf;    // [n][p] standardised genotypes
+    const float* XT2;   // [p][n] the same times log2(e)
+    const uint8_t* y;   // [n]
+    int64_t n;
+    int p;
+    const float* lip;   // ||X||_2^2 / 4 (launch_map_lipschitz)
+    PriorArgs pr;
+};
+constexpr size_t MAP_SMEM_MAX = 200 * 1024;
+bool map_fits(int64_t n, int p);  // the solve's shared-memory plan fits one block
+cudaError_t map_init_attributes();
+cudaError_t launch_map_lipschitz(const MapData& d, float* lip, cudaStream_t st);
+// S independent EM solves from beta0 [S][p] at scale c.
+cudaError_t launch_map(const MapData& d, const float* beta0, int S, double c, int max_em, float tol, float* beta_out,
+                       double* lp_out, cudaStream_t st);
+// The MAP path over T steps from the recorded best particles best [T][p].
+cudaError_t launch_map_path(const MapData& d, const float* best, const double* sched, int T, int max_em, float tol,
+                            float* map_out, double* lp_out, cudaStream_t st);
+// Step t's particle of highest posterior density into best[t].
+cudaError_t launch_best_particle(const MhState& s, const float* beta, int64_t N, int p, PriorArgs pr,
+                                 const double* sched, int t, float* best, cudaStream_t st);
 
 // ------------------------------------------------------------ likelihood
 // tcgen05 split-BF16 GEMM with the fused softplus reduction: partial[c * N_pad + i] receives

@@ -61,7 +61,7 @@ def test_struct_layouts_match_header():
     import paper_1106_0322_gb300 as spa
 
     # int32 x5, double[8], int32, double[8], 4 doubles, pointer (LP64, natural alignment)
-    assert C.sizeof(spa.Config) == 20 + 4 + 64 + 4 + 4 + 64 + 40 + 8
+    assert C.sizeof(spa.Config) == 20 + 4 + 64 + 4 + 4 + 64 + 40 + 4 + 4 + 8
     assert C.sizeof(spa.Result) == 7 * 8
     assert C.sizeof(spa.BatchArgs) == 5 * 8
 
