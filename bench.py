@@ -39,6 +39,28 @@ def _rank_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def replica_seed_base(rank: int) -> int:
+    """Seeds of rank r's sweeps start at 1000 (r + 1): the replicas are independent runs."""
+    return 1000 * (rank + 1)
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (all-reduce MAX; gloo on CPU tensors, NCCL on device ones)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(gmac_per_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank did `steps` sweeps in at most total_ms (weak scaling)."""
+    return world * gmac_per_step * steps / (total_ms / 1e3)
+
+
 def workload_desc(w):
     return (f"{w['name']}: n={w['n']} p={w['p']} N={w['N']} T={w['T']} M={w['M']} "
             f"{w['move'].upper()} nu={w['nu']:g}")
@@ -475,7 +497,7 @@ def main():
         "resampled": torch.empty(T, dtype=torch.uint8, device=dev),
     }
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    seed_base = 1000 * (rank + 1)
+    seed_base = replica_seed_base(rank)
 
     def one_sweep(k):
         reg.run_device(sched_d, w["N"], w["M"], seed_base + k, out_d)
@@ -512,13 +534,10 @@ def main():
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
     launches = reg.last_launch_count() * args.steps
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
     gmac = algorithmic_gmac(w)
-    value = world * gmac * args.steps / (total_ms / 1e3)
+    value = whole_job_value(gmac, args.steps, world, total_ms)
     assert np.all(np.isfinite(out_d["mean"].cpu().numpy()))
 
     # ----------------------------------- dominant kernel: the likelihood GEMM + epilogue

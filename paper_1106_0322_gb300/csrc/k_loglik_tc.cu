@@ -139,8 +139,10 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
 
 template <int BN, int STAGES, bool RESID, bool AR>
 __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
-    k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int n_tiles,
-                int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial, int64_t N_pad,
+    k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt, int tw,
+                int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
+                int64_t N_pad,
                 uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
                 int64_t n_r, float* __restrict__ rsum_part)
 {
@@ -181,7 +183,17 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&mapA);
         tma_prefetch_desc(&mapB);
+        if (tw) {
+            tma_prefetch_desc(&mapAt);
+            tma_prefetch_desc(&mapBt);
+        }
     }
+    // The last k-block is `tw` (16 or 32) columns wide when the K extent does not fill it:
+    // its tiles come from the narrow maps (32- or 64-byte swizzle) and carry fewer bytes.
+    const int kb_last = kblocks - 1;
+    const uint32_t a_tail = tw ? (uint32_t)(BM * tw * 2) : (uint32_t)C::A_TILE;
+    const uint32_t b_tail = tw ? (uint32_t)(BN * tw * 2) : (uint32_t)C::B_TILE;
+    const uint32_t tail_row = tw ? (uint32_t)(tw * 2) : 128u;
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
         tmem_relinquish();
@@ -210,11 +222,12 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(afull_bar, (uint32_t)(kblocks * 2 * C::A_TILE));
+                    mbar_arrive_expect_tx(afull_bar, (uint32_t)(kb_last * 2 * C::A_TILE) + 2u * a_tail);
                     for (int kb = 0; kb < kblocks; ++kb) {
                         const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
-                        tma_load_2d(a, &mapA, afull_bar, kb * BK, mt * BM);
-                        tma_load_2d(a + C::A_TILE, &mapA, afull_bar, Kp + kb * BK, mt * BM);
+                        const CUtensorMap* ma = (tw && kb == kb_last) ? &mapAt : &mapA;
+                        tma_load_2d(a, ma, afull_bar, kb * BK, mt * BM);
+                        tma_load_2d(a + C::A_TILE, ma, afull_bar, Kp + kb * BK, mt * BM);
                     }
                     cur_mt = mt;
                 }
@@ -225,13 +238,18 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                         break;
                     }
                     const uint32_t st = stage0 + s * C::STAGE;
-                    mbar_arrive_expect_tx(FULL_BAR(s), (uint32_t)C::STAGE);
+                    const bool tail = tw && kb == kb_last;
+                    const CUtensorMap* ma = tail ? &mapAt : &mapA;
+                    const CUtensorMap* mb = tail ? &mapBt : &mapB;
+                    const uint32_t bytes = AR ? (tail ? b_tail : (uint32_t)C::B_TILE)
+                                              : (tail ? 2u * a_tail + b_tail : (uint32_t)C::STAGE);
+                    mbar_arrive_expect_tx(FULL_BAR(s), bytes);
                     if (AR) {
-                        tma_load_2d(st, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                        tma_load_2d(st, mb, FULL_BAR(s), kb * BK, nt * BN);
                     } else {
-                        tma_load_2d(st, &mapA, FULL_BAR(s), kb * BK, mt * BM);
-                        tma_load_2d(st + C::A_TILE, &mapA, FULL_BAR(s), Kp + kb * BK, mt * BM);
-                        tma_load_2d(st + 2 * C::A_TILE, &mapB, FULL_BAR(s), kb * BK, nt * BN);
+                        tma_load_2d(st, ma, FULL_BAR(s), kb * BK, mt * BM);
+                        tma_load_2d(st + C::A_TILE, ma, FULL_BAR(s), Kp + kb * BK, mt * BM);
+                        tma_load_2d(st + 2 * C::A_TILE, mb, FULL_BAR(s), kb * BK, nt * BN);
                     }
                     ++it;
                 }
@@ -279,9 +297,10 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                     tc_fence_after();
                     const uint32_t st = stage0 + s * C::STAGE;
                     const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
-                    const uint64_t ahi = sdesc_sw128(a);
-                    const uint64_t alo = sdesc_sw128(a + C::A_TILE);
-                    const uint64_t bg = sdesc_sw128(AR ? st : st + 2 * C::A_TILE);
+                    const uint32_t rb = (tw && kb == kb_last) ? tail_row : 128u;
+                    const uint64_t ahi = sdesc_swz(a, rb);
+                    const uint64_t alo = sdesc_swz(a + C::A_TILE, rb);
+                    const uint64_t bg = sdesc_swz(AR ? st : st + 2 * C::A_TILE, rb);
                     const int nks = (ksteps - 4 * kb) < 4 ? (ksteps - 4 * kb) : 4;
                     for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
                         umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
@@ -563,7 +582,7 @@ EncodeTiledFn encode_fn()
 }
 
 bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint32_t box_inner,
-                 uint32_t box_outer)
+                 uint32_t box_outer, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
@@ -572,12 +591,12 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int BN, int STAGES, bool RESID, bool AR>
-cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
+cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
                       cudaStream_t st)
 {
@@ -594,7 +613,9 @@ cudaError_t launch_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const Tc
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, mapA, mapB, plan.n_tiles, plan.m_tiles,
+    const bool tail = plan.tw != 0;
+    return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
+                              plan.tw, plan.n_tiles, plan.m_tiles,
                               plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
                               ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr);
 }
@@ -631,6 +652,8 @@ TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN)
     const int64_t units = (int64_t)pl.m_tiles * pl.n_tiles;
     pl.grid = (int)(units < num_sms ? units : num_sms);
     pl.n_parts = (int)((n + 31) / 32);
+    const int last = pl.ksteps - 4 * (pl.kblocks - 1);  // k-steps of the last k-block
+    pl.tw = (last == 1 || last == 2) ? 16 * last : 0;
     return pl;
 }
 
@@ -644,14 +667,28 @@ bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp
     return make_map_2d(map, Gbf, (uint64_t)Kp, (uint64_t)n, BK, (uint32_t)BN);
 }
 
-cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n, int Kp,
+static CUtensorMapSwizzle tail_swizzle(int tw) { return tw == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B; }
+
+bool tc_make_map_A_tail(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp, int tw)
+{
+    if (!tw) return true;
+    return make_map_2d(map, A, (uint64_t)(2 * Kp), (uint64_t)N_pad, (uint32_t)tw, BM, tail_swizzle(tw));
+}
+
+bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN, int tw)
+{
+    if (!tw) return true;
+    return make_map_2d(map, Gbf, (uint64_t)Kp, (uint64_t)n, (uint32_t)tw, (uint32_t)BN, tail_swizzle(tw));
+}
+
+cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp,
                              const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
                              const ResidArgs* ra)
 {
     // A stays resident when all its k-blocks fit (K <= 256)
     const bool ar = plan.kblocks <= KB_RES;
 #define TC_CASE(BN_, S_, R_, AR_) \
-    return launch_tc<BN_, S_, R_, AR_>(mapA, mapB, plan, n, Kp, ybits, partial, N_pad, err, ra, st)
+    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, st)
     if (ra) {
         if (plan.BN == 256) {
             if (ar) TC_CASE(256, 3, true, true);

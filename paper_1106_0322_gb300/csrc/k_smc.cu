@@ -33,10 +33,10 @@ __device__ __forceinline__ int64_t warp_global_id()
 // One coordinate's term of the log prior (the -log(2c) constant dropped): Gt sums
 // log1p(|b|/(a c)) and multiplies by -(a+1); the double exponential sums |b| and
 // multiplies by -1/c.
-__device__ __forceinline__ float prior_term(float b, float ac, int de)
+__device__ __forceinline__ float prior_term(float b, float inv_ac, int de)
 {
     const float x = fabsf(b);
-    return de ? x : log1pf(x / ac);
+    return de ? x : log1pf(x * inv_ac);
 }
 __device__ __forceinline__ double prior_coef(PriorArgs pr, double c) { return pr.de ? -1.0 / c : -((double)pr.a + 1.0); }
 
@@ -167,7 +167,7 @@ __device__ __forceinline__ void count_block(unsigned long long* acc_count, int* 
 // `live` masks the memory traffic of a lane whose group lies beyond p.
 template <bool VEC>
 __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool live, bool acc, int noise, float4 z,
-                                         float ac, int de, const float* src, float* dst, float* cur,
+                                         float inv_ac, int de, const float* src, float* dst, float* cur,
                                          __nv_bfloat16* Arow, FSum& lt, float& yd, float& off)
 {
     const int j0 = 4 * g;
@@ -183,7 +183,7 @@ __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool l
         const float4 v = ld4(a.vy + j0);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            lt.add(prior_term(comp(b, k), ac, de));
+            lt.add(prior_term(comp(b, k), inv_ac, de));
             yd = fmaf(comp(b, k), comp(v, k), yd);
         }
         if (Arow) off += pack_coord4(Arow, a.Kp, j0, b, ld4(a.l2e_over_s + j0), ld4(a.mean_f + j0));
@@ -196,7 +196,7 @@ __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool l
                 if (acc) cur[j] = b0;
                 const float b = noise ? fmaf(a.sigma[j], comp(z, k), b0) : b0;
                 dst[j] = b;
-                lt.add(prior_term(b, ac, de));
+                lt.add(prior_term(b, inv_ac, de));
                 yd = fmaf(b, a.vy[j], yd);
                 if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
             }
@@ -214,6 +214,7 @@ __device__ __forceinline__ void step_constants(PriorArgs pr, const double* sched
         sh[0] = (float)((double)pr.a * c);
         sh[2] = 1.0f / (float)c;
         sh[1] = pr.de ? -sh[2] : -(pr.a + 1.0f);
+        sh[3] = (float)(1.0 / ((double)pr.a * c));
     }
     __syncthreads();
 }
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
                                                   const uint64_t* __restrict__ seedp, int noise, uint32_t* err)
 {
     __shared__ int blk;
-    __shared__ float shk[3];
+    __shared__ float shk[4];
     if (DECIDE && threadIdx.x == 0) blk = 0;
     step_constants(pr, sched, t, shk);
     grid_dependency_wait();  // the previous kernel (the likelihood GEMM) has finished
@@ -233,7 +234,6 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
     const int lane = threadIdx.x & 31;
     if (i < N) {
         const uint64_t seed = (noise || DECIDE) ? *seedp : 0ull;
-        const float ac = shk[0];
         bool acc = false;
         if (DECIDE) {
             acc = mh_decide(a.mh, i, lane, shk[1], 0.0f, t, m_prev, seed, err);
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
         for (int g = lane; g < groups; g += 32) {
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             if (noise) z = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
-            rw_group<VEC>(a, p, g, true, acc, noise, z, ac, pr.de, src, dst, cur, Arow, lt, yd, off);
+            rw_group<VEC>(a, p, g, true, acc, noise, z, shk[3], pr.de, src, dst, cur, Arow, lt, yd, off);
         }
         lt = warp_sum(lt);
         yd = warp_sum(yd);
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                                                     uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
 {
     __shared__ int blk;
-    __shared__ float shk[3];
+    __shared__ float shk[4];
     if (DECIDE && threadIdx.x == 0) blk = 0;
     step_constants(pr, sched, t, shk);
     const int64_t i = warp_global_id();
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                     dst[j] = b;
                     const float d = (b - b0) - drift;
                     fw.add(d * d / Dj);
-                    lt.add(prior_term(b, ac, pr.de));
+                    lt.add(prior_term(b, shk[3], pr.de));
                     yd = fmaf(b, a.vy[j], yd);
                     if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
                 }
@@ -395,7 +395,7 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
                             uint32_t m0, int M, const uint64_t* __restrict__ seedp)
 {
     extern __shared__ float site_sm[];
-    __shared__ float shk[3];
+    __shared__ float shk[4];
     __shared__ int blk;
     const int wpc = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -406,7 +406,7 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
     const int64_t i = (int64_t)blockIdx.x * wpc + w;
     if (i < N) {
         const uint64_t seed = *seedp;
-        const float ac = shk[0], coef = shk[1];
+        const float coef = shk[1], inv_ac = shk[3];
         float* bg = a.beta + i * p;
         for (int j = lane; j < p; j += 32) brow[j] = bg[j];
         for (int r = lane; r < n; r += 32) eta[r] = 0.0f;
@@ -431,7 +431,7 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
                 const float lq1 = site_trial(eta, xr, n, lane, delta, dm);
                 const float dsp = warp_sum(dm + (lq1 - lq));
                 const float b0 = brow[j], b1 = b0 + delta;
-                const float dlp = coef * (prior_term(b1, ac, pr.de) - prior_term(b0, ac, pr.de));
+                const float dlp = coef * (prior_term(b1, inv_ac, pr.de) - prior_term(b0, inv_ac, pr.de));
                 const float dl = fmaf(delta, a.vy[j], -0.69314718f * dsp);
                 int acc = logf(u01_open_f(u.z)) < dl + dlp;
                 acc = __shfl_sync(0xffffffffu, acc, 0);
@@ -455,7 +455,7 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
             for (int r = lane; r < n; r += 32) mx += fmaxf(eta[r], 0.0f);
             for (int j = lane; j < p; j += 32) {
                 yd = fmaf(brow[j], a.vy[j], yd);
-                lt.add(prior_term(brow[j], ac, pr.de));
+                lt.add(prior_term(brow[j], inv_ac, pr.de));
             }
             const float sp2 = warp_sum(mx + lq);
             yd = warp_sum(yd);
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
                                                       const uint64_t* __restrict__ seedp, uint32_t* err)
 {
     __shared__ int blk;
-    __shared__ float shk[3];
+    __shared__ float shk[4];
     if (threadIdx.x == 0) blk = 0;
     step_constants(pr, sched, t, shk);
     grid_dependency_wait();
@@ -556,8 +556,9 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
                                                    float2* __restrict__ lpq, int64_t N, int p, PriorArgs pr,
                                                    const double* __restrict__ sched, int t, uint32_t* __restrict__ err)
 {
+    grid_dependency_wait();
     __shared__ float4 sums[RW_PER_BLOCK];
-    __shared__ float shk[4];
+    __shared__ float shk[5];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RW_PER_BLOCK;
     if (threadIdx.x == 0) {  // the scale constants once per block (FP64)
@@ -566,9 +567,10 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
         shk[1] = (float)c;
         shk[2] = (float)((double)pr.a * cp);
         shk[3] = (float)((double)pr.a * c);
+        shk[4] = (float)(1.0 / ((double)pr.a * c));
     }
     __syncthreads();
-    const float k1 = shk[0], kc = shk[1], kac = shk[2], ac = shk[3];
+    const float k1 = shk[0], kc = shk[1], kac = shk[2], inv_ac = shk[4];
     {
         const int q = w;
         const int64_t i = base + q;
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
             for (int j = lane; j < p; j += 32) {
                 const float x = fabsf(beta[i * p + j]);
                 sdiff.add(pr.de ? x : log1pf(x * k1 / (kc * (kac + x))));
-                snew.add(prior_term(x, ac, pr.de));
+                snew.add(prior_term(x, inv_ac, pr.de));
             }
         }
         sdiff = warp_sum(sdiff);
@@ -635,6 +637,7 @@ __global__ void __launch_bounds__(LSE_THREADS) k_lse_partial(const double* __res
                                                       double* __restrict__ logz_out, uint8_t* __restrict__ res_out,
                                                       int* __restrict__ flag, uint32_t* __restrict__ err)
 {
+    grid_dependency_wait();
     __shared__ double sh[BLOCK / 32];
     __shared__ bool last;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -697,6 +700,7 @@ __device__ __forceinline__ uint32_t weight_fix(double W) { return (uint32_t)__do
 
 __global__ void k_normalise(WeightArrays w, int64_t N, const double* __restrict__ lse_ptr)
 {
+    grid_dependency_wait();
     const double lse = *lse_ptr;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const double l = w.logw[i] - lse;
@@ -742,6 +746,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __re
                                                                int t, const uint64_t* __restrict__ seedp,
                                                                double u_override)
 {
+    grid_dependency_wait();
     if (flag && *flag == 0) return;
     __shared__ double tot[RS_TOT];
     const int tid = threadIdx.x;
@@ -796,6 +801,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __re
 __global__ void k_resample_search(const double* __restrict__ cum, int64_t N, int32_t* __restrict__ idx,
                                   const int* __restrict__ flag)
 {
+    grid_dependency_wait();
     if (flag && *flag == 0) return;
     const int64_t nblk = (N + RS_BLOCK - 1) / RS_BLOCK;
     const double u = cum[N + nblk];
@@ -823,6 +829,7 @@ __global__ void __launch_bounds__(BLOCK) k_gather(const int32_t* __restrict__ id
                                                  float2* __restrict__ lpq_tmp, const float* __restrict__ g,
                                                  float* __restrict__ g_tmp, int64_t N, int p, const int* __restrict__ flag)
 {
+    grid_dependency_wait();
     if (*flag == 0) return;
     const int64_t k = warp_global_id();
     const int lane = threadIdx.x & 31;
@@ -855,6 +862,7 @@ __global__ void __launch_bounds__(BLOCK) k_copyback(float* __restrict__ beta, co
                                                    int64_t N, int p, const int* __restrict__ flag, double lw, double wi,
                                                    uint32_t wf)
 {
+    grid_dependency_wait();
     if (*flag == 0) return;
     const int64_t k = warp_global_id();
     const int lane = threadIdx.x & 31;
@@ -885,6 +893,7 @@ constexpr int CS_ROWS = 8;
 __global__ void k_colstats_partial(const float* __restrict__ beta, const float* __restrict__ Wf, int64_t N, int p,
                                    float4* __restrict__ part)
 {
+    grid_dependency_wait();
     __shared__ float4 sh[CS_ROWS][32];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int j = blockIdx.x * 32 + tx;
@@ -932,6 +941,7 @@ __global__ void k_colstats_finish(const float4* __restrict__ part, int p, int sp
                                   int kind, double lam_const, const double* __restrict__ lam_dev, double sd_floor,
                                   const double* __restrict__ sched, int t, float* __restrict__ h_out, double p_pow)
 {
+    grid_dependency_wait();
     const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (j >= p) return;
@@ -1039,6 +1049,7 @@ __device__ int warp_find_bin(const uint32_t* hist, int nbins, unsigned long long
 // coalesced loads. 32 x 32 tiles through shared memory.
 __global__ void k_keys_transpose(const float* __restrict__ beta, int64_t N, int p, uint32_t* __restrict__ keysT)
 {
+    grid_dependency_wait();
     __shared__ uint32_t tile[32][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int j0 = blockIdx.y * 32;
@@ -1070,6 +1081,7 @@ __global__ void __launch_bounds__(SUM_THREADS, 2) k_summaries(const uint32_t* __
                                                                double* __restrict__ quant, double* __restrict__ conc,
                                                                int staged)
 {
+    grid_dependency_wait();
     extern __shared__ uint32_t sm[];
     __shared__ float red_s[SUM_THREADS / 32][9], red_c[SUM_THREADS / 32][9];
     __shared__ unsigned long long shu[SUM_THREADS / 32];
@@ -1314,8 +1326,8 @@ __global__ void k_prior_logpdf(PriorArgs pr, double c, const float* beta, int64_
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= k) return;
-    const float ac = (float)((double)pr.a * c);
-    out[i] = -log(2.0 * c) + prior_coef(pr, c) * (double)prior_term(beta[i], ac, pr.de);
+    const float inv_ac = (float)(1.0 / ((double)pr.a * c));
+    out[i] = -log(2.0 * c) + prior_coef(pr, c) * (double)prior_term(beta[i], inv_ac, pr.de);
 }
 
 }  // namespace
@@ -1339,6 +1351,25 @@ static void pdl_attr(cudaLaunchConfig_t& cfg, cudaLaunchAttribute (&attr)[1])
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+}
+
+// A launch with programmatic stream serialization: the kernels of the sweep's chain begin
+// with grid_dependency_wait, so each may be scheduled while its predecessor drains.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 static unsigned warps_grid(int64_t N) { return (unsigned)((N + WARPS - 1) / WARPS); }
@@ -1378,9 +1409,9 @@ cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, Pri
         return cudaLaunchKernelEx(&cfg, k_move_rw<true, false>, a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
     } else {
         if (vec)
-            k_move_rw<false, true><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+            { const cudaError_t e_ = launch_pdl(k_move_rw<false, true>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, sched, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
         else
-            k_move_rw<false, false><<<grid, BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+            { const cudaError_t e_ = launch_pdl(k_move_rw<false, false>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, sched, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
     }
     return cudaGetLastError();
 }
@@ -1439,8 +1470,8 @@ cudaError_t launch_finish_loglik(const MhState& s, int64_t N, double* logw, doub
 cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_t N, int p, PriorArgs pr,
                             const double* sched, int t, uint32_t* err, cudaStream_t st)
 {
-    k_reweight<<<(unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK), RW_THREADS, 0, st>>>(beta, logw, lpq, N, p, pr, sched,
-                                                                                         t, err);
+    { const cudaError_t e_ = launch_pdl(k_reweight, dim3((unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK)), dim3(RW_THREADS), (size_t)(0), st, beta, logw, lpq, N, p, pr, sched,
+                                                                                         t, err); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1450,11 +1481,11 @@ cudaError_t launch_lse_ess(const WeightArrays& w, int64_t N, double* scratch, un
 {
     int64_t blocks = (N + LSE_THREADS - 1) / LSE_THREADS;
     if (blocks > LSE_BLOCKS) blocks = LSE_BLOCKS;
-    k_lse_partial<<<(unsigned)blocks, LSE_THREADS, 0, st>>>(w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
-                                                      resampled_out, flag, err);
+    { const cudaError_t e_ = launch_pdl(k_lse_partial, dim3((unsigned)blocks), dim3(LSE_THREADS), (size_t)(0), st, w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
+                                                      resampled_out, flag, err); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_normalise<<<elem_grid(N), 256, 0, st>>>(w, N, scratch + 3 * blocks);
+    { const cudaError_t e_ = launch_pdl(k_normalise, dim3(elem_grid(N)), dim3(256), (size_t)(0), st, w, N, scratch + 3 * blocks); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1473,10 +1504,10 @@ cudaError_t launch_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* resa
 cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32_t* idx, const int* flag, int t,
                                   const uint64_t* seed, double u_override, cudaStream_t st)
 {
-    k_resample_scan<<<1, RS_THREADS, 0, st>>>(W, N, cum, flag, t, seed, u_override);
+    { const cudaError_t e_ = launch_pdl(k_resample_scan, dim3(1), dim3(RS_THREADS), (size_t)(0), st, W, N, cum, flag, t, seed, u_override); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_resample_search<<<elem_grid(N), 256, 0, st>>>(cum, N, idx, flag);
+    { const cudaError_t e_ = launch_pdl(k_resample_search, dim3(elem_grid(N)), dim3(256), (size_t)(0), st, cum, N, idx, flag); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1485,11 +1516,11 @@ cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp
                           const int* flag, cudaStream_t st)
 {
     if ((p & 3) == 0)
-        k_gather<true><<<warps_grid(N), BLOCK, 0, st>>>(idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
-                                                        flag);
+        { const cudaError_t e_ = launch_pdl(k_gather<true>, dim3(warps_grid(N)), dim3(BLOCK), (size_t)(0), st, idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
+                                                        flag); if (e_ != cudaSuccess) return e_; }
     else
-        k_gather<false><<<warps_grid(N), BLOCK, 0, st>>>(idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
-                                                         flag);
+        { const cudaError_t e_ = launch_pdl(k_gather<false>, dim3(warps_grid(N)), dim3(BLOCK), (size_t)(0), st, idx, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, N, p,
+                                                         flag); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1502,11 +1533,11 @@ cudaError_t launch_copyback(float* beta, const float* beta_tmp, float2* llq, flo
     const uint32_t wf = (uint32_t)std::llrint(wi * 2147483648.0);
     const double lw = -std::log((double)N);
     if ((p & 3) == 0)
-        k_copyback<true><<<warps_grid(N), BLOCK, 0, st>>>(beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
-                                                          flag, lw, wi, wf);
+        { const cudaError_t e_ = launch_pdl(k_copyback<true>, dim3(warps_grid(N)), dim3(BLOCK), (size_t)(0), st, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
+                                                          flag, lw, wi, wf); if (e_ != cudaSuccess) return e_; }
     else
-        k_copyback<false><<<warps_grid(N), BLOCK, 0, st>>>(beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
-                                                           flag, lw, wi, wf);
+        { const cudaError_t e_ = launch_pdl(k_copyback<false>, dim3(warps_grid(N)), dim3(BLOCK), (size_t)(0), st, beta, beta_tmp, llq, lpq, llq_tmp, lpq_tmp, g, g_tmp, w, N, p,
+                                                           flag, lw, wi, wf); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1516,12 +1547,12 @@ cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p
 {
     dim3 block(32, CS_ROWS);
     dim3 grid((unsigned)((p + 31) / 32), COLSTAT_SPLITS);
-    k_colstats_partial<<<grid, block, 0, st>>>(beta, Wf, N, p, part);
+    { const cudaError_t e_ = launch_pdl(k_colstats_partial, dim3(grid), dim3(block), (size_t)(0), st, beta, Wf, N, p, part); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_colstats_finish<<<(unsigned)((p + 7) / 8), 256, 0, st>>>(part, p, COLSTAT_SPLITS, scale_out, kind, lam_const,
+    { const cudaError_t e_ = launch_pdl(k_colstats_finish, dim3((unsigned)((p + 7) / 8)), dim3(256), (size_t)(0), st, part, p, COLSTAT_SPLITS, scale_out, kind, lam_const,
                                                                lam_dev, sd_floor, sched, t, h_out,
-                                                               std::pow((double)p, -1.0 / 6.0));
+                                                               std::pow((double)p, -1.0 / 6.0)); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1529,8 +1560,8 @@ cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t*
                              const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
                              cudaStream_t st)
 {
-    k_keys_transpose<<<dim3((unsigned)((N + 31) / 32), (unsigned)((p + 31) / 32)), dim3(32, 8), 0, st>>>(beta, N, p,
-                                                                                                      keysT);
+    { const cudaError_t e_ = launch_pdl(k_keys_transpose, dim3(dim3((unsigned)((N + 31) / 32), (unsigned)((p + 31) / 32))), dim3(dim3(32, 8)), (size_t)(0), st, beta, N, p,
+                                                                                                      keysT); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     SummaryArgs a = s;
@@ -1547,7 +1578,7 @@ cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t*
     const size_t staged_bytes = (size_t)N * 2 * sizeof(uint32_t) + hist_bytes;
     const int staged = staged_bytes <= SUM_STAGED_MAX ? 1 : 0;
     const size_t bytes = staged ? staged_bytes : hist_bytes;
-    k_summaries<<<(unsigned)p, SUM_THREADS, bytes, st>>>(keysT, Wf, wfix, N, p, a, t, mean, quant, conc, staged);
+    { const cudaError_t e_ = launch_pdl(k_summaries, dim3((unsigned)p), dim3(SUM_THREADS), (size_t)(bytes), st, keysT, Wf, wfix, N, p, a, t, mean, quant, conc, staged); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 

@@ -55,7 +55,7 @@ struct Workspace {
     int64_t N = 0, N_pad = 0;
     float *beta = nullptr, *beta_p = nullptr, *scale = nullptr;
     __nv_bfloat16* A = nullptr;
-    CUtensorMap mapA;
+    CUtensorMap mapA, mapAt;  // the particle operand (64-column boxes; narrow last k-block)
     int BN = 0;               // n-tile width of the likelihood kernel (tuned per shape)
     float2* lpt_p = nullptr;  // compensated log-prior term sums of the proposals
     float2* ydq = nullptr;    // the proposals' linear log-likelihood term beta' . v
@@ -134,7 +134,7 @@ struct spa_ctx {
     float *l2e_s = nullptr, *mean_f = nullptr, *Xf = nullptr;
     float* colf = nullptr;  // [3p]: 1/s_j, v_j, v_j log2(e) (FP32)
     __nv_bfloat16* Gbf = nullptr;
-    CUtensorMap mapB;
+    CUtensorMap mapB, mapBt;  // the genotype operand for n-tiles of mapB_BN (64 columns; narrow last k-block)
     int mapB_BN = 0;
     __nv_bfloat16* GT = nullptr;  // [p][n_r] for the adjoint
     float* yv = nullptr;
@@ -251,7 +251,9 @@ void drop_graph(spa_ctx* c, bool bump = true)
 int ensure_mapB(spa_ctx* c, int BN)
 {
     if (c->mapB_BN == BN) return SPA_OK;
-    if (!tc_make_map_B(&c->mapB, c->Gbf, c->n, c->Kp, BN))
+    const int tw = tc_plan(c->n, (int)c->p, 128, c->num_sms, BN).tw;
+    if (!tc_make_map_B(&c->mapB, c->Gbf, c->n, c->Kp, BN) ||
+        !tc_make_map_B_tail(&c->mapBt, c->Gbf, c->n, c->Kp, BN, tw))
         return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
     c->mapB_BN = BN;
     return SPA_OK;
@@ -292,15 +294,18 @@ int tune_bn(spa_ctx* c)
     int best = 256;
     float best_ms = -1.0f;
     for (int BN : {128, 256}) {
-        CUtensorMap mB;
-        if (!tc_make_map_B(&mB, c->Gbf, c->n, c->Kp, BN)) continue;
         const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, BN);
+        TcMaps m;
+        m.A = w.mapA;
+        m.At = w.mapAt;
+        if (!tc_make_map_B(&m.B, c->Gbf, c->n, c->Kp, BN) || !tc_make_map_B_tail(&m.Bt, c->Gbf, c->n, c->Kp, BN, plan.tw))
+            continue;
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < 3 && e == cudaSuccess; ++k)
-            e = launch_loglik_tc(w.mapA, mB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
+            e = launch_loglik_tc(m, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
         for (int k = 0; k < 10 && e == cudaSuccess; ++k)
-            e = launch_loglik_tc(w.mapA, mB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
+            e = launch_loglik_tc(m, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -359,7 +364,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     CK(cudaMemsetAsync(w.partial, 0, sizeof(float) * (size_t)(parts * N_pad), c->stream()), "memset partial");
     CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->stream()), "memset flag");
     CK(cudaMemsetAsync(w.lse_counter, 0, sizeof(unsigned int), c->stream()), "memset counter");
-    if (!tc_make_map_A(&w.mapA, w.A, N_pad, c->Kp)) {
+    if (!tc_make_map_A(&w.mapA, w.A, N_pad, c->Kp) || !tc_make_map_A_tail(&w.mapAt, w.A, N_pad, c->Kp, plan.tw)) {
         free_workspace(w);
         return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the particle operand");
     }
@@ -461,6 +466,16 @@ struct Enq {
 // partials of those particles in w.partial.
 TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, c->num_sms, c->ws.BN); }
 
+TcMaps maps_of(const spa_ctx* c)
+{
+    TcMaps m;
+    m.A = c->ws.mapA;
+    m.At = c->ws.mapAt;
+    m.B = c->mapB;
+    m.Bt = c->mapBt;
+    return m;
+}
+
 void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
 {
     spa_ctx* c = q.c;
@@ -468,7 +483,7 @@ void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     const TcPlan plan = plan_of(c);
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     ResidArgs ra{w.R, a.n_r, w.rsum};
-    q.ck(launch_loglik_tc(w.mapA, c->mapB, plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra));
+    q.ck(launch_loglik_tc(maps_of(c), plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra));
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
                             c->pr, cs, out, q.st));
@@ -480,7 +495,7 @@ void enq_loglik(Enq& q)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-        q.ck(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
+        q.ck(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
     } else {
         q.ck(launch_loglik_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
     }
@@ -1173,7 +1188,7 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
     const MoveArgs a = move_args(c, nullptr);
     CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_c, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
     if (tc) {
-        CK(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+        CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
            "loglik tc");
     } else {
         CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
@@ -1192,7 +1207,7 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
     Workspace& w = c->ws;
     for (int32_t k = 0; k < reps; ++k) {
         if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-            CK(launch_loglik_tc(w.mapA, c->mapB, plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+            CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
                "loglik tc");
         } else {
             CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");

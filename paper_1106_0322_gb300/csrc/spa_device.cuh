@@ -244,6 +244,19 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr)
     d |= (uint64_t)2u << 61;
     return d;
 }
+// The same for a K-major tile with rows of `row_bytes` = 64 (64-byte swizzle, layout 4) or
+// 32 (32-byte swizzle, layout 6): 8-row groups are 8 * row_bytes apart.
+__device__ __forceinline__ uint64_t sdesc_swz(uint32_t smem_addr, uint32_t row_bytes)
+{
+    if (row_bytes == 128u) return sdesc_sw128(smem_addr);
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)((8u * row_bytes) >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)(row_bytes == 64u ? 4u : 6u) << 61;
+    return d;
+}
 
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32 accumulate:
 //   [4,6) D format = 1 (F32), [7,10) A = 1 (BF16), [10,13) B = 1 (BF16),

@@ -169,7 +169,7 @@ cudaError_t launch_copyback(float* beta, const float* beta_tmp, float2* llq, flo
 
 // Weighted column moments -> per-coordinate proposal scales. kind 0 (RW):
 // sigma_j = lam/sqrt(p) max(sd_j, floor c); kind 1 (MALA): D_j = max(var_j, (floor c)^2).
-constexpr int COLSTAT_SPLITS = 32;
+constexpr int COLSTAT_SPLITS = 128;
 // With lam_dev (MALA) it also writes h = lambda p^{-1/6} to h_out.
 cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p, float4* part, float* scale_out,
                             int kind, double lam_const, const double* lam_dev, double sd_floor,
@@ -246,6 +246,12 @@ struct TcPlan {
     int ksteps;      // active 16-wide k-steps of each half: ceil((p+1)/16)
     int grid;        // persistent CTAs
     int n_parts;     // partial sums per particle = ceil(n / 32), whatever BN
+    int tw;          // width of a narrow last k-block (16 or 32 columns), or 0
+};
+// The likelihood kernel's tensor maps: A and G with 64-column boxes (128-byte swizzle) and,
+// when the plan has a narrow last k-block, the same with tw-column boxes.
+struct TcMaps {
+    CUtensorMap A, B, At, Bt;
 };
 // BN = 128 or 256 picks the n-tile width (the tuner's choice); 0 picks by the size of n.
 TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN = 0);
@@ -253,6 +259,8 @@ TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN = 0);
 cudaError_t tc_init_attributes();
 bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp);
 bool tc_make_map_B(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN);
+bool tc_make_map_A_tail(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp, int tw);
+bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, int Kp, int BN, int tw);
 // Residual mode of the likelihood kernel (the adjoint's first half): also writes
 // r = y - logit^{-1}(eta) as BF16 hi | lo rows of R [N_pad][2 n_r] and its row sums.
 struct ResidArgs {
@@ -261,8 +269,8 @@ struct ResidArgs {
     float* rsum_part;        // same layout as the softplus partials
 };
 // ybits: y as a bitmask, one word per 32 individuals (ceil(n_tiles * BN / 32) words, zero beyond n).
-cudaError_t launch_loglik_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, const TcPlan& plan, int64_t n,
-                             int Kp, const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
+cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp, const uint32_t* ybits,
+                             float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
                              const ResidArgs* resid = nullptr);
 
 // The adjoint's second half: C = R G (tcgen05, split-BF16 R, exact G^T [p][n_r]) into
