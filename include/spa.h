@@ -232,7 +232,14 @@ int spa_marginal_device(const double* log_z_inc, const double* mean, const doubl
  * config.map_path set, at each step t the EM starts from the step's particle of highest
  * posterior density and (t > 0) from the previous step's MAP, and the mode with the higher
  * log posterior is kept: map_out [T][p] (host, FP32), logpost [T] (host, may be NULL).
- * One thread block walks the steps in order. Blocks until done.
+ * The rule is the recurrence S_0 = A_0, S_t = better(A_t, EM(c_t, S_{t-1})) with A_t the
+ * mode from step t's best particle; it is solved by parallel rounds over t (all A_t, then
+ * EM(c_t, S_{t-1}) again wherever S_{t-1} changed, until a round changes nothing), which
+ * gives bit for bit what walking the steps in order gives. Blocks until done.
+ *
+ * spa_map_path_rounds: the number of rounds after the first that the last spa_map_path on
+ * ctx took (1 when no step's chained start beat its best-particle start in a way that moved
+ * a later step; at most T); -1 for a NULL ctx.
  *
  * Errors: SPA_EINVAL (NULL arguments, S or T < 1, c <= 0, max_em < 1, tol <= 0, no recorded
  * run of T steps with map_path, or n + 5p too large for one block's shared memory),
@@ -240,6 +247,7 @@ int spa_marginal_device(const double* log_z_inc, const double* mean, const doubl
 int spa_map(spa_ctx* ctx, const float* beta0, int32_t S, double c, int32_t max_em, double tol, float* beta_out,
             double* logpost);
 int spa_map_path(spa_ctx* ctx, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost);
+int spa_map_path_rounds(const spa_ctx* ctx);
 
 /* ------------------------------------------------------- per-step entry points */
 

@@ -88,6 +88,7 @@ _SIGS = {
     "spa_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                           C.c_void_p]),
     "spa_map_path": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
+    "spa_map_path_rounds": (C.c_int, [C.c_void_p]),
     "spa_loglik_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "spa_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_loglik_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -275,6 +276,10 @@ class Region:
         lp = np.zeros(T)
         _check(load().spa_map_path(self._h, int(T), int(max_em), float(tol), _ptr(out), _ptr(lp)), self._h)
         return out, lp
+
+    def map_path_rounds(self) -> int:
+        """Rounds after the first that the last map_path took to reach its fixed point."""
+        return int(load().spa_map_path_rounds(self._h))
 
     def loglik_tile_width(self) -> int:
         """n-tile width of the tensor-core likelihood kernel (0 before the first run)."""

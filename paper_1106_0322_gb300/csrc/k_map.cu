@@ -14,7 +14,13 @@
 //
 // Along a sweep (Section 4.1): at step t the EM starts from the particle with the highest
 // posterior density and from the previous step's MAP, and keeps the mode with the higher
-// log posterior l(beta) + log p(beta | a, c_t).
+// log posterior l(beta) + log p(beta | a, c_t). With A_t the mode from the best particle this
+// is the recurrence S_0 = A_0, S_t = better(A_t, EM(c_t, S_{t-1})), solved here in parallel
+// over t by Jacobi rounds: round 0 solves every A_t at once; round k re-solves
+// EM(c_t, S_{t-1}) only for the steps whose predecessor changed in round k - 1. After round
+// k the first k + 1 entries are final, and a round that changes nothing has reached the
+// recurrence's unique solution. One EM solve is a deterministic function of its start and
+// c, so the result is bit-identical to walking the steps in order.
 #include <cfloat>
 #include <cmath>
 
@@ -200,33 +206,65 @@ __global__ void __launch_bounds__(MAP_THREADS) k_map(MapData d, const float* __r
     if (threadIdx.x == 0) lp_out[s] = lp;
 }
 
-// The MAP path (Section 4.1), one block walking the steps: at step t, EM from the step's
-// best particle and (t > 0) from the previous MAP; the higher log posterior is kept.
-__global__ void __launch_bounds__(MAP_THREADS) k_map_path(MapData d, const float* __restrict__ best,
-                                                         const double* __restrict__ sched, int T, int max_em, float tol,
-                                                         float* __restrict__ map_out, double* __restrict__ lp_out)
+// One Jacobi round of the MAP path recurrence, block t = step t. Round 0 solves from the
+// step's best particle into A / lpA and seeds S = A with every step marked changed. Round
+// k >= 1 reads the previous round's S_r / lpS_r / chg_r and writes S_w / lpS_w / chg_w: a
+// step whose predecessor did not change copies its entry; the others solve
+// EM(c_t, S_r[t-1]), keep it if its log posterior is above lpA[t] (ties keep A_t), and
+// count themselves in *n_changed when the kept mode differs from S_r[t].
+__global__ void __launch_bounds__(MAP_THREADS) k_map_round(MapData d, const float* __restrict__ best,
+                                                          const double* __restrict__ sched, int round, int max_em,
+                                                          float tol, float* __restrict__ A, double* __restrict__ lpA,
+                                                          const float* __restrict__ S_r, const double* __restrict__ lpS_r,
+                                                          const int* __restrict__ chg_r, float* __restrict__ S_w,
+                                                          double* __restrict__ lpS_w, int* __restrict__ chg_w,
+                                                          int* __restrict__ n_changed)
 {
     extern __shared__ float map_sm[];
     const MapSmem m = map_smem(map_sm, d.n, d.p);
-    const int p = d.p;
-    for (int t = 0; t < T; ++t) {
-        const double c = sched[t];
-        for (int j = threadIdx.x; j < p; j += blockDim.x) m.beta[j] = best[(int64_t)t * p + j];
+    const int p = d.p, t = blockIdx.x;
+    const int64_t o = (int64_t)t * p;
+    const double c = sched[t];
+    if (round == 0) {
+        for (int j = threadIdx.x; j < p; j += blockDim.x) m.beta[j] = best[o + j];
         __syncthreads();
-        double lp = map_em_block(d, c, max_em, tol, m);
-        for (int j = threadIdx.x; j < p; j += blockDim.x) map_out[(int64_t)t * p + j] = m.beta[j];
-        __syncthreads();
-        if (t > 0) {
-            for (int j = threadIdx.x; j < p; j += blockDim.x) m.beta[j] = map_out[(int64_t)(t - 1) * p + j];
-            __syncthreads();
-            const double lp2 = map_em_block(d, c, max_em, tol, m);
-            if (lp2 > lp) {
-                for (int j = threadIdx.x; j < p; j += blockDim.x) map_out[(int64_t)t * p + j] = m.beta[j];
-                lp = lp2;
-            }
+        const double lp = map_em_block(d, c, max_em, tol, m);
+        for (int j = threadIdx.x; j < p; j += blockDim.x) {
+            A[o + j] = m.beta[j];
+            S_w[o + j] = m.beta[j];
         }
-        if (threadIdx.x == 0) lp_out[t] = lp;
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            lpA[t] = lp;
+            lpS_w[t] = lp;
+            chg_w[t] = 1;
+        }
+        return;
+    }
+    if (t == 0 || chg_r[t - 1] == 0) {
+        for (int j = threadIdx.x; j < p; j += blockDim.x) S_w[o + j] = S_r[o + j];
+        if (threadIdx.x == 0) {
+            lpS_w[t] = lpS_r[t];
+            chg_w[t] = 0;
+        }
+        return;
+    }
+    for (int j = threadIdx.x; j < p; j += blockDim.x) m.beta[j] = S_r[o - p + j];
+    __syncthreads();
+    const double lp2 = map_em_block(d, c, max_em, tol, m);
+    const bool chain = lp2 > lpA[t];
+    float ndiff = 0.0f;
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        const float v = chain ? m.beta[j] : A[o + j];
+        S_w[o + j] = v;
+        if (__float_as_uint(v) != __float_as_uint(S_r[o + j])) ndiff = 1.0f;
+    }
+    ndiff = block_max_f(ndiff, m.red);
+    if (threadIdx.x == 0) {
+        const double lpn = chain ? lp2 : lpA[t];
+        const bool changed = ndiff > 0.0f || lpn != lpS_r[t];
+        lpS_w[t] = lpn;
+        chg_w[t] = changed ? 1 : 0;
+        if (changed) atomicAdd(n_changed, 1);
     }
 }
 
@@ -314,7 +352,7 @@ cudaError_t map_init_attributes()
 {
     cudaError_t e = cudaFuncSetAttribute(k_map, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAP_SMEM_MAX);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_map_path, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAP_SMEM_MAX);
+        e = cudaFuncSetAttribute(k_map_round, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAP_SMEM_MAX);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_map_lipschitz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MAP_SMEM_MAX);
     return e;
@@ -333,10 +371,14 @@ cudaError_t launch_map(const MapData& d, const float* beta0, int S, double c, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_map_path(const MapData& d, const float* best, const double* sched, int T, int max_em, float tol,
-                            float* map_out, double* lp_out, cudaStream_t st)
+cudaError_t launch_map_round(const MapData& d, const float* best, const double* sched, int T, int round, int max_em,
+                             float tol, const MapRoundBufs& b, cudaStream_t st)
 {
-    k_map_path<<<1, MAP_THREADS, map_smem_bytes(d.n, d.p), st>>>(d, best, sched, T, max_em, tol, map_out, lp_out);
+    const int r = (round + 1) & 1, w = round & 1;
+    const int64_t tp = (int64_t)T * d.p;
+    k_map_round<<<T, MAP_THREADS, map_smem_bytes(d.n, d.p), st>>>(
+        d, best, sched, round, max_em, tol, b.A, b.lpA, b.S + r * tp, b.lpS + r * T, b.chg + r * T, b.S + w * tp,
+        b.lpS + w * T, b.chg + w * T, b.n_changed);
     return cudaGetLastError();
 }
 

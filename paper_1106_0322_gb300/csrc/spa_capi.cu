@@ -153,6 +153,7 @@ struct spa_ctx {
     int64_t graph_launches = 0;
     int64_t last_launches = 0;
     int64_t best_T = 0;        // steps recorded in rb.best by the last run (0: none)
+    int map_rounds = 0;        // Jacobi rounds after round 0 of the last spa_map_path
     float* lip = nullptr;      // ||X||_2^2 / 4 for the MAP solver
     bool lip_ok = false;
 
@@ -1269,19 +1270,45 @@ int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_o
     int rc = ensure_lipschitz(c, st);
     if (rc != SPA_OK) return rc;
     const int64_t p = c->p;
-    float* dm = nullptr;
-    double* dl = nullptr;
-    cudaError_t e = dalloc(&dm, (size_t)(T * p));
-    if (e == cudaSuccess) e = dalloc(&dl, (size_t)T);
-    if (e == cudaSuccess) e = launch_map_path(map_data(c), c->rb.best, c->rb.sched, (int)T, max_em, (float)tol, dm, dl, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(map_out, dm, sizeof(float) * (size_t)(T * p), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess && logpost) e = cudaMemcpyAsync(logpost, dl, sizeof(double) * (size_t)T, cudaMemcpyDeviceToHost, st);
+    MapRoundBufs b{};
+    cudaError_t e = dalloc(&b.A, (size_t)(T * p));
+    if (e == cudaSuccess) e = dalloc(&b.lpA, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&b.S, (size_t)(2 * T * p));
+    if (e == cudaSuccess) e = dalloc(&b.lpS, (size_t)(2 * T));
+    if (e == cudaSuccess) e = dalloc(&b.chg, (size_t)(2 * T));
+    if (e == cudaSuccess) e = dalloc(&b.n_changed, 1);
+    // Round k leaves the first k + 1 steps final, so at most T rounds after round 0 change
+    // anything; the loop ends at the first round that changes nothing.
+    int last = 0;  // the last round launched; its copy holds the result
+    if (e == cudaSuccess) e = launch_map_round(map_data(c), c->rb.best, c->rb.sched, (int)T, 0, max_em, (float)tol, b, st);
+    for (int round = 1; e == cudaSuccess && round <= T; ++round) {
+        int changed = 0;
+        e = cudaMemsetAsync(b.n_changed, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_map_round(map_data(c), c->rb.best, c->rb.sched, (int)T, round, max_em, (float)tol, b, st);
+        if (e == cudaSuccess) last = round;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&changed, b.n_changed, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && changed == 0) break;
+    }
+    c->map_rounds = last;
+    const int w = last & 1;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(map_out, b.S + w * T * p, sizeof(float) * (size_t)(T * p), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && logpost)
+        e = cudaMemcpyAsync(logpost, b.lpS + w * T, sizeof(double) * (size_t)T, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    dfree(dm);
-    dfree(dl);
+    dfree(b.A);
+    dfree(b.lpA);
+    dfree(b.S);
+    dfree(b.lpS);
+    dfree(b.chg);
+    dfree(b.n_changed);
     if (e != cudaSuccess) return cuda_fail(c, e, "MAP path");
     return read_error_word(c);
 }
+
+int spa_map_path_rounds(const spa_ctx* c) { return c ? c->map_rounds : -1; }
 
 int spa_loglik(spa_ctx* c, const float* B, int64_t N, double* ll_out)
 {

@@ -227,9 +227,21 @@ cudaError_t launch_map_lipschitz(const MapData& d, float* lip, cudaStream_t st);
 // S independent EM solves from beta0 [S][p] at scale c.
 cudaError_t launch_map(const MapData& d, const float* beta0, int S, double c, int max_em, float tol, float* beta_out,
                        double* lp_out, cudaStream_t st);
-// The MAP path over T steps from the recorded best particles best [T][p].
-cudaError_t launch_map_path(const MapData& d, const float* best, const double* sched, int T, int max_em, float tol,
-                            float* map_out, double* lp_out, cudaStream_t st);
+// The MAP path over T steps from the recorded best particles best [T][p], as Jacobi rounds
+// of its recurrence: A / lpA the modes from the best particles (round 0), S / lpS / chg two
+// ping-pong copies ([2][T][p], [2][T], [2][T]) of the kept modes and of whether each changed
+// in the round that wrote it, n_changed the count of changes of one round (zeroed by the
+// caller). Round k writes copy k & 1.
+struct MapRoundBufs {
+    float* A;
+    double* lpA;
+    float* S;
+    double* lpS;
+    int* chg;
+    int* n_changed;
+};
+cudaError_t launch_map_round(const MapData& d, const float* best, const double* sched, int T, int round, int max_em,
+                             float tol, const MapRoundBufs& b, cudaStream_t st);
 // Step t's particle of highest posterior density into best[t].
 cudaError_t launch_best_particle(const MhState& s, const float* beta, int64_t N, int p, PriorArgs pr,
                                  const double* sched, int t, float* best, cudaStream_t st);

@@ -78,6 +78,31 @@ def test_map_path_is_stationary_along_the_sweep(spa):
     assert np.count_nonzero(m[-1]) <= np.count_nonzero(m[0])
 
 
+@pytest.mark.parametrize("a,move", [(4.0, "rw"), (1.0, "site")])
+def test_map_path_satisfies_its_recurrence(spa, a, move):
+    """S_t is the better of the mode from step t's best particle and EM(c_t, S_{t-1}) (Section
+    4.1): EM from S_{t-1} at c_t, run alone, either gives S_t bit for bit or a log posterior no
+    higher than S_t's, and the parallel rounds reach that fixed point within T rounds."""
+    reg = synth.make_region(300, 12, 0.9, (0.6, -0.5), seed=44)
+    T = 24
+    sched = synth.paper_schedule(1.0, T, a, ratio=0.8)
+    cfg = spa.make_config(map_path=True, move=move, init="resample_move", burn_in_steps=3)
+    with spa.Region(reg.G, reg.y, a, config=cfg) as r:
+        r.run(sched, 256, 2, 8)
+        m, lp = r.map_path(T, max_em=300, tol=1e-6)
+        rounds = r.map_path_rounds()
+        assert 1 <= rounds <= T
+        for t in range(1, T):
+            x, xlp = r.map(m[t - 1][None, :], float(sched[t]), max_em=300, tol=1e-6)
+            if np.array_equal(x[0].view(np.uint32), m[t].view(np.uint32)):
+                assert xlp[0] == lp[t]
+            else:
+                assert xlp[0] <= lp[t], t
+        # a second call is the same computation
+        m2, lp2 = r.map_path(T, max_em=300, tol=1e-6)
+    assert np.array_equal(m.view(np.uint32), m2.view(np.uint32)) and np.array_equal(lp, lp2)
+
+
 def test_map_path_needs_a_recorded_run(spa):
     reg = synth.make_region(200, 6, 0.9, (0.5,), seed=43)
     with spa.Region(reg.G, reg.y, 1.0) as r:
