@@ -17,7 +17,7 @@
 // depend on the tile shape, so the result is the same for every BN the tuner picks.
 //
 // Tile: 128 particles (M, TMEM lanes) x BN individuals (N, TMEM columns). A persistent
-// grid walks the (particle-tile, individual-tile) units in order. Warp roles: warp 0
+// grid walks the (particle-tile, individual-tile) units in order, one range per CTA. Warp roles: warp 0
 // issues TMA loads, warp 1 (one thread) issues the MMAs and owns TMEM, the epilogue warps
 // drain the double-buffered accumulator (warp w reads TMEM lanes 32 (w % 4) .. +31 and
 // one of EPI/4 column groups). Every wait is bounded.
@@ -137,6 +137,35 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
     return sp[0];
 }
 
+// The units of CTA b of G. Contiguous ranges of the row-major unit order, except with a
+// resident A, at least one CTA per particle tile, and no longer longest range than the
+// contiguous split's: then tile mt gets floor or ceil of G / m_tiles CTAs that split its
+// n-tiles, so no CTA reloads A in the middle of its range.
+__device__ __forceinline__ void tc_unit_range(bool ar, int m_tiles, int n_tiles, int b, int G, int64_t& u_begin,
+                                              int64_t& u_end)
+{
+    const int64_t U = (int64_t)m_tiles * n_tiles;
+    const int q = G / m_tiles, r = G % m_tiles;
+    if (ar && q >= 1 && (n_tiles + q - 1) / q <= (U + G - 1) / G) {
+        int mt, k, cnt;
+        if (b < r * (q + 1)) {
+            mt = b / (q + 1);
+            k = b % (q + 1);
+            cnt = q + 1;
+        } else {
+            const int b2 = b - r * (q + 1);
+            mt = r + b2 / q;
+            k = b2 % q;
+            cnt = q;
+        }
+        u_begin = (int64_t)mt * n_tiles + (int64_t)n_tiles * k / cnt;
+        u_end = (int64_t)mt * n_tiles + (int64_t)n_tiles * (k + 1) / cnt;
+    } else {
+        u_begin = U * b / G;
+        u_end = U * (b + 1) / G;
+    }
+}
+
 template <int BN, int STAGES, bool RESID, bool AR>
 __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -162,9 +191,8 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
 #define ACCF_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
 #define ACCE_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
 
-    const int64_t U = (int64_t)m_tiles * n_tiles;
-    const int64_t u_begin = U * blockIdx.x / gridDim.x;
-    const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
+    int64_t u_begin, u_end;
+    tc_unit_range(AR, m_tiles, n_tiles, (int)blockIdx.x, (int)gridDim.x, u_begin, u_end);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
