@@ -145,13 +145,6 @@ __device__ __forceinline__ bool mh_decide(const MhState& s, int64_t i, int lane,
 }
 
 
-// Accepted-proposal count: per block in shared memory, one global atomic per block.
-__device__ __forceinline__ void count_block(unsigned long long* acc_count, int* blk, bool any)
-{
-    __syncthreads();
-    if (threadIdx.x == 0 && any && *blk) atomicAdd(acc_count, (unsigned long long)*blk);
-}
-
 // ------------------------------------------------------------ RW move kernel
 // One warp per particle. With DECIDE, the warp first runs the MH test of the proposal
 // left by the previous move (its log-likelihood partials are complete, the GEMM having run
@@ -204,41 +197,50 @@ __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool l
     }
 }
 
-// The block's scale constants, formed once by thread 0: a c_t (FP64 product), 1/c_t and the
-// log-prior coefficient (FP64 instructions cost a whole warp's issue time, so not once per
-// warp).
-__device__ __forceinline__ void step_constants(PriorArgs pr, const double* sched, int t, float* sh)
+// The scale constants of every step of a schedule, formed once per sweep, so that the move
+// kernels read their step's float4 instead of redoing FP64 arithmetic in every block:
+// x = a c_t (FP64 product), y = the log-prior coefficient (-(a+1), or -1/c_t for the double
+// exponential), z = 1/c_t, w = 1/(a c_t) (FP64 quotient).
+__global__ void k_step_constants(PriorArgs pr, const double* __restrict__ sched, int T, float4* __restrict__ out)
 {
-    if (threadIdx.x == 0) {
-        const double c = sched[t];
-        sh[0] = (float)((double)pr.a * c);
-        sh[2] = 1.0f / (float)c;
-        sh[1] = pr.de ? -sh[2] : -(pr.a + 1.0f);
-        sh[3] = (float)(1.0 / ((double)pr.a * c));
-    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double c = sched[t];
+    float4 k;
+    k.x = (float)((double)pr.a * c);
+    k.z = 1.0f / (float)c;
+    k.y = pr.de ? -k.z : -(pr.a + 1.0f);
+    k.w = (float)(1.0 / ((double)pr.a * c));
+    out[t] = k;
+}
+
+// Accepted-proposal count of a block: one slot per warp, written by its lane 0 whatever the
+// outcome; thread 0 sums them and makes one global atomic.
+__device__ __forceinline__ void count_warps(unsigned long long* acc_count, const int* accw)
+{
     __syncthreads();
+    if (threadIdx.x == 0 && acc_count) {
+        int s = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += accw[k];
+        if (s) atomicAdd(acc_count, (unsigned long long)s);
+    }
 }
 
 template <bool DECIDE, bool VEC>
 __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int p, PriorArgs pr,
-                                                  const double* __restrict__ sched, int t, uint32_t m, uint32_t m_prev,
+                                                  const float4* __restrict__ stepk, int t, uint32_t m, uint32_t m_prev,
                                                   const uint64_t* __restrict__ seedp, int noise, uint32_t* err)
 {
-    __shared__ int blk;
-    __shared__ float shk[4];
-    if (DECIDE && threadIdx.x == 0) blk = 0;
-    step_constants(pr, sched, t, shk);
+    __shared__ int accw[BLOCK / 32];
     grid_dependency_wait();  // the previous kernel (the likelihood GEMM) has finished
     grid_launch_dependents();
+    const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
+    bool acc = false;
     if (i < N) {
         const uint64_t seed = (noise || DECIDE) ? *seedp : 0ull;
-        bool acc = false;
-        if (DECIDE) {
-            acc = mh_decide(a.mh, i, lane, shk[1], 0.0f, t, m_prev, seed, err);
-            if (acc && lane == 0) atomicAdd(&blk, 1);
-        }
+        if (DECIDE) acc = mh_decide(a.mh, i, lane, sk.y, 0.0f, t, m_prev, seed, err);
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         float* dst = a.beta_p + i * p;
         float* cur = a.beta + i * p;
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
         for (int g = lane; g < groups; g += 32) {
             float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
             if (noise) z = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
-            rw_group<VEC>(a, p, g, true, acc, noise, z, shk[3], pr.de, src, dst, cur, Arow, lt, yd, off);
+            rw_group<VEC>(a, p, g, true, acc, noise, z, sk.w, pr.de, src, dst, cur, Arow, lt, yd, off);
         }
         lt = warp_sum(lt);
         yd = warp_sum(yd);
@@ -260,7 +262,10 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
             if (Arow) pack_offset(Arow, a.Kp, p, off);
         }
     }
-    if (DECIDE) count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+    if (DECIDE) {
+        if (lane == 0) accw[threadIdx.x >> 5] = acc ? 1 : 0;
+        count_warps(a.mh.acc_count, accw);
+    }
 }
 
 // ------------------------------------------------------------ MALA move kernel
@@ -276,21 +281,19 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
 // are written back as the state while being read.
 template <bool DECIDE>
 __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
-                                                    const double* __restrict__ sched, int t, uint32_t m,
+                                                    const float4* __restrict__ stepk, int t, uint32_t m,
                                                     uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
 {
-    __shared__ int blk;
-    __shared__ float shk[4];
-    if (DECIDE && threadIdx.x == 0) blk = 0;
-    step_constants(pr, sched, t, shk);
+    __shared__ int accw[BLOCK / 32];
+    const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
+    bool acc = false;
     if (i < N) {
         const uint64_t seed = *seedp;
-        const float ac = shk[0], a1 = pr.a + 1.0f, inv_c = shk[2];
+        const float ac = sk.x, a1 = pr.a + 1.0f, inv_c = sk.z;
         const float h = *a.h, h2 = 0.5f * h * h;
         const float* D = a.sigma;
-        bool acc = false;
         if (DECIDE) {
             FSum bwd;
             const float* b0 = a.beta + i * p;
@@ -305,8 +308,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             bwd = warp_sum(bwd);
             const float2 fw = a.fwd[i];
             const float extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
-            acc = mh_decide(a.mh, i, lane, shk[1], extra, t, m_prev, seed, err);
-            if (acc && lane == 0) atomicAdd(&blk, 1);
+            acc = mh_decide(a.mh, i, lane, sk.y, extra, t, m_prev, seed, err);
         }
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         const float* gsrc = (acc ? a.gl_p : a.gl) + i * p;
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                     dst[j] = b;
                     const float d = (b - b0) - drift;
                     fw.add(d * d / Dj);
-                    lt.add(prior_term(b, shk[3], pr.de));
+                    lt.add(prior_term(b, sk.w, pr.de));
                     yd = fmaf(b, a.vy[j], yd);
                     if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
                 }
@@ -352,7 +354,10 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             if (Arow) pack_offset(Arow, a.Kp, p, off);
         }
     }
-    if (DECIDE) count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+    if (DECIDE) {
+        if (lane == 0) accw[threadIdx.x >> 5] = acc ? 1 : 0;
+        count_warps(a.mh.acc_count, accw);
+    }
 }
 
 // ------------------------------------------------- single-coordinate update cycle
@@ -391,22 +396,22 @@ __device__ __forceinline__ float site_trial(const float* __restrict__ eta, const
     return lq;
 }
 
-__global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, const double* __restrict__ sched, int t,
+__global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, const float4* __restrict__ stepk, int t,
                             uint32_t m0, int M, const uint64_t* __restrict__ seedp)
 {
     extern __shared__ float site_sm[];
-    __shared__ float shk[4];
     __shared__ int blk;
     const int wpc = blockDim.x >> 5;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) blk = 0;
-    step_constants(pr, sched, t, shk);
+    __syncthreads();
+    const float4 sk = stepk[t];
     float* eta = site_sm + (size_t)w * (size_t)(n + p);
     float* brow = eta + n;
     const int64_t i = (int64_t)blockIdx.x * wpc + w;
     if (i < N) {
         const uint64_t seed = *seedp;
-        const float coef = shk[1], inv_ac = shk[3];
+        const float coef = sk.y, inv_ac = sk.w;
         float* bg = a.beta + i * p;
         for (int j = lane; j < p; j += 32) brow[j] = bg[j];
         for (int r = lane; r < n; r += 32) eta[r] = 0.0f;
@@ -476,20 +481,19 @@ __global__ void k_move_site(SiteArgs a, int64_t N, int p, int n, PriorArgs pr, c
 // beta and gl hold the particles.
 template <bool MALA, bool VEC>
 __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, int p, PriorArgs pr,
-                                                      const double* __restrict__ sched, int t, uint32_t m_prev,
+                                                      const float4* __restrict__ stepk, int t, uint32_t m_prev,
                                                       const uint64_t* __restrict__ seedp, uint32_t* err)
 {
-    __shared__ int blk;
-    __shared__ float shk[4];
-    if (threadIdx.x == 0) blk = 0;
-    step_constants(pr, sched, t, shk);
+    __shared__ int accw[BLOCK / 32];
     grid_dependency_wait();
+    const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
+    bool acc = false;
     if (i < N) {
         float extra = 0.0f;
         if (MALA) {
-            const float ac = shk[0], a1 = pr.a + 1.0f, inv_c = shk[2];
+            const float ac = sk.x, a1 = pr.a + 1.0f, inv_c = sk.z;
             const float h = *a.h, h2 = 0.5f * h * h;
             FSum bwd;
             const float* b0 = a.beta + i * p;
@@ -505,9 +509,8 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
             const float2 fw = a.fwd[i];
             extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
         }
-        const bool acc = mh_decide(a.mh, i, lane, shk[1], extra, t, m_prev, *seedp, err);
+        acc = mh_decide(a.mh, i, lane, sk.y, extra, t, m_prev, *seedp, err);
         if (acc) {
-            if (lane == 0) atomicAdd(&blk, 1);
             const float* src = a.beta_p + i * p;
             float* dst = a.beta + i * p;
             if (VEC) {
@@ -521,7 +524,8 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
             }
         }
     }
-    count_block(a.mh.acc_count, &blk, a.mh.acc_count != nullptr);
+    if (lane == 0) accw[threadIdx.x >> 5] = acc ? 1 : 0;
+    count_warps(a.mh.acc_count, accw);
 }
 
 // ------------------------------------------------------------ log-likelihood finish
@@ -1395,7 +1399,13 @@ cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, float4* out, cudaStream_t st)
+{
+    k_step_constants<<<(T + 127) / 128, 128, 0, st>>>(pr, sched, T, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                            uint32_t m, uint32_t m_prev, const uint64_t* seed, int noise, uint32_t* err, cudaStream_t st)
 {
     const bool vec = (p & 3) == 0;
@@ -1405,28 +1415,28 @@ cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, Pri
         cudaLaunchAttribute attr[1];
         pdl_attr(cfg, attr);
         if (vec)
-            return cudaLaunchKernelEx(&cfg, k_move_rw<true, true>, a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
-        return cudaLaunchKernelEx(&cfg, k_move_rw<true, false>, a, N, p, pr, sched, t, m, m_prev, seed, noise, err);
+            return cudaLaunchKernelEx(&cfg, k_move_rw<true, true>, a, N, p, pr, stepk, t, m, m_prev, seed, noise, err);
+        return cudaLaunchKernelEx(&cfg, k_move_rw<true, false>, a, N, p, pr, stepk, t, m, m_prev, seed, noise, err);
     } else {
         if (vec)
-            { const cudaError_t e_ = launch_pdl(k_move_rw<false, true>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, sched, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
+            { const cudaError_t e_ = launch_pdl(k_move_rw<false, true>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, stepk, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
         else
-            { const cudaError_t e_ = launch_pdl(k_move_rw<false, false>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, sched, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
+            { const cudaError_t e_ = launch_pdl(k_move_rw<false, false>, dim3(grid), dim3(BLOCK), (size_t)(0), st, a, N, p, pr, stepk, t, m, m_prev, seed, noise, err); if (e_ != cudaSuccess) return e_; }
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
     if (decide)
-        k_move_mala<true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, err);
+        k_move_mala<true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
     else
-        k_move_mala<false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, sched, t, m, m_prev, seed, err);
+        k_move_mala<false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                                uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
     const bool vec = (p & 3) == 0;
@@ -1434,11 +1444,11 @@ cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, P
     cudaLaunchAttribute attr[1];
     pdl_attr(cfg, attr);
     if (mala) {
-        if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<true, true>, a, N, p, pr, sched, t, m_prev, seed, err);
-        return cudaLaunchKernelEx(&cfg, k_move_commit<true, false>, a, N, p, pr, sched, t, m_prev, seed, err);
+        if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<true, true>, a, N, p, pr, stepk, t, m_prev, seed, err);
+        return cudaLaunchKernelEx(&cfg, k_move_commit<true, false>, a, N, p, pr, stepk, t, m_prev, seed, err);
     }
-    if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<false, true>, a, N, p, pr, sched, t, m_prev, seed, err);
-    return cudaLaunchKernelEx(&cfg, k_move_commit<false, false>, a, N, p, pr, sched, t, m_prev, seed, err);
+    if (vec) return cudaLaunchKernelEx(&cfg, k_move_commit<false, true>, a, N, p, pr, stepk, t, m_prev, seed, err);
+    return cudaLaunchKernelEx(&cfg, k_move_commit<false, false>, a, N, p, pr, stepk, t, m_prev, seed, err);
 }
 
 int site_warps_per_block(int64_t n, int p)
@@ -1449,14 +1459,14 @@ int site_warps_per_block(int64_t n, int p)
     return (int)w;
 }
 
-cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m0, int M, const uint64_t* seed, cudaStream_t st)
 {
     if (M <= 0) return cudaSuccess;
     const int wpc = site_warps_per_block(n, p);
     if (wpc < 1) return cudaErrorInvalidValue;
     const size_t smem = (size_t)wpc * (size_t)(n + p) * sizeof(float);
-    k_move_site<<<(unsigned)((N + wpc - 1) / wpc), 32 * wpc, smem, st>>>(a, N, p, (int)n, pr, sched, t, m0, M, seed);
+    k_move_site<<<(unsigned)((N + wpc - 1) / wpc), 32 * wpc, smem, st>>>(a, N, p, (int)n, pr, stepk, t, m0, M, seed);
     return cudaGetLastError();
 }
 

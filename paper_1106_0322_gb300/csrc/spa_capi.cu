@@ -93,6 +93,7 @@ struct RunBufs {
     uint8_t* res = nullptr;
     uint64_t* seed = nullptr;
     float* best = nullptr;  // [T][p] each step's particle of highest posterior density (map_path)
+    float4* stepk = nullptr;  // [T] the move kernels' constants of each scale (launch_step_constants)
 };
 
 struct GraphKey {
@@ -131,6 +132,7 @@ struct spa_ctx {
     uint8_t* y = nullptr;
     unsigned long long* sums = nullptr;
     double *mean = nullptr, *sd = nullptr, *v = nullptr, *unit_c = nullptr;
+    float4* unit_k = nullptr;  // the move kernels' constants at c = 1 (packing at fixed scale)
     float *l2e_s = nullptr, *mean_f = nullptr, *Xf = nullptr;
     float* colf = nullptr;  // [3p]: 1/s_j, v_j, v_j log2(e) (FP32)
     __nv_bfloat16* Gbf = nullptr;
@@ -235,7 +237,7 @@ void free_workspace(Workspace& w)
 void free_runbufs(RunBufs& r)
 {
     dfree(r.sched); dfree(r.mean); dfree(r.quant); dfree(r.conc); dfree(r.ess); dfree(r.logz); dfree(r.accrate);
-    dfree(r.acc); dfree(r.res); dfree(r.seed); dfree(r.best);
+    dfree(r.acc); dfree(r.res); dfree(r.seed); dfree(r.best); dfree(r.stepk);
     r.T = 0;
 }
 
@@ -438,6 +440,7 @@ int ensure_runbufs(spa_ctx* c, int64_t T)
     RA(res, T);
     RA(seed, 1);
     RA(best, T * p);
+    RA(stepk, T);
 #undef RA
     if (e != cudaSuccess) {
         free_runbufs(r);
@@ -572,7 +575,7 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     if (c->cfg.move_kind == SPA_MOVE_SITE) {  // all M cycles in one launch
         const float inv_sp = c->cfg.precision == SPA_PREC_SPLIT_BF16 ? (float)LOG2E : 1.0f;
         const SiteArgs sa{w.beta, w.llq, w.lpq, inv_sp, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
-        q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.sched, t, m0, M, c->rb.seed, q.st));
+        q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.stepk, t, m0, M, c->rb.seed, q.st));
         return;
     }
     const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
@@ -581,12 +584,12 @@ void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
     for (int mm = 0; mm < M; ++mm) {
         const uint32_t m = m0 + (uint32_t)mm;
         if (mala)
-            q.ck(launch_move_mala(a, mm > 0, w.N, p, c->pr, c->rb.sched, t, m, m - 1u, c->rb.seed, c->d_err, q.st));
+            q.ck(launch_move_mala(a, mm > 0, w.N, p, c->pr, c->rb.stepk, t, m, m - 1u, c->rb.seed, c->d_err, q.st));
         else
-            q.ck(launch_move_rw(a, mm > 0, w.N, p, c->pr, c->rb.sched, t, m, m - 1u, c->rb.seed, 1, c->d_err, q.st));
+            q.ck(launch_move_rw(a, mm > 0, w.N, p, c->pr, c->rb.stepk, t, m, m - 1u, c->rb.seed, 1, c->d_err, q.st));
         enq_proposal_likelihood(q, mala);
     }
-    q.ck(launch_move_commit(a, mala, w.N, p, c->pr, c->rb.sched, t, m0 + (uint32_t)(M - 1), c->rb.seed, c->d_err, q.st));
+    q.ck(launch_move_commit(a, mala, w.N, p, c->pr, c->rb.stepk, t, m0 + (uint32_t)(M - 1), c->rb.seed, c->d_err, q.st));
 }
 
 void enq_resample(Enq& q, int t)
@@ -638,10 +641,11 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
     if (mala) q.ck(launch_set_f64(w.lambda, cfg.mala_h, q.st));
     const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
+    q.ck(launch_step_constants(c->pr, r.sched, (int)T, r.stepk, q.st));
     // t = 0: prior draws, their log-likelihoods, importance weights
     q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
     const MoveArgs a0 = move_args(c, nullptr);
-    q.ck(launch_move_rw(a0, false, w.N, p, c->pr, r.sched, 0, 0u, 0u, r.seed, 0, c->d_err, q.st));
+    q.ck(launch_move_rw(a0, false, w.N, p, c->pr, r.stepk, 0, 0u, 0u, r.seed, 0, c->d_err, q.st));
     if (mala && tc) {
         enq_grad_tc(q, w.gl, w.beta, 0.0, w.N);  // also leaves the softplus partials of the draws
     } else {
@@ -738,7 +742,7 @@ void destroy(spa_ctx* c)
     drop_graph(c);
     free_workspace(c->ws);
     free_runbufs(c->rb);
-    dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c);
+    dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c); dfree(c->unit_k);
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
     dfree(c->ybits); dfree(c->XT2); dfree(c->lip);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -906,7 +910,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     CA(G, n * p);
     CA(y, n);
     CA(sums, 3 * p + 1);
-    CA(mean, p); CA(sd, p); CA(v, p); CA(unit_c, 1);
+    CA(mean, p); CA(sd, p); CA(v, p); CA(unit_c, 1); CA(unit_k, 1);
     CA(l2e_s, p); CA(mean_f, p); CA(colf, 3 * p);
     CA(Xf, n * p);
     CA(Gbf, n * c->Kp);
@@ -926,6 +930,8 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     }
     const double one = 1.0;
     e = cudaMemcpy(c->unit_c, &one, sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_step_constants(c->pr, c->unit_c, 1, c->unit_k, c->own_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
     if (e != cudaSuccess) {
         set_thread_error_str(cudaGetErrorString(e));
         destroy(c);
@@ -1187,7 +1193,7 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
                        st),
        "copy B");
     const MoveArgs a = move_args(c, nullptr);
-    CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_c, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
+    CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_k, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
     if (tc) {
         CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
            "loglik tc");
@@ -1346,7 +1352,7 @@ static int grad_impl(spa_ctx* c, const float* B, bool dev, int64_t N, double cs,
         q.c = c;
         q.st = st;
         const MoveArgs a = move_args(c, nullptr);
-        q.ck(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_c, 0, 0u, 0u, nullptr, 0, c->d_err, st));
+        q.ck(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_k, 0, 0u, 0u, nullptr, 0, c->d_err, st));
         enq_grad_tc(q, dev ? grad : w.grad, w.beta, cs, N);
         q.ck(launch_finish_loglik(a.mh, N, nullptr, (dev && ll) ? ll : w.ll, c->d_err, st));
         if (q.e != cudaSuccess) return cuda_fail(c, q.e, "gradient (tensor cores)");

@@ -116,18 +116,21 @@ struct SiteArgs {
 constexpr size_t SITE_SMEM_MAX = 220 * 1024;  // eta2 and beta rows of a block's particles
 // Particles per block (one warp each) for n individuals and p markers; 0 if one does not fit.
 int site_warps_per_block(int64_t n, int p);
-cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m0, int M, const uint64_t* seed, cudaStream_t st);
 
+// The move kernels' per-step constants of a schedule sched [T]: (a c_t, log-prior
+// coefficient, 1/c_t, 1/(a c_t)) into out [T].
+cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, float4* out, cudaStream_t st);
 // Random-walk move (decide: MH test of the pending proposal first; noise = 0: pack beta
 // unchanged, for the log-likelihood entry points and t = 0).
-cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                            uint32_t m, uint32_t m_prev, const uint64_t* seed, int noise, uint32_t* err, cudaStream_t st);
 // MALA move: needs grad l of the states in gl, D_j (sigma) and h from launch_colstats kind 1.
-cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st);
 // MH test of the pending proposals, then accepted rows (and gradients) into the state.
-cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const double* sched, int t,
+cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                                uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st);
 // The packed particles' log-likelihoods as the state (llq, lpq), and in FP64 to logw
 // (prior-IS weights) and/or ll_out; either may be NULL.
