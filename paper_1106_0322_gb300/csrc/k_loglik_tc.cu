@@ -53,8 +53,8 @@ struct TcCfg {
     static constexpr int A_RES = AR ? KB_RES * 2 * A_TILE : 0;
     static constexpr int STAGE = AR ? B_TILE : 2 * A_TILE + B_TILE;
     static constexpr int BAR_OFF = A_RES + STAGES * STAGE;
-    // full[S], empty[S], acc_full[2], acc_empty[2], drain, a_full, a_empty
-    static constexpr int NBARS = 2 * STAGES + 7;
+    // full[S], empty[S], acc_full[2], acc_empty[2], drain, a_empty, a_full[KB_RES]
+    static constexpr int NBARS = 2 * STAGES + 6 + KB_RES;
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
     static constexpr int BYTES = SLOT_OFF + 16;
     static constexpr int SMEM = BYTES + 1024;  // slack for the 1024-byte alignment of the tiles
@@ -183,13 +183,15 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = sbase + C::BAR_OFF;
     const uint32_t drain_bar = bar0 + 8 * (2 * STAGES + 4);
-    const uint32_t afull_bar = bar0 + 8 * (2 * STAGES + 5);
-    const uint32_t aempty_bar = bar0 + 8 * (2 * STAGES + 6);
+    const uint32_t aempty_bar = bar0 + 8 * (2 * STAGES + 5);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
 #define FULL_BAR(s) (bar0 + 8u * (uint32_t)(s))
 #define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
 #define ACCF_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
 #define ACCE_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
+// one per k-block of the resident A, so that the first MMAs of an epoch need only their own
+// k-block of A, not all of it
+#define AFULL_BAR(kb) (bar0 + 8u * (uint32_t)(2 * STAGES + 6 + (kb)))
 
     int64_t u_begin, u_end;
     tc_unit_range(AR, m_tiles, n_tiles, (int)blockIdx.x, (int)gridDim.x, u_begin, u_end);
@@ -204,8 +206,8 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             mbar_init(ACCE_BAR(b), Epi<RESID>::WARPS);
         }
         mbar_init(drain_bar, 1);
-        mbar_init(afull_bar, 1);
         mbar_init(aempty_bar, 1);
+        for (int kb = 0; kb < KB_RES; ++kb) mbar_init(AFULL_BAR(kb), 1);
         mbar_fence_init();
     }
     if (warp == 0 && lane == 0) {
@@ -241,8 +243,10 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             uint32_t it = 0;
             bool ok = true;
             int epoch = -1, cur_mt = -1;  // A-resident: one epoch per run of units with the same m-tile
+            int a_issued = 0;             // k-blocks of the current epoch's A sent out
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
                 const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+                bool a_first = false;  // the epoch's first unit: A's k-blocks go out between its G stages
                 if (AR && mt != cur_mt) {
                     ++epoch;
                     // the previous epoch's MMAs must be done with the resident A
@@ -250,16 +254,20 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(afull_bar, (uint32_t)(kb_last * 2 * C::A_TILE) + 2u * a_tail);
-                    for (int kb = 0; kb < kblocks; ++kb) {
-                        const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
-                        const CUtensorMap* ma = (tw && kb == kb_last) ? &mapAt : &mapA;
-                        tma_load_2d(a, ma, afull_bar, kb * BK, mt * BM);
-                        tma_load_2d(a + C::A_TILE, ma, afull_bar, Kp + kb * BK, mt * BM);
-                    }
+                    a_first = true;
+                    a_issued = 0;
                     cur_mt = mt;
                 }
                 for (int kb = 0; kb < kblocks; ++kb) {
+                    if (AR && a_first) {
+                        const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
+                        const bool tail = tw && kb == kb_last;
+                        const CUtensorMap* ma = tail ? &mapAt : &mapA;
+                        mbar_arrive_expect_tx(AFULL_BAR(kb), tail ? 2u * a_tail : 2u * (uint32_t)C::A_TILE);
+                        tma_load_2d(a, ma, AFULL_BAR(kb), kb * BK, mt * BM);
+                        tma_load_2d(a + C::A_TILE, ma, AFULL_BAR(kb), Kp + kb * BK, mt * BM);
+                        ++a_issued;
+                    }
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
                     if (!mbar_wait_bounded(EMPTY_BAR(s), ph ^ 1u, err)) {
                         ok = false;
@@ -289,7 +297,9 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 const uint32_t i2 = it - k;
                 mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
             }
-            if (AR && epoch >= 0) mbar_wait_bounded(afull_bar, (uint32_t)(epoch & 1), err, 100000000ull);
+            if (AR && epoch >= 0)
+                for (int kb = 0; kb < a_issued; ++kb)
+                    mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err, 100000000ull);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
@@ -306,18 +316,20 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                     ok = false;
                     break;
                 }
+                bool a_first = false;  // the epoch's first unit waits for each k-block of A
                 if (AR && mt != cur_mt) {
                     ++epoch;
-                    if (!mbar_wait_bounded(afull_bar, (uint32_t)(epoch & 1), err)) {
-                        ok = false;
-                        break;
-                    }
+                    a_first = true;
                     cur_mt = mt;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
                 for (int kb = 0; kb < kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
+                    if (AR && a_first && !mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err)) {
+                        ok = false;
+                        break;
+                    }
                     if (!mbar_wait_bounded(FULL_BAR(s), ph, err)) {
                         ok = false;
                         break;
@@ -407,6 +419,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
 #undef EMPTY_BAR
 #undef ACCF_BAR
 #undef ACCE_BAR
+#undef AFULL_BAR
     __syncwarp();
     tc_fence_before();
     __syncthreads();
