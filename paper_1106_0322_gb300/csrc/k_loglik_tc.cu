@@ -65,8 +65,10 @@ struct TcCfg {
 };
 
 // Sum over the first `valid` of 32 columns of softplus2(eta2) = log2(1 + 2^eta2): 32
-// independent ex2/lg2 pairs, then a tree. (Folding the logarithms into one of a running
-// product was measured slower: the epilogue is latency-bound, and the product is a chain.)
+// independent ex2/lg2 pairs, then a tree. (Folding the logarithms into one lg2 of the
+// product of the (1 + 2^-|eta2|) factors was measured slower, both as a running product, a
+// 32-long chain, and as a depth-5 product tree: the epilogue is bound by instruction issue,
+// not by the SFU.)
 __device__ __forceinline__ float sum_sp2_32(const uint32_t (&r)[32], int valid)
 {
     float t[32];
