@@ -1050,13 +1050,23 @@ __device__ int warp_find_bin(const uint32_t* hist, int nbins, unsigned long long
 
 // keysT[j][i] = float_key(beta[i][j]): the particles' values marker-major as
 // order-preserving integer keys, so each summaries CTA streams its marker's column with
-// coalesced loads. 32 x 32 tiles through shared memory.
-__global__ void k_keys_transpose(const float* __restrict__ beta, int64_t N, int p, uint32_t* __restrict__ keysT)
+// coalesced loads. 32 x 32 tiles through shared memory. With WfS != NULL the weights (Wf,
+// wfix) are copied beside them, so that the summaries read nothing the next step rewrites.
+__global__ void k_keys_transpose(const float* __restrict__ beta, int64_t N, int p, uint32_t* __restrict__ keysT,
+                                 const float* __restrict__ Wf, const uint32_t* __restrict__ wfix,
+                                 float* __restrict__ WfS, uint32_t* __restrict__ wfixS)
 {
     grid_dependency_wait();
     __shared__ uint32_t tile[32][33];
     const int64_t i0 = (int64_t)blockIdx.x * 32;
     const int j0 = blockIdx.y * 32;
+    if (WfS && blockIdx.y == 0 && threadIdx.y == 0) {
+        const int64_t i = i0 + threadIdx.x;
+        if (i < N) {
+            WfS[i] = Wf[i];
+            wfixS[i] = wfix[i];
+        }
+    }
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t i = i0 + r;
         const int j = j0 + threadIdx.x;
@@ -1566,14 +1576,19 @@ cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p
     return cudaGetLastError();
 }
 
-cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p,
-                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
-                             cudaStream_t st)
+cudaError_t launch_keys(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p, uint32_t* keysT,
+                        float* WfS, uint32_t* wfixS, bool pdl, cudaStream_t st)
 {
-    { const cudaError_t e_ = launch_pdl(k_keys_transpose, dim3(dim3((unsigned)((N + 31) / 32), (unsigned)((p + 31) / 32))), dim3(dim3(32, 8)), (size_t)(0), st, beta, N, p,
-                                                                                                      keysT); if (e_ != cudaSuccess) return e_; }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((p + 31) / 32)), block(32, 8);
+    if (pdl) return launch_pdl(k_keys_transpose, grid, block, (size_t)0, st, beta, N, p, keysT, Wf, wfix, WfS, wfixS);
+    k_keys_transpose<<<grid, block, 0, st>>>(beta, N, p, keysT, Wf, wfix, WfS, wfixS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_summaries_keys(const uint32_t* keysT, const float* Wf, const uint32_t* wfix, int64_t N, int p,
+                                  const SummaryArgs& s, int t, double* mean, double* quant, double* conc, bool pdl,
+                                  cudaStream_t st)
+{
     SummaryArgs a = s;
     // host-side constants: the smallest float >= Delta (the open interval |b| < Delta tested
     // in FP32) and the fixed-point quantile targets ceil(q 2^31)
@@ -1588,8 +1603,20 @@ cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t*
     const size_t staged_bytes = (size_t)N * 2 * sizeof(uint32_t) + hist_bytes;
     const int staged = staged_bytes <= SUM_STAGED_MAX ? 1 : 0;
     const size_t bytes = staged ? staged_bytes : hist_bytes;
-    { const cudaError_t e_ = launch_pdl(k_summaries, dim3((unsigned)p), dim3(SUM_THREADS), (size_t)(bytes), st, keysT, Wf, wfix, N, p, a, t, mean, quant, conc, staged); if (e_ != cudaSuccess) return e_; }
+    if (pdl)
+        return launch_pdl(k_summaries, dim3((unsigned)p), dim3(SUM_THREADS), bytes, st, keysT, Wf, wfix, N, p, a, t, mean,
+                          quant, conc, staged);
+    k_summaries<<<(unsigned)p, SUM_THREADS, bytes, st>>>(keysT, Wf, wfix, N, p, a, t, mean, quant, conc, staged);
     return cudaGetLastError();
+}
+
+cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p,
+                             const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
+                             cudaStream_t st)
+{
+    const cudaError_t e = launch_keys(beta, Wf, wfix, N, p, keysT, nullptr, nullptr, true, st);
+    if (e != cudaSuccess) return e;
+    return launch_summaries_keys(keysT, Wf, wfix, N, p, s, t, mean, quant, conc, true, st);
 }
 
 cudaError_t launch_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,

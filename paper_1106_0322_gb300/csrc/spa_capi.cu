@@ -65,6 +65,8 @@ struct Workspace {
     uint32_t* wfix = nullptr;
     double *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
     uint32_t* keysT = nullptr;  // [p][N] order-preserving keys of beta for the summaries
+    float* WfS = nullptr;       // the weights the summaries of a step read, copied beside the keys
+    uint32_t* wfixS = nullptr;
     unsigned int* lse_counter = nullptr;
     float4* colpart = nullptr;
     float* h = nullptr;  // MALA step h = lambda p^(-1/6)
@@ -125,6 +127,10 @@ struct spa_ctx {
     PriorArgs pr{1.0f, 0};
     int device = 0, num_sms = 0;
     cudaStream_t own_stream = nullptr;
+    // the summaries of step t run on side_stream beside step t + 1 (fork after the key
+    // transpose, join before the next one)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     spa_config cfg;
     std::string err;
     // genotype store
@@ -226,7 +232,7 @@ void free_workspace(Workspace& w)
 {
     dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
     dfree(w.lpt_p); dfree(w.ydq); dfree(w.llq); dfree(w.lpq); dfree(w.llq_tmp); dfree(w.lpq_tmp);
-    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.keysT); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
+    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.keysT); dfree(w.WfS); dfree(w.wfixS); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
     dfree(w.lse_scratch); dfree(w.lse_counter);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
     dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
@@ -348,6 +354,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     WA(lpt_p, N); WA(ydq, N); WA(llq, N); WA(lpq, N); WA(llq_tmp, N); WA(lpq_tmp, N);
     WA(ll, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
     WA(keysT, N * p);
+    WA(WfS, N); WA(wfixS, N);
     WA(cum, N + nblk + 1);
     WA(colpart, (int64_t)COLSTAT_SPLITS * p);
     WA(lambda, 1);
@@ -628,6 +635,10 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     const bool mala = cfg.move_kind == SPA_MOVE_MALA;
     const int p = (int)c->p;
     const bool site = cfg.move_kind == SPA_MOVE_SITE;
+    // The step's summaries overlap the next step when that step is many short kernels (RW,
+    // MALA). The single-coordinate cycle is one long launch per step whose blocks fill the
+    // SMs: the summaries would only take SMs from it (measured 2% slower), so they stay inline.
+    const bool fork_sum = !site;
     // acceptance is per proposal: per coordinate update for the single-coordinate cycle
     const double denom = (double)w.N * (double)M * (site ? (double)p : 1.0);
     SummaryArgs sa;
@@ -683,12 +694,25 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
         enq_resample(q, (int)t);
         if (!site) enq_colstats(q, (int)t);
         enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
-        q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
+        if (fork_sum) {
+            // The summaries of step t run on the side stream beside step t + 1: the transpose
+            // snapshots the keys and the weights, and the next transpose waits for them.
+            if (t > 0 && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_join, 0);
+            q.ck(launch_keys(w.beta, w.Wf, w.wfix, w.N, p, w.keysT, w.WfS, w.wfixS, false, q.st));
+            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_fork, q.st);
+            if (q.e == cudaSuccess) q.e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+            q.ck(launch_summaries_keys(w.keysT, w.WfS, w.wfixS, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, false,
+                                       c->side_stream));
+            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_join, c->side_stream);
+        } else {
+            q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
+        }
         ++q.launches;  // the key transpose and the summaries
         if (cfg.map_path)
             q.ck(launch_best_particle(mh_state(c, nullptr), w.beta, w.N, p, c->pr, r.sched, (int)t, r.best, q.st));
         if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
     }
+    if (fork_sum && T > 0 && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_join, 0);  // the last summaries
     q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
     *err_out = q.e;
     return q.launches;
@@ -745,6 +769,9 @@ void destroy(spa_ctx* c)
     dfree(c->G); dfree(c->y); dfree(c->sums); dfree(c->mean); dfree(c->sd); dfree(c->v); dfree(c->unit_c); dfree(c->unit_k);
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
     dfree(c->ybits); dfree(c->XT2); dfree(c->lip);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
 }
@@ -905,6 +932,9 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     c->pr.de = std::isinf(nu) ? 1 : 0;
     c->pr.a = c->pr.de ? 1.0f : (float)nu;
     cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
 #define CA(ptr, cnt) \
     if (e == cudaSuccess) e = dalloc(&c->ptr, (size_t)(cnt))
     CA(G, n * p);

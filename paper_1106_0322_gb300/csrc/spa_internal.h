@@ -192,6 +192,14 @@ struct SummaryArgs {
 cudaError_t launch_summaries(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p,
                              const SummaryArgs& s, int t, double* mean, double* quant, double* conc, uint32_t* keysT,
                              cudaStream_t st);
+// The two halves of launch_summaries, for running the summaries beside the next step: the
+// key transpose (with WfS != NULL also a copy of the weights into WfS, wfixS), then the
+// summaries from keys and weights. pdl: launch with programmatic stream serialization.
+cudaError_t launch_keys(const float* beta, const float* Wf, const uint32_t* wfix, int64_t N, int p, uint32_t* keysT,
+                        float* WfS, uint32_t* wfixS, bool pdl, cudaStream_t st);
+cudaError_t launch_summaries_keys(const uint32_t* keysT, const float* Wf, const uint32_t* wfix, int64_t N, int p,
+                                  const SummaryArgs& s, int t, double* mean, double* quant, double* conc, bool pdl,
+                                  cudaStream_t st);
 
 // Scale-marginalised summaries (mixture over the steps with weights Z_t / Z_1).
 cudaError_t launch_marginal(const double* log_z_inc, const double* mean, const double* conc, int64_t T, int64_t p,
