@@ -706,8 +706,8 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
             if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_join, c->side_stream);
         } else {
             q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
+            ++q.launches;  // the key transpose and the summaries
         }
-        ++q.launches;  // the key transpose and the summaries
         if (cfg.map_path)
             q.ck(launch_best_particle(mh_state(c, nullptr), w.beta, w.N, p, c->pr, r.sched, (int)t, r.best, q.st));
         if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
