@@ -201,7 +201,8 @@ __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool l
 // kernels read their step's float4 instead of redoing FP64 arithmetic in every block:
 // x = a c_t (FP64 product), y = the log-prior coefficient (-(a+1), or -1/c_t for the double
 // exponential), z = 1/c_t, w = 1/(a c_t) (FP64 quotient).
-__global__ void k_step_constants(PriorArgs pr, const double* __restrict__ sched, int T, float4* __restrict__ out)
+__global__ void k_step_constants(PriorArgs pr, const double* __restrict__ sched, int T, int p, float4* __restrict__ out,
+                                 ReweightK* __restrict__ rk)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= T) return;
@@ -212,6 +213,19 @@ __global__ void k_step_constants(PriorArgs pr, const double* __restrict__ sched,
     k.y = pr.de ? -k.z : -(pr.a + 1.0f);
     k.w = (float)(1.0 / ((double)pr.a * c));
     out[t] = k;
+    if (rk) {
+        ReweightK r{};
+        if (t > 0) {
+            const double cp = sched[t - 1];
+            r.k1 = (float)(cp - c);
+            r.kc = (float)c;
+            r.kac = (float)((double)pr.a * cp);
+            r.inv_ac = (float)(1.0 / ((double)pr.a * c));
+            r.lbase = -(double)p * log(c / cp);
+            r.dinv = 1.0 / c - 1.0 / cp;
+        }
+        rk[t] = r;
+    }
 }
 
 // Accepted-proposal count of a block: one slot per warp, written by its lane 0 whatever the
@@ -552,29 +566,20 @@ __global__ void __launch_bounds__(BLOCK) k_finish_loglik(MhState s, int64_t N, d
 // cancellation: -log(c_t/c_{t-1}) - (a+1) log1p(x (c_{t-1} - c_t) / (c_t (a c_{t-1} + x))),
 // x = |beta_ij| (double exponential: -log(c_t/c_{t-1}) - x (1/c_t - 1/c_{t-1})).
 // A block handles 32 particles: its warps form the FP32 row sums, then warp 0 finishes one
-// particle per lane in FP64.
-constexpr int RW_PER_BLOCK = 32;
+// particle per lane in FP64. The step's constants come from the per-sweep table.
+constexpr int RW_PER_BLOCK = 8;
 constexpr int RW_THREADS = 32 * RW_PER_BLOCK;
 
 __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict__ beta, double* __restrict__ logw,
                                                    float2* __restrict__ lpq, int64_t N, int p, PriorArgs pr,
-                                                   const double* __restrict__ sched, int t, uint32_t* __restrict__ err)
+                                                   const ReweightK* __restrict__ rkp, int t, uint32_t* __restrict__ err)
 {
     grid_dependency_wait();
     __shared__ float4 sums[RW_PER_BLOCK];
-    __shared__ float shk[5];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * RW_PER_BLOCK;
-    if (threadIdx.x == 0) {  // the scale constants once per block (FP64)
-        const double c = sched[t], cp = sched[t - 1];
-        shk[0] = (float)(cp - c);
-        shk[1] = (float)c;
-        shk[2] = (float)((double)pr.a * cp);
-        shk[3] = (float)((double)pr.a * c);
-        shk[4] = (float)(1.0 / ((double)pr.a * c));
-    }
-    __syncthreads();
-    const float k1 = shk[0], kc = shk[1], kac = shk[2], inv_ac = shk[4];
+    const ReweightK rk = rkp[t];
+    const float k1 = rk.k1, kc = rk.kc, kac = rk.kac, inv_ac = rk.inv_ac;
     {
         const int q = w;
         const int64_t i = base + q;
@@ -591,14 +596,12 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
         if (lane == 0) sums[q] = make_float4(sdiff.s, sdiff.c, snew.s, snew.c);
     }
     __syncthreads();
-    if (w == 0) {
+    if (w == 0 && lane < RW_PER_BLOCK) {
         const int64_t i = base + lane;
-        const double c = sched[t], cp = sched[t - 1];
         if (i < N) {
             const float4 s = sums[lane];
             const double sd = (double)s.x + (double)s.y;
-            const double lbase = -(double)p * log(c / cp);
-            const double d = pr.de ? lbase - sd * (1.0 / c - 1.0 / cp) : lbase - ((double)pr.a + 1.0) * sd;
+            const double d = pr.de ? rk.lbase - sd * rk.dinv : rk.lbase - ((double)pr.a + 1.0) * sd;
             const double nl = logw[i] + d;
             if (!isfinite(nl)) atomicOr(err, DERR_NONFINITE);
             logw[i] = nl;
@@ -1409,9 +1412,10 @@ cudaError_t launch_init_prior(float* beta, int64_t N, int p, PriorArgs pr, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, float4* out, cudaStream_t st)
+cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, int p, float4* out, ReweightK* rk,
+                                  cudaStream_t st)
 {
-    k_step_constants<<<(T + 127) / 128, 128, 0, st>>>(pr, sched, T, out);
+    k_step_constants<<<(T + 127) / 128, 128, 0, st>>>(pr, sched, T, p, out, rk);
     return cudaGetLastError();
 }
 
@@ -1488,9 +1492,9 @@ cudaError_t launch_finish_loglik(const MhState& s, int64_t N, double* logw, doub
 }
 
 cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_t N, int p, PriorArgs pr,
-                            const double* sched, int t, uint32_t* err, cudaStream_t st)
+                            const ReweightK* rk, int t, uint32_t* err, cudaStream_t st)
 {
-    { const cudaError_t e_ = launch_pdl(k_reweight, dim3((unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK)), dim3(RW_THREADS), (size_t)(0), st, beta, logw, lpq, N, p, pr, sched,
+    { const cudaError_t e_ = launch_pdl(k_reweight, dim3((unsigned)((N + RW_PER_BLOCK - 1) / RW_PER_BLOCK)), dim3(RW_THREADS), (size_t)(0), st, beta, logw, lpq, N, p, pr, rk,
                                                                                          t, err); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }

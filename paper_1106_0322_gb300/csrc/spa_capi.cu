@@ -96,6 +96,7 @@ struct RunBufs {
     uint64_t* seed = nullptr;
     float* best = nullptr;  // [T][p] each step's particle of highest posterior density (map_path)
     float4* stepk = nullptr;  // [T] the move kernels' constants of each scale (launch_step_constants)
+    ReweightK* rk = nullptr;  // [T] the reweighting kernel's constants of each step
 };
 
 struct GraphKey {
@@ -243,7 +244,7 @@ void free_workspace(Workspace& w)
 void free_runbufs(RunBufs& r)
 {
     dfree(r.sched); dfree(r.mean); dfree(r.quant); dfree(r.conc); dfree(r.ess); dfree(r.logz); dfree(r.accrate);
-    dfree(r.acc); dfree(r.res); dfree(r.seed); dfree(r.best); dfree(r.stepk);
+    dfree(r.acc); dfree(r.res); dfree(r.seed); dfree(r.best); dfree(r.stepk); dfree(r.rk);
     r.T = 0;
 }
 
@@ -448,6 +449,7 @@ int ensure_runbufs(spa_ctx* c, int64_t T)
     RA(seed, 1);
     RA(best, T * p);
     RA(stepk, T);
+    RA(rk, T);
 #undef RA
     if (e != cudaSuccess) {
         free_runbufs(r);
@@ -652,7 +654,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
     if (mala) q.ck(launch_set_f64(w.lambda, cfg.mala_h, q.st));
     const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
-    q.ck(launch_step_constants(c->pr, r.sched, (int)T, r.stepk, q.st));
+    q.ck(launch_step_constants(c->pr, r.sched, (int)T, p, r.stepk, r.rk, q.st));
     // t = 0: prior draws, their log-likelihoods, importance weights
     q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
     const MoveArgs a0 = move_args(c, nullptr);
@@ -686,7 +688,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     }
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0) {
-            q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.sched, (int)t, c->d_err, q.st));
+            q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.rk, (int)t, c->d_err, q.st));
             q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
                                 c->d_err, q.st));
             ++q.launches;
@@ -960,7 +962,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     }
     const double one = 1.0;
     e = cudaMemcpy(c->unit_c, &one, sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_step_constants(c->pr, c->unit_c, 1, c->unit_k, c->own_stream);
+    if (e == cudaSuccess) e = launch_step_constants(c->pr, c->unit_c, 1, (int)c->p, c->unit_k, nullptr, c->own_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->own_stream);
     if (e != cudaSuccess) {
         set_thread_error_str(cudaGetErrorString(e));
@@ -1505,14 +1507,17 @@ int spa_incr_weight(double nu, double c_prev, double c_new, const float* B, int6
     float2* dL = s.get<float2>(N);
     double* dS = s.get<double>(2);
     uint32_t* dE = s.get<uint32_t>(1);
-    if (!dB || !dW || !dL || !dS || !dE) return fail(nullptr, SPA_ENOMEM, "device allocation");
+    float4* dK = s.get<float4>(2);
+    ReweightK* dR = s.get<ReweightK>(2);
+    if (!dB || !dW || !dL || !dS || !dE || !dK || !dR) return fail(nullptr, SPA_ENOMEM, "device allocation");
     cudaStream_t st = cudaStreamPerThread;
     const double sched[2] = {c_prev, c_new};
     cudaError_t e = cudaMemcpyAsync(dB, B, sizeof(float) * (size_t)(N * p), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dS, sched, sizeof(sched), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dW, 0, sizeof(double) * (size_t)N, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(dE, 0, sizeof(uint32_t), st);
-    if (e == cudaSuccess) e = launch_reweight(dB, dW, dL, N, (int)p, pr, dS, 1, dE, st);
+    if (e == cudaSuccess) e = launch_step_constants(pr, dS, 2, (int)p, dK, dR, st);
+    if (e == cudaSuccess) e = launch_reweight(dB, dW, dL, N, (int)p, pr, dR, 1, dE, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dW, sizeof(double) * (size_t)N, cudaMemcpyDeviceToHost, st);
     return finish_free(e, "incremental weight");
 }

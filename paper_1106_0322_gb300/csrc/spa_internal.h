@@ -119,9 +119,17 @@ int site_warps_per_block(int64_t n, int p);
 cudaError_t launch_move_site(const SiteArgs& a, int64_t N, int p, int64_t n, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m0, int M, const uint64_t* seed, cudaStream_t st);
 
-// The move kernels' per-step constants of a schedule sched [T]: (a c_t, log-prior
-// coefficient, 1/c_t, 1/(a c_t)) into out [T].
-cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, float4* out, cudaStream_t st);
+// The reweighting kernel's constants of step t >= 1 (entry 0 unused).
+struct ReweightK {
+    float k1, kc, kac, inv_ac;  // c_{t-1} - c_t, c_t, a c_{t-1}, 1/(a c_t)
+    double lbase;               // -p log(c_t / c_{t-1})
+    double dinv;                // 1/c_t - 1/c_{t-1}
+};
+// The per-step constants of a schedule sched [T]: the move kernels' (a c_t, log-prior
+// coefficient, 1/c_t, 1/(a c_t)) into out [T] and, with rk != NULL, the reweighting
+// kernel's into rk [T] (p markers).
+cudaError_t launch_step_constants(PriorArgs pr, const double* sched, int T, int p, float4* out, ReweightK* rk,
+                                  cudaStream_t st);
 // Random-walk move (decide: MH test of the pending proposal first; noise = 0: pack beta
 // unchanged, for the log-likelihood entry points and t = 0).
 cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
@@ -142,7 +150,7 @@ cudaError_t launch_set_f64(double* ptr, double v, cudaStream_t st);
 
 // logw += log p(beta | c_t) - log p(beta | c_{t-1}); the log-prior pair lpq refreshed at c_t.
 cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_t N, int p, PriorArgs pr,
-                            const double* sched, int t, uint32_t* err, cudaStream_t st);
+                            const ReweightK* rk, int t, uint32_t* err, cudaStream_t st);
 
 // Log-sum-exp and ESS of logw (per-CTA partial (max, sum e, sum e^2) combined in block order
 // by the last CTA), then normalisation into W, Wf, wfix.

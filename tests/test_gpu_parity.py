@@ -185,6 +185,27 @@ def test_loglik_split_bf16_bound(spa, n, p, N):
     assert np.median(err / bound) < 0.05
 
 
+@pytest.mark.parametrize("n,p,N", [(300, 37, 700), (2000, 200, 8192), (5000, 500, 384)])
+def test_loglik_same_for_every_tile_width(spa, monkeypatch, n, p, N):
+    """One partial per 32-individual chunk whatever the n-tile width: the log-likelihoods at
+    BN = 128 and 256, and at the tuner's own choice, are bit-identical (resident and
+    streaming particle operand, ragged n and N)."""
+    reg = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=51)
+    B = synth.random_particles(N, p, 0.05, seed=52)
+    out = {}
+    for bn in ("128", "256", None):
+        if bn is None:
+            monkeypatch.delenv("SPA_LOGLIK_BN", raising=False)
+        else:
+            monkeypatch.setenv("SPA_LOGLIK_BN", bn)
+        with spa.Region(reg.G, reg.y, 1.0) as r:
+            out[bn] = r.loglik(B)
+            if bn is not None:
+                assert r.loglik_tile_width() == int(bn)
+    assert np.array_equal(out["128"].view(np.uint64), out["256"].view(np.uint64))
+    assert np.array_equal(out["128"].view(np.uint64), out[None].view(np.uint64))
+
+
 @pytest.mark.parametrize("n,p,N", SMALL_SHAPES)
 def test_loglik_fp32_relative(spa, n, p, N):
     reg = synth.make_region(max(n, 2), p, 0.9, (0.5, -0.3), seed=n + p)
