@@ -9,8 +9,8 @@
 // gradient steps beta <- S(z + grad l(z) / L, w / L) with L = ||X||_2^2 / 4 (the logistic
 // loss's curvature bound), Nesterov momentum, and the gradient-based restart of
 // O'Donoghue and Candes (2015): momentum is dropped whenever (z - beta') . (beta' - beta) > 0.
-// Each step is two FP32 matrix-vector products with the standardised X (rows of X for
-// X z, rows of X^T for X^T r, both read with unit stride) on the block's shared memory.
+// Each step is two FP32 matrix-vector products with the standardised X, both from X^T
+// log2(e) in [p][n] layout (coalesced columns for X z, coalesced rows for X^T r).
 //
 // Along a sweep (Section 4.1): at step t the EM starts from the particle with the highest
 // posterior density and from the previous step's MAP, and keeps the mode with the higher
@@ -69,14 +69,21 @@ __device__ __forceinline__ double block_sum_d(double v, double* red)
     return r;
 }
 
-// eta = X z, one thread per individual (its row of X, z from shared memory)
+// eta = X z, one thread per individual: it walks column j of X^T log2(e) (consecutive
+// threads read consecutive individuals, so every load is coalesced; a row of X would put
+// each thread on its own cache line), z from shared memory, scaled back by ln 2
 __device__ void gemv_x(const MapData& d, const float* z, float* eta)
 {
     for (int64_t i = threadIdx.x; i < d.n; i += blockDim.x) {
-        const float* row = d.Xf + i * d.p;
-        float acc = 0.0f;
-        for (int j = 0; j < d.p; ++j) acc = fmaf(row[j], z[j], acc);
-        eta[i] = acc;
+        const float* col = d.XT2 + i;
+        float a0 = 0.0f, a1 = 0.0f;
+        int j = 0;
+        for (; j + 1 < d.p; j += 2) {
+            a0 = fmaf(col[(int64_t)j * d.n], z[j], a0);
+            a1 = fmaf(col[(int64_t)(j + 1) * d.n], z[j + 1], a1);
+        }
+        if (j < d.p) a0 = fmaf(col[(int64_t)j * d.n], z[j], a0);
+        eta[i] = (a0 + a1) * 0.69314718f;
     }
 }
 
