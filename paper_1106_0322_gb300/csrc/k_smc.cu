@@ -117,25 +117,40 @@ __device__ __forceinline__ FSum proposal_loglik(const MhState& s, int64_t i, int
     return L;
 }
 
+// log U of the MH test of move m for the block's particles (one warp per particle, so
+// blockDim.x / 32 of them), by the kernel that proposes move m: lanes 0.. of warp 0 draw
+// them side by side instead of lane 0 of every warp one at a time in the test.
+__device__ __forceinline__ void draw_accept_logu(const MhState& s, int64_t N, int t, uint32_t m, uint64_t seed)
+{
+    const int lane = threadIdx.x & 31;
+    if (!s.lu || threadIdx.x >= 32 || lane >= (int)(blockDim.x >> 5)) return;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + lane;
+    if (i >= N) return;
+    const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m), seed_key(seed));
+    s.lu[(int64_t)(m & 1u) * s.ld_lu + i] = logf(u01_open_f(u.x));
+}
+
 // Warp-cooperative MH test of particle i's pending proposal; `extra` is the MALA
-// q-correction. Lane 0 decides with the accept uniform of move m_prev and, on acceptance,
-// moves the proposal's log-likelihood and log-prior into the current state. Returns the
-// decision on every lane.
-__device__ __forceinline__ bool mh_decide(const MhState& s, int64_t i, int lane, float coef, float extra, int t,
-                                          uint32_t m_prev, uint64_t seed, uint32_t* err)
+// q-correction. Lane 0 decides with the accept uniform of move m_prev (drawn by the kernel
+// that proposed it) and, on acceptance, moves the proposal's log-likelihood and log-prior
+// into the current state. Returns the decision on every lane.
+__device__ __forceinline__ bool mh_decide(const MhState& s, int64_t i, int lane, float coef, float extra,
+                                          uint32_t m_prev, uint32_t* err)
 {
     const FSum L = proposal_loglik(s, i, lane);
     int accept = 0;
     if (lane == 0) {
         const float2 L0 = s.llq[i];
         const float2 Q1 = s.lpt_p[i], Q0 = s.lpq[i];
+        // written two launches back, by the kernel that proposed (read from L2)
+        const float lu = __ldcg(s.lu + (int64_t)(m_prev & 1u) * s.ld_lu + i);
         const float dL = (L.s - L0.x) + (L.c - L0.y);
         const float dQ = (Q1.x - Q0.x) + (Q1.y - Q0.y);
-        const float log_alpha = s.sp_scale * dL + coef * dQ + extra;
+        // rounded as written (no contraction), so that the decision does not depend on
+        // how the compiler schedules the surrounding code
+        const float log_alpha = __fadd_rn(__fadd_rn(__fmul_rn(s.sp_scale, dL), __fmul_rn(coef, dQ)), extra);
         if (!isfinite(L.s)) atomicOr(err, DERR_NONFINITE);
-        const uint4 u = philox4x32_10(make_uint4(0u, (uint32_t)i, (uint32_t)t, (TAG_ACCEPT << 16) | m_prev),
-                                      seed_key(seed));
-        accept = logf(u01_open_f(u.x)) < log_alpha;
+        accept = lu < log_alpha;
         if (accept) {
             s.llq[i] = make_float2(L.s, L.c);
             s.lpq[i] = Q1;
@@ -254,7 +269,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
     bool acc = false;
     if (i < N) {
         const uint64_t seed = (noise || DECIDE) ? *seedp : 0ull;
-        if (DECIDE) acc = mh_decide(a.mh, i, lane, sk.y, 0.0f, t, m_prev, seed, err);
+        if (DECIDE) acc = mh_decide(a.mh, i, lane, sk.y, 0.0f, m_prev, err);
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         float* dst = a.beta_p + i * p;
         float* cur = a.beta + i * p;
@@ -276,6 +291,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
             if (Arow) pack_offset(Arow, a.Kp, p, off);
         }
     }
+    if (noise) draw_accept_logu(a.mh, N, t, m, *seedp);
     if (DECIDE) {
         if (lane == 0) accw[threadIdx.x >> 5] = acc ? 1 : 0;
         count_warps(a.mh.acc_count, accw);
@@ -322,7 +338,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             bwd = warp_sum(bwd);
             const float2 fw = a.fwd[i];
             const float extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
-            acc = mh_decide(a.mh, i, lane, sk.y, extra, t, m_prev, seed, err);
+            acc = mh_decide(a.mh, i, lane, sk.y, extra, m_prev, err);
         }
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         const float* gsrc = (acc ? a.gl_p : a.gl) + i * p;
@@ -368,6 +384,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             if (Arow) pack_offset(Arow, a.Kp, p, off);
         }
     }
+    draw_accept_logu(a.mh, N, t, m, *seedp);
     if (DECIDE) {
         if (lane == 0) accw[threadIdx.x >> 5] = acc ? 1 : 0;
         count_warps(a.mh.acc_count, accw);
@@ -523,7 +540,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
             const float2 fw = a.fwd[i];
             extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
         }
-        acc = mh_decide(a.mh, i, lane, sk.y, extra, t, m_prev, *seedp, err);
+        acc = mh_decide(a.mh, i, lane, sk.y, extra, m_prev, err);
         if (acc) {
             const float* src = a.beta_p + i * p;
             float* dst = a.beta + i * p;

@@ -65,6 +65,7 @@ struct Workspace {
     uint32_t* wfix = nullptr;
     double *cum = nullptr, *lambda = nullptr, *lse_scratch = nullptr;
     uint32_t* keysT = nullptr;  // [p][N] order-preserving keys of beta for the summaries
+    float* lu = nullptr;        // [2][N_pad] log U of the pending proposals' MH tests
     float* WfS = nullptr;       // the weights the summaries of a step read, copied beside the keys
     uint32_t* wfixS = nullptr;
     unsigned int* lse_counter = nullptr;
@@ -233,7 +234,7 @@ void free_workspace(Workspace& w)
 {
     dfree(w.beta); dfree(w.beta_p); dfree(w.scale); dfree(w.A);
     dfree(w.lpt_p); dfree(w.ydq); dfree(w.llq); dfree(w.lpq); dfree(w.llq_tmp); dfree(w.lpq_tmp);
-    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.keysT); dfree(w.WfS); dfree(w.wfixS); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
+    dfree(w.ll); dfree(w.logw); dfree(w.W); dfree(w.Wf); dfree(w.wfix); dfree(w.cum); dfree(w.keysT); dfree(w.WfS); dfree(w.wfixS); dfree(w.lu); dfree(w.colpart); dfree(w.lambda); dfree(w.h);
     dfree(w.lse_scratch); dfree(w.lse_counter);
     dfree(w.partial); dfree(w.idx); dfree(w.flag); dfree(w.eta); dfree(w.grad);
     dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
@@ -356,6 +357,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     WA(ll, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
     WA(keysT, N * p);
     WA(WfS, N); WA(wfixS, N);
+    WA(lu, 2 * N_pad);
     WA(cum, N + nblk + 1);
     WA(colpart, (int64_t)COLSTAT_SPLITS * p);
     WA(lambda, 1);
@@ -531,6 +533,8 @@ MhState mh_state(spa_ctx* c, unsigned long long* acc)
     m.sp_scale_d = tc ? LN2 : 1.0;
     m.sp_scale = (float)m.sp_scale_d;
     m.acc_count = acc;
+    m.lu = w.lu;
+    m.ld_lu = w.N_pad;
     return m;
 }
 

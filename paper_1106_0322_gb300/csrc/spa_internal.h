@@ -81,6 +81,10 @@ struct MhState {
     float sp_scale;            // natural-log units per partial unit
     double sp_scale_d;         // the same in FP64 (for the log-weights)
     unsigned long long* acc_count;
+    // log of each pending proposal's accept uniform, [2][ld_lu]: the kernel that proposes
+    // move m writes row m & 1 for its block's particles, the MH test of move m reads it
+    float* lu;
+    int64_t ld_lu;
 };
 
 struct MoveArgs {
