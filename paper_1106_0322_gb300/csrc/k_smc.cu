@@ -1526,7 +1526,9 @@ cudaError_t launch_lse_ess(const WeightArrays& w, int64_t N, double* scratch, un
                                                       resampled_out, flag, err); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    { const cudaError_t e_ = launch_pdl(k_normalise, dim3(elem_grid(N)), dim3(256), (size_t)(0), st, w, N, scratch + 3 * blocks); if (e_ != cudaSuccess) return e_; }
+    // one FP64 exp per weight: blocks of 64 spread them over the SMs' FP64 units
+    const unsigned nb = (unsigned)std::min<int64_t>((N + 63) / 64, 8192);
+    { const cudaError_t e_ = launch_pdl(k_normalise, dim3(nb), dim3(64), (size_t)(0), st, w, N, scratch + 3 * blocks); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 
@@ -1591,7 +1593,8 @@ cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p
     { const cudaError_t e_ = launch_pdl(k_colstats_partial, dim3(grid), dim3(block), (size_t)(0), st, beta, Wf, N, p, part); if (e_ != cudaSuccess) return e_; }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    { const cudaError_t e_ = launch_pdl(k_colstats_finish, dim3((unsigned)((p + 7) / 8)), dim3(256), (size_t)(0), st, part, p, COLSTAT_SPLITS, scale_out, kind, lam_const,
+    // one warp (and block) per coordinate: its FP64 sums and square roots on their own SM
+    { const cudaError_t e_ = launch_pdl(k_colstats_finish, dim3((unsigned)p), dim3(32), (size_t)(0), st, part, p, COLSTAT_SPLITS, scale_out, kind, lam_const,
                                                                lam_dev, sd_floor, sched, t, h_out,
                                                                std::pow((double)p, -1.0 / 6.0)); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
