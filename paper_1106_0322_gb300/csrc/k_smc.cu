@@ -1518,12 +1518,19 @@ cudaError_t launch_reweight(const float* beta, double* logw, float2* lpq, int64_
 
 cudaError_t launch_lse_ess(const WeightArrays& w, int64_t N, double* scratch, unsigned int* counter, int t, int mode,
                            double ess_frac, double* ess_out, double* logz_out, uint8_t* resampled_out, int* flag,
-                           uint32_t* err, cudaStream_t st)
+                           uint32_t* err, cudaStream_t st, bool pdl)
 {
     int64_t blocks = (N + LSE_THREADS - 1) / LSE_THREADS;
     if (blocks > LSE_BLOCKS) blocks = LSE_BLOCKS;
-    { const cudaError_t e_ = launch_pdl(k_lse_partial, dim3((unsigned)blocks), dim3(LSE_THREADS), (size_t)(0), st, w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
-                                                      resampled_out, flag, err); if (e_ != cudaSuccess) return e_; }
+    if (pdl) {
+        const cudaError_t e_ = launch_pdl(k_lse_partial, dim3((unsigned)blocks), dim3(LSE_THREADS), (size_t)(0), st,
+                                          w.logw, N, scratch, counter, t, mode, ess_frac, ess_out, logz_out,
+                                          resampled_out, flag, err);
+        if (e_ != cudaSuccess) return e_;
+    } else {  // after a wait on another stream's event
+        k_lse_partial<<<(unsigned)blocks, LSE_THREADS, 0, st>>>(w.logw, N, scratch, counter, t, mode, ess_frac, ess_out,
+                                                               logz_out, resampled_out, flag, err);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // one FP64 exp per weight: blocks of 64 spread them over the SMs' FP64 units

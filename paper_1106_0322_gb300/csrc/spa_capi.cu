@@ -129,10 +129,11 @@ struct spa_ctx {
     PriorArgs pr{1.0f, 0};
     int device = 0, num_sms = 0;
     cudaStream_t own_stream = nullptr;
-    // the summaries of step t run on side_stream beside step t + 1 (fork after the key
-    // transpose, join before the next one)
+    // the key transpose and the summaries of step t run on side_stream beside step t + 1
+    // (fork after the step's moves; the next step waits for the transpose before it
+    // rewrites the weights, and the sweep's end joins the last summaries)
     cudaStream_t side_stream = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_keys = nullptr, ev_join = nullptr;
     spa_config cfg;
     std::string err;
     // genotype store
@@ -693,6 +694,8 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
     for (int64_t t = 0; t < T; ++t) {
         if (t > 0) {
             q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.rk, (int)t, c->d_err, q.st));
+            // the previous step's transpose has read beta and the weights (forked runs)
+            if (fork_sum && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_keys, 0);
             q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
                                 c->d_err, q.st));
             ++q.launches;
@@ -701,12 +704,14 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
         if (!site) enq_colstats(q, (int)t);
         enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
         if (fork_sum) {
-            // The summaries of step t run on the side stream beside step t + 1: the transpose
-            // snapshots the keys and the weights, and the next transpose waits for them.
-            if (t > 0 && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_join, 0);
-            q.ck(launch_keys(w.beta, w.Wf, w.wfix, w.N, p, w.keysT, w.WfS, w.wfixS, false, q.st));
+            // The key transpose and the summaries of step t run on the side stream beside step
+            // t + 1. The transpose reads beta and the weights, which step t + 1 first rewrites
+            // in its normalisation (it waits for ev_keys before); it copies the weights for the
+            // summaries, which then read nothing that the main stream writes.
             if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_fork, q.st);
             if (q.e == cudaSuccess) q.e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+            q.ck(launch_keys(w.beta, w.Wf, w.wfix, w.N, p, w.keysT, w.WfS, w.wfixS, false, c->side_stream));
+            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_keys, c->side_stream);
             q.ck(launch_summaries_keys(w.keysT, w.WfS, w.wfixS, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, false,
                                        c->side_stream));
             if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_join, c->side_stream);
@@ -776,6 +781,7 @@ void destroy(spa_ctx* c)
     dfree(c->l2e_s); dfree(c->mean_f); dfree(c->colf); dfree(c->Xf); dfree(c->Gbf); dfree(c->d_err); dfree(c->GT); dfree(c->yv);
     dfree(c->ybits); dfree(c->XT2); dfree(c->lip);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_keys) cudaEventDestroy(c->ev_keys);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side_stream) cudaStreamDestroy(c->side_stream);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -940,6 +946,7 @@ int spa_create(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double n
     cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_keys, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
 #define CA(ptr, cnt) \
     if (e == cudaSuccess) e = dalloc(&c->ptr, (size_t)(cnt))

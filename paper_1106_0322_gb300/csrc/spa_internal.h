@@ -164,7 +164,7 @@ constexpr int LSE_BLOCKS = 128;
 constexpr int LSE_SCRATCH = 3 * LSE_BLOCKS + 4;  // doubles
 cudaError_t launch_lse_ess(const WeightArrays& w, int64_t N, double* scratch, unsigned int* counter, int t, int mode,
                            double ess_frac, double* ess_out, double* logz_out, uint8_t* resampled_out, int* flag,
-                           uint32_t* err, cudaStream_t st);
+                           uint32_t* err, cudaStream_t st, bool pdl = true);
 // Wf and wfix from a given W (for the summaries entry point).
 cudaError_t launch_weight_forms(const double* W, int64_t N, float* Wf, uint32_t* wfix, cudaStream_t st);
 
