@@ -141,7 +141,10 @@ int spa_run(spa_ctx* ctx, const double* scale_schedule, int64_t T, int64_t N,
 
 /* As spa_run, but the schedule and every spa_result array are DEVICE pointers and the
  * call only enqueues the sweep on the configured stream (no host synchronisation).
- * Device-side errors are reported by the next spa_sync(). */
+ * Inside the sweep each step's summaries run on a second stream owned by the context and
+ * are joined back before the sweep's last kernel. Work enqueued on the configured stream
+ * after the call therefore sees the whole sweep, outputs included. Device-side errors are
+ * reported by the next spa_sync(). */
 int spa_run_device(spa_ctx* ctx, const double* scale_schedule_device, int64_t T, int64_t N,
                    int32_t moves_per_step, uint64_t seed, spa_result* out_device);
 
