@@ -293,11 +293,16 @@ int spa_resample_systematic(const double* W, int64_t N, double u, int32_t* idx_o
  * The kernel's scratch (N + ceil(N/256) + 1 doubles) is a fixed device array of
  * SPA_NOALLOC_RESAMPLE_MAX_N + 1025 doubles (about 2.1 MB), held by every GPU that loads
  * the library until the process exits. N > SPA_NOALLOC_RESAMPLE_MAX_N is rejected with
- * SPA_EINVAL (message in spa_last_error(NULL)). The first call on a device looks the
- * array's address up (cudaGetSymbolAddress) with that device current: make that first call
- * before any stream capture. All calls share the array: calls whose kernels overlap on
- * the GPU (different streams, no ordering between them) race and must be serialised by
- * the caller. Nothing needs to start at zero: each call writes every entry it reads. */
+ * SPA_EINVAL (message in spa_last_error(NULL)); a device that is not compute capability
+ * 10.x with SPA_EUNSUPPORTED; a failed CUDA call with SPA_ECUDA and CUDA's error string.
+ * The first call on a device looks the array's address up (cudaGetSymbolAddress) with that
+ * device current: make that first call before any stream capture. The address is kept per
+ * device together with the unique ID of the CUDA context it belongs to; after a
+ * cudaDeviceReset the next call sees a new context and looks the address up again (that
+ * call, too, must come before any capture). All calls share the array: calls whose kernels
+ * overlap on the GPU (different streams, no ordering between them) race and must be
+ * serialised by the caller. Nothing needs to start at zero: each call writes every entry it
+ * reads. */
 #define SPA_NOALLOC_RESAMPLE_MAX_N 262144
 int spa_resample_systematic_noalloc(const double* W_device, int64_t N, double u, int32_t* idx_device,
                                     void* stream);

@@ -422,9 +422,35 @@ def resample_systematic(W, u: float) -> np.ndarray:
 NOALLOC_RESAMPLE_MAX_N = 262144
 
 
+def check_noalloc_buffers(W_dev, idx_dev):
+    """Reject buffers the allocation-free resampling cannot take as they are: the kernel reads
+    N contiguous doubles at W_dev's address and writes N int32 at idx_dev's, so anything else
+    (another dtype, a strided view, host memory, two devices, a short index buffer) would give
+    wrong ancestors or write past the caller's buffer. Raises ValueError."""
+    import torch
+
+    if W_dev.dtype != torch.float64:
+        raise ValueError(f"W_dev must be float64, got {W_dev.dtype}")
+    if idx_dev.dtype != torch.int32:
+        raise ValueError(f"idx_dev must be int32, got {idx_dev.dtype}")
+    if not (W_dev.is_cuda and idx_dev.is_cuda):
+        raise ValueError("W_dev and idx_dev must be CUDA tensors")
+    if W_dev.device != idx_dev.device:
+        raise ValueError(f"W_dev and idx_dev are on different devices ({W_dev.device}, {idx_dev.device})")
+    if W_dev.device.index is not None and W_dev.device.index != torch.cuda.current_device():
+        raise ValueError(f"the buffers are on {W_dev.device}, the current device is {torch.cuda.current_device()}")
+    if not (W_dev.is_contiguous() and idx_dev.is_contiguous()):
+        raise ValueError("W_dev and idx_dev must be contiguous")
+    if idx_dev.numel() != W_dev.numel():
+        raise ValueError(f"idx_dev has {idx_dev.numel()} entries, W_dev {W_dev.numel()}: they must match")
+
+
 def resample_systematic_noalloc(W_dev, u: float, idx_dev, stream: int = 0):
     """Allocation-free systematic resampling on device buffers (torch tensors): W_dev float64,
-    idx_dev int32, both of length N <= NOALLOC_RESAMPLE_MAX_N. Enqueued on `stream`."""
+    idx_dev int32, both contiguous, on the current device and of the same length
+    N <= NOALLOC_RESAMPLE_MAX_N. Enqueued on `stream`, which must be ordered after whatever
+    wrote W_dev (the call does not synchronise)."""
+    check_noalloc_buffers(W_dev, idx_dev)
     _check(load().spa_resample_systematic_noalloc(_ptr(W_dev), W_dev.numel(), float(u), _ptr(idx_dev),
                                                   stream or None))
 

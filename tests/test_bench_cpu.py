@@ -80,3 +80,12 @@ def test_cli_parses_without_a_gpu():
     assert out.returncode == 0
     for flag in ("--gpus", "--steps", "--warmup", "--workload", "--impl"):
         assert flag in out.stdout
+
+
+def test_isolated_kernel_takes_the_burst_tensor_peak():
+    """The likelihood kernel is timed alone (a 200-launch burst at the unthrottled clock), so
+    its fraction divides by the burst BF16 peak, not the power-capped sustained one."""
+    peak, src = bench.tensor_peak_burst()
+    peaks, _ = bench.measured_peaks()
+    assert peak == peaks["bf16_tflops"]
+    assert "burst" in src

@@ -98,3 +98,50 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text and "spa_oracle" not in text, f
+
+
+class _FakeTensor:
+    """Just the attributes the allocation-free resampling's argument checks read."""
+
+    def __init__(self, dtype, is_cuda=True, device="cuda:0", contiguous=True, numel=16):
+        import torch
+
+        self.dtype = dtype
+        self.is_cuda = is_cuda
+        self.device = torch.device(device)
+        self._contiguous = contiguous
+        self._numel = numel
+
+    def is_contiguous(self):
+        return self._contiguous
+
+    def numel(self):
+        return self._numel
+
+
+def test_noalloc_resampling_rejects_unusable_buffers(monkeypatch):
+    import torch
+
+    import paper_1106_0322_gb300 as spa
+
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    f64, i32 = torch.float64, torch.int32
+    good_W, good_idx = _FakeTensor(f64), _FakeTensor(i32)
+    spa.check_noalloc_buffers(good_W, good_idx)  # accepted
+    cases = [
+        (_FakeTensor(torch.float32), good_idx, "float64"),
+        (good_W, _FakeTensor(torch.int64), "int32"),
+        (torch.zeros(16, dtype=f64), torch.zeros(16, dtype=i32), "CUDA"),
+        (good_W, _FakeTensor(i32, device="cuda:1"), "different devices"),
+        (_FakeTensor(f64, device="cuda:1"), _FakeTensor(i32, device="cuda:1"), "current device"),
+        (_FakeTensor(f64, contiguous=False), good_idx, "contiguous"),
+        (good_W, _FakeTensor(i32, contiguous=False), "contiguous"),
+        (good_W, _FakeTensor(i32, numel=15), "must match"),
+        (good_W, _FakeTensor(i32, numel=17), "must match"),
+    ]
+    for W, idx, what in cases:
+        with pytest.raises(ValueError, match=what):
+            spa.check_noalloc_buffers(W, idx)
+        # the public call rejects them before it reaches the library
+        with pytest.raises(ValueError, match=what):
+            spa.resample_systematic_noalloc(W, 0.5, idx)

@@ -33,6 +33,8 @@ def test_noalloc_resampling_matches_allocating_entry_point():
         ref = spa.resample_systematic(W, u)
         W_dev = torch.tensor(W, dtype=torch.float64, device="cuda")
         idx_dev = torch.full((N,), -1, dtype=torch.int32, device="cuda")
+        # the buffers were filled on torch's current stream; order the side stream after it
+        stream.wait_stream(torch.cuda.current_stream())
         spa.resample_systematic_noalloc(W_dev, u, idx_dev, stream.cuda_stream)
         stream.synchronize()
         assert np.array_equal(idx_dev.cpu().numpy(), ref), f"call {call}"
@@ -40,12 +42,14 @@ def test_noalloc_resampling_matches_allocating_entry_point():
     N = spa.NOALLOC_RESAMPLE_MAX_N
     W_dev = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
     idx_dev = torch.empty(N, dtype=torch.int32, device="cuda")
+    stream.wait_stream(torch.cuda.current_stream())
     spa.resample_systematic_noalloc(W_dev, 0.5, idx_dev, stream.cuda_stream)
     stream.synchronize()
     assert np.array_equal(idx_dev.cpu().numpy(), np.arange(N, dtype=np.int32))
     # one more than the fixed scratch holds: rejected with a clear error
     big = torch.zeros(N + 1, dtype=torch.float64, device="cuda")
     idx = torch.zeros(N + 1, dtype=torch.int32, device="cuda")
+    stream.wait_stream(torch.cuda.current_stream())
     with pytest.raises(spa.SpaError) as err:
         spa.resample_systematic_noalloc(big, 0.5, idx, stream.cuda_stream)
     assert err.value.code == spa.SPA_EINVAL
