@@ -188,6 +188,25 @@ void spa_batch_destroy(spa_batch* batch);
 /* Number of kernels the last spa_run / spa_run_device of this context launched. */
 int64_t spa_last_launch_count(const spa_ctx* ctx);
 
+/* Failure detection (the paper has no counterpart; the sweep must never hang the GPU).
+ * Every mbarrier wait in the context's tensor-core kernels (likelihood, adjoint) is bounded.
+ * When a wait runs out, the kernel sets an error bit, waits (at most 100 ms) for its own TMA
+ * copies and MMAs in flight, frees its TMEM and returns; later waits of the same sweep give
+ * up at once, the rest of the sweep runs on to its end, and the call that reads the error
+ * word (spa_run, spa_sync, spa_loglik, ...) returns SPA_ETIMEOUT. The context stays usable:
+ * the next sweep starts with a clear error word.
+ * spa_set_wait_limit sets that bound for later launches of this context (limit_ns = 0: the
+ * default, 4 s). A short limit lets a deployment fail fast and lets a test make a wait run
+ * out on purpose. It replaces the context's captured sweep graph. Errors: SPA_EINVAL for a
+ * NULL ctx.
+ * Host-side fault injection, for tests of the error paths: the environment variable
+ * SPA_FAULT, read at each call that can inject, holds a comma-separated list of
+ *   alloc       every device allocation by the library fails (the call returns SPA_ENOMEM)
+ *   nan_weight  the first log-weight of a sweep is set to NaN after the initial weighting
+ *               (SPA_ENUMERIC, from the device-side finiteness check of the log-sum-exp)
+ * Nothing is injected into a kernel. */
+int spa_set_wait_limit(spa_ctx* ctx, uint64_t limit_ns);
+
 /* Individuals per n-tile (128 or 256) of the tensor-core likelihood kernel for the
  * context's current workspace, or 0 before the first run. The library times both widths
  * once per shape (device, N, n, p) and keeps the faster; the environment variable

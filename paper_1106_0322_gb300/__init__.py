@@ -84,6 +84,7 @@ _SIGS = {
     "spa_batch_launch_count": (C.c_int64, [C.c_void_p]),
     "spa_batch_destroy": (None, [C.c_void_p]),
     "spa_last_launch_count": (C.c_int64, [C.c_void_p]),
+    "spa_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint64]),
     "spa_loglik_tile_width": (C.c_int, [C.c_void_p]),
     "spa_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                           C.c_void_p]),
@@ -258,6 +259,10 @@ class Region:
 
     def last_launch_count(self) -> int:
         return int(load().spa_last_launch_count(self._h))
+
+    def set_wait_limit(self, limit_ns: int = 0):
+        """Bound of the tensor-core kernels' device waits (spa_set_wait_limit; 0: 4 s)."""
+        _check(load().spa_set_wait_limit(self._h, C.c_uint64(int(limit_ns))), self._h)
 
     def map(self, beta0, c: float, max_em: int = 200, tol: float = 1e-5):
         """MAP by EM (Section 2.1) from each row of beta0 [S, p] at scale c: (modes [S, p],

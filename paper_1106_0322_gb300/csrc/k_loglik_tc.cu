@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
                 int64_t N_pad,
                 uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
-                int64_t n_r, float* __restrict__ rsum_part)
+                int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns)
 {
     using C = TcCfg<BN, STAGES, AR>;
     extern __shared__ uint8_t smem_raw[];
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 if (AR && mt != cur_mt) {
                     ++epoch;
                     // the previous epoch's MMAs must be done with the resident A
-                    if (epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((epoch - 1) & 1), err)) {
+                    if (epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((epoch - 1) & 1), err, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                         ++a_issued;
                     }
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                    if (!mbar_wait_bounded(EMPTY_BAR(s), ph ^ 1u, err)) {
+                    if (!mbar_wait_bounded(EMPTY_BAR(s), ph ^ 1u, err, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -297,11 +297,11 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
             for (uint32_t k = 1; k <= last; ++k) {
                 const uint32_t i2 = it - k;
-                mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
+                mbar_drain(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err);
             }
             if (AR && epoch >= 0)
                 for (int kb = 0; kb < a_issued; ++kb)
-                    mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err, 100000000ull);
+                    mbar_drain(AFULL_BAR(kb), (uint32_t)(epoch & 1), err);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             for (int64_t u = u_begin; u < u_end && ok; ++u, ++lt) {
                 const int mt = (int)(u / n_tiles);
                 const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
-                if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err)) {
+                if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err, wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -328,11 +328,11 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
                 for (int kb = 0; kb < kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                    if (AR && a_first && !mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err)) {
+                    if (AR && a_first && !mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err, wait_ns)) {
                         ok = false;
                         break;
                     }
-                    if (!mbar_wait_bounded(FULL_BAR(s), ph, err)) {
+                    if (!mbar_wait_bounded(FULL_BAR(s), ph, err, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             }
             // Wait for every MMA this thread issued before TMEM can be released.
             umma_commit(drain_bar);
-            mbar_wait_bounded(drain_bar, 0u, err, 100000000ull);
+            mbar_drain(drain_bar, 0u, err);
         }
     } else {
         // --------------------------------------------------------------- epilogue
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
         for (int64_t u = u_begin; u < u_end; ++u, ++lt) {
             const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
             const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
-            if (!mbar_wait_bounded(ACCF_BAR(b), aph, err)) break;
+            if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
             tc_fence_after();
             const int valid0 = n - nt * BN - col0;  // valid columns from col0 on
             const uint32_t tbase = tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)col0;
@@ -458,7 +458,7 @@ template <int BN2, int STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adjoint_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapGT, int m_tiles,
                  int p_tiles, int kblocks, int ksplit, int n_r, int p, float* __restrict__ gpart, int64_t N_pad,
-                 uint32_t* __restrict__ err)
+                 uint32_t* __restrict__ err, uint64_t wait_ns)
 {
     using C = AdjCfg<BN2, STAGES>;
     extern __shared__ uint8_t smem_raw[];
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             uint32_t it = 0;
             for (int kb = kb0; kb < kb1; ++kb) {
                 const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
-                if (!mbar_wait_bounded(EMPTY_BAR(q), ph ^ 1u, err)) break;
+                if (!mbar_wait_bounded(EMPTY_BAR(q), ph ^ 1u, err, wait_ns)) break;
                 const uint32_t st = sbase + q * C::STAGE;
                 mbar_arrive_expect_tx(FULL_BAR(q), (uint32_t)C::STAGE);
                 tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
@@ -516,7 +516,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
             for (uint32_t k = 1; k <= last; ++k) {
                 const uint32_t i2 = it - k;
-                mbar_wait_bounded(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err, 100000000ull);
+                mbar_drain(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err);
             }
         }
     } else if (warp == 1) {
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             bool ok = true;
             for (int kb = kb0; kb < kb1; ++kb) {
                 const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
-                if (!mbar_wait_bounded(FULL_BAR(q), ph, err)) {
+                if (!mbar_wait_bounded(FULL_BAR(q), ph, err, wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -543,13 +543,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             }
             if (ok) umma_commit(accf_bar);
             umma_commit(drain_bar);
-            mbar_wait_bounded(drain_bar, 0u, err, 100000000ull);
+            mbar_drain(drain_bar, 0u, err);
         }
     } else {
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         const int cols = (p - pt * BN2) < BN2 ? (p - pt * BN2) : BN2;
-        if (kb1 > kb0 && mbar_wait_bounded(accf_bar, 0u, err)) {
+        if (kb1 > kb0 && mbar_wait_bounded(accf_bar, 0u, err, wait_ns)) {
             tc_fence_after();
             float* out = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + row) * p + (int64_t)pt * BN2;
 #pragma unroll 1
@@ -641,7 +641,7 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
 template <int BN, int STAGES, bool RESID, bool AR>
 cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
-                      cudaStream_t st)
+                      uint64_t wait_ns, cudaStream_t st)
 {
     using C = TcCfg<BN, STAGES, AR>;
     // programmatic dependent launch: the prologue (barriers, TMEM, descriptor prefetch)
@@ -660,7 +660,7 @@ cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
     return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
                               plan.tw, plan.n_tiles, plan.m_tiles,
                               plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
-                              ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr);
+                              ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr, wait_ns);
 }
 
 }  // namespace
@@ -726,12 +726,13 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
 
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp,
                              const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
-                             const ResidArgs* ra)
+                             const ResidArgs* ra, uint64_t wait_ns)
 {
+    if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     // A stays resident when all its k-blocks fit (K <= 256)
     const bool ar = plan.kblocks <= KB_RES;
 #define TC_CASE(BN_, S_, R_, AR_) \
-    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, st)
+    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, st)
     if (ra) {
         if (plan.BN == 256) {
             if (ar) TC_CASE(256, 3, true, true);
@@ -778,15 +779,16 @@ bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n
 }
 
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p,
-                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st)
+                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns)
 {
+    if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     if (a.BN2 == ADJ_BN_SMALL) {
         k_adjoint_tc<ADJ_BN_SMALL, 3><<<a.grid, ADJ_THREADS, AdjCfg<ADJ_BN_SMALL, 3>::SMEM, st>>>(
-            mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit, (int)a.n_r, p, gpart, N_pad, err);
+            mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns);
     } else {
         k_adjoint_tc<256, 3><<<a.grid, ADJ_THREADS, AdjCfg<256, 3>::SMEM, st>>>(mapR, mapGT, a.m_tiles, a.p_tiles,
                                                                                a.kblocks, a.ksplit, (int)a.n_r, p, gpart,
-                                                                               N_pad, err);
+                                                                               N_pad, err, wait_ns);
     }
     return cudaGetLastError();
 }

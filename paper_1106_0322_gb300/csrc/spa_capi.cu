@@ -33,10 +33,37 @@ thread_local char g_thread_error[512] = {0};
 
 void set_thread_error_str(const std::string& m) { std::snprintf(g_thread_error, sizeof(g_thread_error), "%s", m.c_str()); }
 
+// Host-side fault injection for the failure-path tests: SPA_FAULT holds a comma-separated
+// list of faults, read at every call that can inject one.
+//   alloc       every device allocation of the library fails (SPA_ENOMEM)
+//   nan_weight  a sweep's first log-weight is set to NaN after the initial weighting
+//               (SPA_ENUMERIC from the device-side check of the log-sum-exp)
+// Nothing here touches a kernel: the GPU sees only ordinary data.
+enum : int { FAULT_ALLOC = 1, FAULT_NAN_WEIGHT = 2 };
+
+int fault_mask()
+{
+    const char* s = std::getenv("SPA_FAULT");
+    if (!s || !*s) return 0;
+    int m = 0;
+    std::string v(s);
+    size_t a = 0;
+    while (a <= v.size()) {
+        size_t b = v.find(',', a);
+        if (b == std::string::npos) b = v.size();
+        const std::string tok = v.substr(a, b - a);
+        if (tok == "alloc") m |= FAULT_ALLOC;
+        if (tok == "nan_weight") m |= FAULT_NAN_WEIGHT;
+        a = b + 1;
+    }
+    return m;
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
 {
     *p = nullptr;
+    if (fault_mask() & FAULT_ALLOC) return cudaErrorMemoryAllocation;
     if (count == 0) count = 1;
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
@@ -103,10 +130,12 @@ struct RunBufs {
 struct GraphKey {
     int64_t T = -1, N = -1;
     int32_t M = -1;
+    int fault = 0;  // injected faults captured into the graph
     spa_config cfg;
     bool operator==(const GraphKey& o) const
     {
-        return T == o.T && N == o.N && M == o.M && std::memcmp(&cfg, &o.cfg, sizeof(spa_config)) == 0;
+        return T == o.T && N == o.N && M == o.M && fault == o.fault &&
+               std::memcmp(&cfg, &o.cfg, sizeof(spa_config)) == 0;
     }
 };
 
@@ -167,6 +196,8 @@ struct spa_ctx {
     int map_rounds = 0;        // Jacobi rounds after round 0 of the last spa_map_path
     float* lip = nullptr;      // ||X||_2^2 / 4 for the MAP solver
     bool lip_ok = false;
+    uint64_t wait_ns = 0;      // limit of the tensor-core kernels' bounded waits (0: the default)
+    int fault = 0;             // faults injected into the current sweep graph (SPA_FAULT)
 
     cudaStream_t stream() const { return cfg.stream ? static_cast<cudaStream_t>(cfg.stream) : own_stream; }
 };
@@ -499,8 +530,9 @@ void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     const TcPlan plan = plan_of(c);
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     ResidArgs ra{w.R, a.n_r, w.rsum};
-    q.ck(launch_loglik_tc(maps_of(c), plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra));
-    q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st));
+    q.ck(launch_loglik_tc(maps_of(c), plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra,
+                          c->wait_ns));
+    q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st, c->wait_ns));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
                             c->pr, cs, out, q.st));
 }
@@ -511,7 +543,8 @@ void enq_loglik(Enq& q)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-        q.ck(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st));
+        q.ck(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st,
+                              nullptr, c->wait_ns));
     } else {
         q.ck(launch_loglik_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
     }
@@ -674,6 +707,7 @@ int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
         }
     }
     q.ck(launch_finish_loglik(a0.mh, w.N, w.logw, nullptr, c->d_err, q.st));
+    if (c->fault & FAULT_NAN_WEIGHT) q.ck(launch_set_f64(w.logw, std::nan(""), q.st));
     const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
     q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
                         c->d_err, q.st));
@@ -1024,6 +1058,14 @@ const char* spa_last_error(const spa_ctx* c)
 
 int64_t spa_last_launch_count(const spa_ctx* c) { return c ? c->last_launches : 0; }
 
+int spa_set_wait_limit(spa_ctx* c, uint64_t limit_ns)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (limit_ns != c->wait_ns) drop_graph(c);  // the limit is a kernel argument of the captured sweep
+    c->wait_ns = limit_ns;
+    return SPA_OK;
+}
+
 int spa_loglik_tile_width(const spa_ctx* c) { return (c && c->ws.N > 0) ? c->ws.BN : 0; }
 
 static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int64_t T, int64_t N, int32_t M,
@@ -1057,6 +1099,8 @@ static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int
     key.N = N;
     key.M = M;
     key.cfg = c->cfg;
+    key.fault = fault_mask() & FAULT_NAN_WEIGHT;
+    c->fault = key.fault;
     if (!c->gexec || !(key == c->gkey)) {
         drop_graph(c, false);  // buffers and config were settled above
         cudaGraph_t g = nullptr;
@@ -1238,7 +1282,8 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
     const MoveArgs a = move_args(c, nullptr);
     CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_k, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
     if (tc) {
-        CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+        CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st, nullptr,
+                            c->wait_ns),
            "loglik tc");
     } else {
         CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");
@@ -1257,7 +1302,8 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
     Workspace& w = c->ws;
     for (int32_t k = 0; k < reps; ++k) {
         if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-            CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st),
+            CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st, nullptr,
+                            c->wait_ns),
                "loglik tc");
         } else {
             CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");

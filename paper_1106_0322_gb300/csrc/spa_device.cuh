@@ -179,10 +179,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
+// The default limit of a bounded wait (a context can set another, spa_set_wait_limit).
+constexpr uint64_t WAIT_LIMIT_DEFAULT_NS = 4000000000ull;
+// The limit of a drain: the wait for a CTA's own copies and MMAs in flight before it frees
+// TMEM and exits.
+constexpr uint64_t DRAIN_LIMIT_NS = 100000000ull;
+
 // Wait until the phase with the given parity of barrier `bar` has completed. Gives up
 // after `limit_ns` (setting DERR_TIMEOUT) or as soon as another thread has given up.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t* err,
-                                                  uint64_t limit_ns = 4000000000ull)
+                                                  uint64_t limit_ns = WAIT_LIMIT_DEFAULT_NS)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
@@ -194,6 +200,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
                 atomicOr(err, DERR_TIMEOUT);
                 return false;
             }
+        }
+    }
+}
+
+// The drain before a CTA frees TMEM or exits: wait for this CTA's own asynchronous work
+// (TMA copies into its shared memory, its MMAs) to complete. Unlike mbar_wait_bounded it does
+// not stop when another thread has given up -- that is exactly when the work in flight must
+// still land -- and only its own limit (DRAIN_LIMIT_NS) ends it.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, uint32_t* err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t spin = 1;; ++spin) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spin & 63u) == 0u && globaltimer_ns() - t0 > DRAIN_LIMIT_NS) {
+            atomicOr(err, DERR_TIMEOUT);
+            return false;
         }
     }
 }

@@ -304,9 +304,10 @@ struct ResidArgs {
     float* rsum_part;        // same layout as the softplus partials
 };
 // ybits: y as a bitmask, one word per 32 individuals (ceil(n_tiles * BN / 32) words, zero beyond n).
+// wait_ns: the limit of each bounded mbarrier wait (0: the default, WAIT_LIMIT_DEFAULT_NS).
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp, const uint32_t* ybits,
                              float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
-                             const ResidArgs* resid = nullptr);
+                             const ResidArgs* resid = nullptr, uint64_t wait_ns = 0);
 
 // The adjoint's second half: C = R G (tcgen05, split-BF16 R, exact G^T [p][n_r]) into
 // gpart[ksplit][N_pad][p], then grad l = (sum C - m_j sum r) / s_j (+ prior gradient).
@@ -318,7 +319,7 @@ AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms);
 bool adj_make_map_R(CUtensorMap* map, const __nv_bfloat16* R, int64_t N_pad, int64_t n_r);
 bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n_r, int BN2);
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p, float* gpart,
-                              int64_t N_pad, uint32_t* err, cudaStream_t st);
+                              int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns = 0);
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
                                int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st);
