@@ -271,6 +271,16 @@ int spa_map(spa_ctx* ctx, const float* beta0, int32_t S, double c, int32_t max_e
 int spa_map_path(spa_ctx* ctx, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost);
 int spa_map_path_rounds(const spa_ctx* ctx);
 
+/* spa_map_path_given: the same MAP path rule and solver from caller-given starts instead of a
+ * recorded run: sched [T] the scales c_t > 0 (host), best [T][p] step t's best particle (host,
+ * FP32). At t = 0 the EM starts from best[0]; at each later t from best[t] and from the MAP
+ * kept at t - 1, and the mode with the higher log posterior is kept (a tie keeps the one from
+ * best[t]). Outputs as spa_map_path. It lets the path be checked against an independent walk
+ * of the rule from the same starts. Errors: SPA_EINVAL (NULL arguments, T < 1, a schedule
+ * value not finite and > 0, max_em < 1, tol <= 0, n + 5p too large), SPA_ENOMEM, SPA_ECUDA. */
+int spa_map_path_given(spa_ctx* ctx, const double* sched, const float* best, int64_t T, int32_t max_em, double tol,
+                       float* map_out, double* logpost);
+
 /* ------------------------------------------------------- per-step entry points */
 
 /* Log-likelihood l(beta) = sum_i [y_i eta_i - log(1 + exp(eta_i))], eta = X beta

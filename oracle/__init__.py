@@ -67,6 +67,7 @@ class OrResult(C.Structure):
         ("resampled", C.POINTER(C.c_uint8)),
         ("final_beta", C.POINTER(C.c_double)),
         ("final_logw", C.POINTER(C.c_double)),
+        ("best", C.POINTER(C.c_double)),
     ]
 
 
@@ -110,6 +111,10 @@ def _load():
         lib.or_map.argtypes = [P(C.c_int8), P(C.c_uint8), C.c_int64, C.c_int64, C.c_double, C.c_double, P(C.c_double),
                                C.c_int32, C.c_double, P(C.c_double), P(C.c_double)]
         lib.or_map.restype = C.c_int
+        lib.or_map_path.argtypes = [P(C.c_int8), P(C.c_uint8), C.c_int64, C.c_int64, C.c_double, P(C.c_double),
+                                    C.c_int64, P(C.c_double), C.c_int32, C.c_double, P(C.c_double), P(C.c_double),
+                                    P(C.c_uint8)]
+        lib.or_map_path.restype = C.c_int
         _lib = lib
         return lib
 
@@ -239,6 +244,28 @@ def map_em(G, y, a: float, c: float, beta0, max_em: int = 500, tol: float = 1e-1
     return out, lp.value
 
 
+def map_path(G, y, a: float, sched, best, max_em: int = 500, tol: float = 1e-10):
+    """The MAP path of Section 4.1 walked in step order from the per-step best particles
+    best [T, p]: (modes [T, p], log posteriors [T], chained [T] = 1 where EM from the
+    previous step's MAP was kept)."""
+    G = np.ascontiguousarray(G, dtype=np.int8)
+    y = np.ascontiguousarray(y, dtype=np.uint8)
+    sched = np.ascontiguousarray(sched, dtype=np.float64)
+    best = np.ascontiguousarray(best, dtype=np.float64)
+    n, p = G.shape
+    T = sched.size
+    if best.shape != (T, p):
+        raise ValueError("best must be T x p")
+    out = np.zeros((T, p))
+    lp = np.zeros(T)
+    ch = np.zeros(T, np.uint8)
+    if _load().or_map_path(_p(G, C.c_int8), _p(y, C.c_uint8), n, p, float(a), _p(sched, C.c_double), T,
+                           _p(best, C.c_double), int(max_em), float(tol), _p(out, C.c_double), _p(lp, C.c_double),
+                           _p(ch, C.c_uint8)) != 0:
+        raise ValueError("or_map_path: bad input")
+    return out, lp, ch
+
+
 def marginal(log_z_inc, mean, conc) -> dict:
     """Scale-marginalised summaries (Section 4, eq. all_particles) from a sweep's per-step
     outputs: log_z_inc [T], mean [T, p], conc [T, p, D]. Returns post_c [T] (the weights
@@ -281,7 +308,7 @@ def make_config(move: str = "rw", init: str = "prior_is", burn_in_steps: int = 0
 
 
 def run(G, y, a: float, sched, N: int, M: int, seed: int, cfg: OrConfig | None = None,
-        keep_particles: bool = False) -> dict:
+        keep_particles: bool = False, keep_best: bool = False) -> dict:
     """Run the SMC sweep of Section 4 and return the per-scale outputs as numpy arrays."""
     if cfg is None:
         cfg = make_config()
@@ -313,6 +340,9 @@ def run(G, y, a: float, sched, N: int, M: int, seed: int, cfg: OrConfig | None =
         out["final_logw"] = np.zeros(N)
         res.final_beta = _p(out["final_beta"], C.c_double)
         res.final_logw = _p(out["final_logw"], C.c_double)
+    if keep_best:
+        out["best"] = np.zeros((T, p))
+        res.best = _p(out["best"], C.c_double)
     rc = _load().or_run(_p(G, C.c_int8), _p(y, C.c_uint8), n, p, float(a), _p(sched, C.c_double), T, N, M,
                         C.c_uint64(seed), C.byref(cfg), C.byref(res))
     if rc != 0:

@@ -28,6 +28,12 @@
  *   or_map                pinned: the double-exponential case against scikit-learn's L1
  *                         logistic regression; the EM fixed point's optimality (KKT)
  *                         conditions; monotone increase of the EM objective
+ *   or_map_path           pinned: for the double exponential (a unique mode) every step's
+ *                         MAP is scikit-learn's L1 logistic regression at c_t; for one
+ *                         marker with a spike and a slab mode, the kept mode is the global
+ *                         maximum of the log posterior on a fine grid at every c_t
+ *   or_run's best output  pinned: the recorded particle has the largest l + log p of the
+ *                         final particles of a one-step run (brute force)
  *   or_marginal           pinned: equal evidence gives the plain average, one dominant
  *                         step gives its summary, shift invariance of log Z, and the
  *                         p <= 2 quadrature of the scale-marginalised posterior
@@ -435,6 +441,9 @@ typedef struct {
     uint8_t* resampled;     /* [T] */
     double* final_beta;     /* [N * p], may be NULL */
     double* final_logw;     /* [N], may be NULL */
+    double* best;           /* [T * p], may be NULL: after the moves of step t, the particle of
+                               highest posterior density l + log p(. | a, c_t) (ties: the
+                               lowest index), the start of Section 4.1's MAP tracking */
 } or_result;
 
 typedef struct {
@@ -789,6 +798,12 @@ int or_run(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, co
         if (r->accept_rate) r->accept_rate[t] = rate;
         if (cfg->move_kind == 1 && M > 0) lam *= exp(rate - 0.574);
         or_summaries(&s, W, cfg, t, r);
+        if (r->best) {
+            int64_t k = 0;
+            for (int64_t i = 1; i < N; ++i)
+                if (s.ll[i] + s.lp[i] > s.ll[k] + s.lp[k]) k = i;
+            memcpy(r->best + t * p, s.beta + k * p, sizeof(double) * (size_t)p);
+        }
     }
     if (r->final_beta) memcpy(r->final_beta, s.beta, sizeof(double) * (size_t)(N * p));
     if (r->final_logw) memcpy(r->final_logw, logw, sizeof(double) * (size_t)N);
@@ -904,6 +919,43 @@ int or_map(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, do
     if (logpost) *logpost = or_loglik_x(X, y, n, p, b, NULL) + or_logprior(a, c, b, p);
     free(X); free(eta); free(w); free(L); free(prev);
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* The MAP path along a sweep (Section 4.1): at every step t the EM of Section   */
+/* 2.1 is started from the step's particle of highest posterior density and,    */
+/* for t > 0, from the previous step's MAP; the mode with the higher log        */
+/* posterior is kept (on a tie, the one from the best particle). This walks the  */
+/* steps in order:                                                               */
+/*   A_t = EM(c_t, best_t),  S_0 = A_0,                                          */
+/*   S_t = EM(c_t, S_{t-1}) if its log posterior exceeds A_t's, else A_t.        */
+/* best: [T * p] starts; map_out [T * p] the kept modes, logpost [T] their       */
+/* log l + log p, chained [T] (may be NULL) 1 where EM from S_{t-1} was kept.    */
+/* ------------------------------------------------------------------------- */
+int or_map_path(const int8_t* G, const uint8_t* y, int64_t n, int64_t p, double a, const double* sched, int64_t T,
+                const double* best, int32_t max_em, double tol, double* map_out, double* logpost, uint8_t* chained)
+{
+    if (T < 1) return -1;
+    double* B = (double*)malloc(sizeof(double) * (size_t)p);
+    if (!B) return -1;
+    int rc = 0;
+    for (int64_t t = 0; t < T && rc == 0; ++t) {
+        double* S = map_out + t * p;
+        double lpA = 0.0, lpB = 0.0;
+        rc = or_map(G, y, n, p, a, sched[t], best + t * p, max_em, tol, S, &lpA);
+        if (rc != 0) break;
+        logpost[t] = lpA;
+        if (chained) chained[t] = 0;
+        if (t == 0) continue;
+        rc = or_map(G, y, n, p, a, sched[t], map_out + (t - 1) * p, max_em, tol, B, &lpB);
+        if (rc == 0 && lpB > lpA) {
+            memcpy(S, B, sizeof(double) * (size_t)p);
+            logpost[t] = lpB;
+            if (chained) chained[t] = 1;
+        }
+    }
+    free(B);
+    return rc;
 }
 
 int or_max_threads(void)

@@ -90,6 +90,8 @@ _SIGS = {
                           C.c_void_p]),
     "spa_map_path": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
     "spa_map_path_rounds": (C.c_int, [C.c_void_p]),
+    "spa_map_path_given": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
+                                     C.c_void_p]),
     "spa_loglik_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "spa_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_loglik_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
@@ -280,6 +282,20 @@ class Region:
         out = np.zeros((T, self.p), np.float32)
         lp = np.zeros(T)
         _check(load().spa_map_path(self._h, int(T), int(max_em), float(tol), _ptr(out), _ptr(lp)), self._h)
+        return out, lp
+
+    def map_path_given(self, schedule, best, max_em: int = 200, tol: float = 1e-5):
+        """The MAP path rule (Section 4.1) from given per-step starts best [T, p]: (map [T, p],
+        log posteriors [T])."""
+        sched = np.ascontiguousarray(schedule, dtype=np.float64)
+        b = np.ascontiguousarray(best, dtype=np.float32)
+        T = sched.size
+        if b.shape != (T, self.p):
+            raise ValueError("best must be T x p")
+        out = np.zeros((T, self.p), np.float32)
+        lp = np.zeros(T)
+        _check(load().spa_map_path_given(self._h, _ptr(sched), _ptr(b), T, int(max_em), float(tol), _ptr(out),
+                                         _ptr(lp)), self._h)
         return out, lp
 
     def map_path_rounds(self) -> int:

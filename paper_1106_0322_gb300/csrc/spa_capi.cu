@@ -1354,13 +1354,10 @@ int spa_map(spa_ctx* c, const float* beta0, int32_t S, double cs, int32_t max_em
     return read_error_word(c);
 }
 
-int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost)
+// The MAP path rounds from device arrays of starts best [T][p] and scales sched [T].
+static int map_path_impl(spa_ctx* c, const float* best, const double* sched, int64_t T, int32_t max_em, double tol,
+                         float* map_out, double* logpost)
 {
-    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
-    if (!map_out || T < 1 || max_em < 1 || !(tol > 0.0)) return fail(c, SPA_EINVAL, "bad arguments");
-    if (c->best_T != T || c->rb.T != T || !c->rb.best)
-        return fail(c, SPA_EINVAL, "no recorded run of T steps with config.map_path set");
-    if (!map_fits(c->n, (int)c->p)) return fail(c, SPA_EINVAL, "n + 5p too large for the MAP solver's shared memory");
     cudaStream_t st = c->stream();
     int rc = ensure_lipschitz(c, st);
     if (rc != SPA_OK) return rc;
@@ -1375,12 +1372,11 @@ int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_o
     // Round k leaves the first k + 1 steps final, so at most T rounds after round 0 change
     // anything; the loop ends at the first round that changes nothing.
     int last = 0;  // the last round launched; its copy holds the result
-    if (e == cudaSuccess) e = launch_map_round(map_data(c), c->rb.best, c->rb.sched, (int)T, 0, max_em, (float)tol, b, st);
+    if (e == cudaSuccess) e = launch_map_round(map_data(c), best, sched, (int)T, 0, max_em, (float)tol, b, st);
     for (int round = 1; e == cudaSuccess && round <= T; ++round) {
         int changed = 0;
         e = cudaMemsetAsync(b.n_changed, 0, sizeof(int), st);
-        if (e == cudaSuccess)
-            e = launch_map_round(map_data(c), c->rb.best, c->rb.sched, (int)T, round, max_em, (float)tol, b, st);
+        if (e == cudaSuccess) e = launch_map_round(map_data(c), best, sched, (int)T, round, max_em, (float)tol, b, st);
         if (e == cudaSuccess) last = round;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&changed, b.n_changed, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1401,6 +1397,41 @@ int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_o
     dfree(b.n_changed);
     if (e != cudaSuccess) return cuda_fail(c, e, "MAP path");
     return read_error_word(c);
+}
+
+int spa_map_path(spa_ctx* c, int64_t T, int32_t max_em, double tol, float* map_out, double* logpost)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!map_out || T < 1 || max_em < 1 || !(tol > 0.0)) return fail(c, SPA_EINVAL, "bad arguments");
+    if (c->best_T != T || c->rb.T != T || !c->rb.best)
+        return fail(c, SPA_EINVAL, "no recorded run of T steps with config.map_path set");
+    if (!map_fits(c->n, (int)c->p)) return fail(c, SPA_EINVAL, "n + 5p too large for the MAP solver's shared memory");
+    return map_path_impl(c, c->rb.best, c->rb.sched, T, max_em, tol, map_out, logpost);
+}
+
+int spa_map_path_given(spa_ctx* c, const double* sched, const float* best, int64_t T, int32_t max_em, double tol,
+                       float* map_out, double* logpost)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (!sched || !best || !map_out || T < 1 || T > (int64_t)1 << 24 || max_em < 1 || !(tol > 0.0))
+        return fail(c, SPA_EINVAL, "bad arguments");
+    for (int64_t t = 0; t < T; ++t)
+        if (!(sched[t] > 0.0) || !std::isfinite(sched[t])) return fail(c, SPA_EINVAL, "schedule values must be finite and > 0");
+    if (!map_fits(c->n, (int)c->p)) return fail(c, SPA_EINVAL, "n + 5p too large for the MAP solver's shared memory");
+    const int64_t p = c->p;
+    cudaStream_t st = c->stream();
+    double* d_sched = nullptr;
+    float* d_best = nullptr;
+    cudaError_t e = dalloc(&d_sched, (size_t)T);
+    if (e == cudaSuccess) e = dalloc(&d_best, (size_t)(T * p));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_sched, sched, sizeof(double) * (size_t)T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_best, best, sizeof(float) * (size_t)(T * p), cudaMemcpyHostToDevice, st);
+    int rc = e == cudaSuccess ? map_path_impl(c, d_best, d_sched, T, max_em, tol, map_out, logpost)
+                              : cuda_fail(c, e, "MAP path inputs");
+    cudaStreamSynchronize(st);
+    dfree(d_sched);
+    dfree(d_best);
+    return rc;
 }
 
 int spa_map_path_rounds(const spa_ctx* c) { return c ? c->map_rounds : -1; }

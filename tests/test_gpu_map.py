@@ -109,3 +109,32 @@ def test_map_path_needs_a_recorded_run(spa):
         r.run(synth.geometric_schedule(3), 64, 1, 1)
         with pytest.raises(spa.SpaError):
             r.map_path(3)
+
+
+@pytest.mark.parametrize("seed", [44, 45])
+def test_map_path_matches_the_oracle_walk_from_the_same_starts(spa, seed):
+    """Section 4.1's rule, GPU (parallel rounds) against the oracle (the steps walked in
+    order), from the same starts: the oracle's own sweep records each step's best particle
+    (rounded to FP32, the form the GPU takes), and both sides run the path from those. The
+    kept modes and their log posteriors must agree at every step, and the chained start must
+    win with a mode of its own at some steps, so the comparison exercises the rule."""
+    a = 1.0
+    reg = synth.make_region(300, 12, 0.9, (0.6, -0.5), seed=seed)
+    T = 20
+    sched = synth.paper_schedule(1.0, T, a, ratio=0.8)  # diffuse to sparse, as in the paper
+    out = oracle.run(reg.G, reg.y, a, sched, 512, 2, seed=8, cfg=oracle.make_config(init="mcmc", burn_in_steps=3),
+                     keep_best=True)
+    best = out["best"].astype(np.float32)
+    om, olp, och = oracle.map_path(reg.G, reg.y, a, sched, best.astype(np.float64), max_em=300, tol=1e-8)
+    with spa.Region(reg.G, reg.y, a) as r:
+        gm, glp = r.map_path_given(sched, best, max_em=300, tol=1e-6)
+        assert 1 <= r.map_path_rounds() <= T
+    own_mode = 0
+    for t in range(T):
+        scale = max(1.0, np.max(np.abs(om[t])))
+        assert np.max(np.abs(gm[t] - om[t])) < 2e-3 * scale, t
+        assert abs(glp[t] - olp[t]) < 1e-5 * abs(olp[t]) + 1e-4, t
+        A, _ = oracle.map_em(reg.G, reg.y, a, float(sched[t]), best[t].astype(np.float64), max_em=300, tol=1e-8)
+        if och[t] and np.max(np.abs(A - om[t])) > 1e-3:
+            own_mode += 1
+    assert own_mode >= 2
