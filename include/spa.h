@@ -196,15 +196,19 @@ int64_t spa_last_launch_count(const spa_ctx* ctx);
  * word (spa_run, spa_sync, spa_loglik, ...) returns SPA_ETIMEOUT. The context stays usable:
  * the next sweep starts with a clear error word.
  * spa_set_wait_limit sets that bound for later launches of this context (limit_ns = 0: the
- * default, 4 s). A short limit lets a deployment fail fast and lets a test make a wait run
- * out on purpose. It replaces the context's captured sweep graph. Errors: SPA_EINVAL for a
- * NULL ctx.
+ * default, 4 s). A short limit lets a deployment fail fast on a wait that cannot complete.
+ * It replaces the context's captured sweep graph. Errors: SPA_EINVAL for a NULL ctx.
  * Host-side fault injection, for tests of the error paths: the environment variable
  * SPA_FAULT, read at each call that can inject, holds a comma-separated list of
  *   alloc       every device allocation by the library fails (the call returns SPA_ENOMEM)
  *   nan_weight  the first log-weight of a sweep is set to NaN after the initial weighting
  *               (SPA_ENUMERIC, from the device-side finiteness check of the log-sum-exp)
- * Nothing is injected into a kernel. */
+ *   stall       each tensor-core likelihood launch first waits on a barrier that nothing
+ *               arrives at, so that wait runs out after the wait limit (set a short one
+ *               with spa_set_wait_limit first) and the call returns SPA_ETIMEOUT
+ * A wait that runs out is the only way the timeout path is reached: mbarrier waits that
+ * will complete suspend the thread until they do, so a short limit alone does not end them.
+ * None of these faults, traps or hangs the GPU. */
 int spa_set_wait_limit(spa_ctx* ctx, uint64_t limit_ns);
 
 /* Individuals per n-tile (128 or 256) of the tensor-core likelihood kernel for the

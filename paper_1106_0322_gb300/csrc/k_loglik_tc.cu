@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
                 int64_t N_pad,
                 uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
-                int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns)
+                int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns, int stall)
 {
     using C = TcCfg<BN, STAGES, AR>;
     extern __shared__ uint8_t smem_raw[];
@@ -311,6 +311,11 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             int lt = 0;
             bool ok = true;
             int epoch = -1, cur_mt = -1;
+            // Injected stall (tests of the timeout path): wait first on the drain barrier,
+            // which nothing arrives at before this thread's own final commit, so the wait
+            // runs out after wait_ns; no MMA has been issued, and the other roles give up and
+            // drain as after any timeout.
+            if (stall && !mbar_wait_bounded(drain_bar, 0u, err, wait_ns)) ok = false;
             for (int64_t u = u_begin; u < u_end && ok; ++u, ++lt) {
                 const int mt = (int)(u / n_tiles);
                 const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
@@ -641,7 +646,7 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
 template <int BN, int STAGES, bool RESID, bool AR>
 cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
-                      uint64_t wait_ns, cudaStream_t st)
+                      uint64_t wait_ns, int stall, cudaStream_t st)
 {
     using C = TcCfg<BN, STAGES, AR>;
     // programmatic dependent launch: the prologue (barriers, TMEM, descriptor prefetch)
@@ -660,7 +665,7 @@ cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
     return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
                               plan.tw, plan.n_tiles, plan.m_tiles,
                               plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
-                              ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr, wait_ns);
+                              ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr, wait_ns, stall);
 }
 
 }  // namespace
@@ -726,13 +731,13 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
 
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp,
                              const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
-                             const ResidArgs* ra, uint64_t wait_ns)
+                             const ResidArgs* ra, uint64_t wait_ns, int stall)
 {
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     // A stays resident when all its k-blocks fit (K <= 256)
     const bool ar = plan.kblocks <= KB_RES;
 #define TC_CASE(BN_, S_, R_, AR_) \
-    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, st)
+    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, stall, st)
     if (ra) {
         if (plan.BN == 256) {
             if (ar) TC_CASE(256, 3, true, true);

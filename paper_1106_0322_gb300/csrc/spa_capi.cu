@@ -38,8 +38,11 @@ void set_thread_error_str(const std::string& m) { std::snprintf(g_thread_error, 
 //   alloc       every device allocation of the library fails (SPA_ENOMEM)
 //   nan_weight  a sweep's first log-weight is set to NaN after the initial weighting
 //               (SPA_ENUMERIC from the device-side check of the log-sum-exp)
-// Nothing here touches a kernel: the GPU sees only ordinary data.
-enum : int { FAULT_ALLOC = 1, FAULT_NAN_WEIGHT = 2 };
+//   stall       every tensor-core likelihood launch first waits on a barrier that nothing
+//               arrives at, so that bounded wait runs out after the context's wait limit
+//               (SPA_ETIMEOUT); the kernel then drains its own copies and returns
+// None of these faults, traps or hangs the GPU.
+enum : int { FAULT_ALLOC = 1, FAULT_NAN_WEIGHT = 2, FAULT_STALL = 4 };
 
 int fault_mask()
 {
@@ -54,6 +57,7 @@ int fault_mask()
         const std::string tok = v.substr(a, b - a);
         if (tok == "alloc") m |= FAULT_ALLOC;
         if (tok == "nan_weight") m |= FAULT_NAN_WEIGHT;
+        if (tok == "stall") m |= FAULT_STALL;
         a = b + 1;
     }
     return m;
@@ -531,7 +535,7 @@ void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     ResidArgs ra{w.R, a.n_r, w.rsum};
     q.ck(launch_loglik_tc(maps_of(c), plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra,
-                          c->wait_ns));
+                          c->wait_ns, c->fault & FAULT_STALL));
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st, c->wait_ns));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
                             c->pr, cs, out, q.st));
@@ -544,7 +548,7 @@ void enq_loglik(Enq& q)
     Workspace& w = c->ws;
     if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
         q.ck(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st,
-                              nullptr, c->wait_ns));
+                              nullptr, c->wait_ns, c->fault & FAULT_STALL));
     } else {
         q.ck(launch_loglik_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.partial, w.N_pad, q.st));
     }
@@ -1099,7 +1103,7 @@ static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int
     key.N = N;
     key.M = M;
     key.cfg = c->cfg;
-    key.fault = fault_mask() & FAULT_NAN_WEIGHT;
+    key.fault = fault_mask() & (FAULT_NAN_WEIGHT | FAULT_STALL);
     c->fault = key.fault;
     if (!c->gexec || !(key == c->gkey)) {
         drop_graph(c, false);  // buffers and config were settled above
@@ -1283,7 +1287,7 @@ static int loglik_impl(spa_ctx* c, const float* B, bool B_dev, int64_t N, double
     CK(launch_move_rw(a, false, N, (int)p, c->pr, c->unit_k, 0, 0u, 0u, nullptr, 0, c->d_err, st), "pack");
     if (tc) {
         CK(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, st, nullptr,
-                            c->wait_ns),
+                            c->wait_ns, fault_mask() & FAULT_STALL),
            "loglik tc");
     } else {
         CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)p, w.partial, w.N_pad, st), "loglik simt");

@@ -305,9 +305,11 @@ struct ResidArgs {
 };
 // ybits: y as a bitmask, one word per 32 individuals (ceil(n_tiles * BN / 32) words, zero beyond n).
 // wait_ns: the limit of each bounded mbarrier wait (0: the default, WAIT_LIMIT_DEFAULT_NS).
+// stall != 0 (injected, for tests of the timeout path): the MMA issuer first waits on a
+// barrier that nothing arrives at, so that wait runs out and the kernel returns early.
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp, const uint32_t* ybits,
                              float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
-                             const ResidArgs* resid = nullptr, uint64_t wait_ns = 0);
+                             const ResidArgs* resid = nullptr, uint64_t wait_ns = 0, int stall = 0);
 
 // The adjoint's second half: C = R G (tcgen05, split-BF16 R, exact G^T [p][n_r]) into
 // gpart[ksplit][N_pad][p], then grad l = (sum C - m_j sum r) / s_j (+ prior gradient).

@@ -1,10 +1,11 @@
 """Failure detection through the C ABI, with no GPU fault (none of these traps, hangs or
 faults the device).
 
-- A bounded device wait that runs out: the context's wait limit is set to 1 ns, so the
-  tensor-core kernels' first mbarrier waits give up. The kernels drain their own copies and
-  MMAs, free TMEM and return; the sweep reports SPA_ETIMEOUT. With the default limit back,
-  the same context reproduces a clean sweep bit for bit.
+- A bounded device wait that runs out: with SPA_FAULT=stall the likelihood kernel's MMA
+  issuer waits on a barrier that nothing arrives at, under a 1 ms limit. The wait runs out,
+  the kernel's other roles give up, drain their own copies, free TMEM and return, and the
+  sweep reports SPA_ETIMEOUT. Without the stall the same context reproduces a clean sweep bit
+  for bit, under the short limit and the default one.
 - Host-side injection (SPA_FAULT): failed device allocations give SPA_ENOMEM, a NaN log-weight
   gives SPA_ENUMERIC; a NaN particle handed to the log-likelihood gives SPA_ENUMERIC; bad
   schedules and sizes give SPA_EINVAL. After each, the context runs a clean sweep again.
@@ -41,22 +42,25 @@ SCHED = np.exp(np.linspace(-5.0, 0.0, 5))
 
 
 @pytest.mark.parametrize("move", ["rw", "mala"])
-def test_a_wait_that_runs_out_reports_etimeout_and_the_context_recovers(spa, region, move):
+def test_a_wait_that_runs_out_reports_etimeout_and_the_context_recovers(spa, region, move, monkeypatch):
     cfg = spa.make_config(move=move)
     with spa.Region(region.G, region.y, 1.0, config=cfg) as r:
         ref = r.run(SCHED, 512, 2, seed=5)
-        r.set_wait_limit(1)  # 1 ns: the first wait that does not succeed at once gives up
+        r.set_wait_limit(1_000_000)  # 1 ms
+        monkeypatch.setenv("SPA_FAULT", "stall")
         with pytest.raises(spa.SpaError) as err:
             r.run(SCHED, 512, 2, seed=5)
         assert err.value.code == spa.SPA_ETIMEOUT
         assert "bounded device wait" in str(err.value)
-        # the per-step entry points see the same limit
+        # the per-step entry points report it the same way
         with pytest.raises(spa.SpaError) as err:
             r.loglik(np.zeros((256, region.G.shape[1]), np.float32))
         assert err.value.code == spa.SPA_ETIMEOUT
+        monkeypatch.delenv("SPA_FAULT")
+        # with nothing stalled, the short limit does not end waits that complete
+        _same(ref, r.run(SCHED, 512, 2, seed=5))
         r.set_wait_limit(0)  # back to the default
-        again = r.run(SCHED, 512, 2, seed=5)
-        _same(ref, again)
+        _same(ref, r.run(SCHED, 512, 2, seed=5))
         ll = r.loglik(np.zeros((256, region.G.shape[1]), np.float32))
         assert np.allclose(ll, -region.G.shape[0] * np.log(2.0), rtol=1e-6)
 

@@ -294,7 +294,10 @@ def grad_split_bound(G, B):
     return acc / s[None, :] + (e_eta / 4 + 2.0 ** -20) @ np.abs(X)
 
 
-@pytest.mark.parametrize("n,p,N", [(7, 3, 5), (300, 37, 70), (600, 130, 300), (2000, 200, 256), (1000, 300, 129)])
+# The last three are the batched workload's extreme region shapes (n up to 5000, p from 20 to
+# 500) at its N = 4096 particles, so the adjoint runs with the K-split those sweeps use.
+@pytest.mark.parametrize("n,p,N", [(7, 3, 5), (300, 37, 70), (600, 130, 300), (2000, 200, 256), (1000, 300, 129),
+                                   (5000, 500, 4096), (5000, 20, 4096), (1000, 500, 4096)])
 def test_gradient_tensor_core_bound(spa, n, p, N):
     reg = synth.make_region(n, p, 0.9, (0.5, -0.4), seed=n + 3 * p)
     B = synth.random_particles(N, p, 0.2, seed=N + 1)
