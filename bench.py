@@ -239,7 +239,7 @@ METRIC_BATCHED = ("batched SPA sweeps: particle-loglik throughput over all regio
 BATCHED = dict(R=64, N=4096, T=100, M=5, move="mala", seed=1004)
 
 
-def batched_bench(args):
+def batched_bench(args, emit=True):
     """The batched workload: 64 uneven regions (n ~ U[1000, 5000], p ~ U[20, 500]), each its
     own MALA sweep (N = 4096, T = 100, M = 5, split-BF16), all captured into one CUDA graph
     (spa_batch) and launched once per step. Timed on the host around spa_batch_run, which
@@ -248,8 +248,9 @@ def batched_bench(args):
     import torch
 
     rank, world, _ = _rank_env()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    if emit:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     import __graft_entry__
 
     __graft_entry__.build()
@@ -300,11 +301,18 @@ def batched_bench(args):
         "sequential_regions_ms": seq_ms,
         "speedup_vs_sequential": seq_ms / ms,
         "clocks": clocks,
+        "roofline": {"bound": "tensor", "achieved": 2 * 1e9 * gmac / (ms / 1e3) / 1e12,
+                     "peak": tensor_peak_burst()[0], "unit": "TFLOP/s",
+                     "frac": 2 * 1e9 * gmac / (ms / 1e3) / 1e12 / tensor_peak_burst()[0], "traffic": None,
+                     "kernel": "whole batch (all regions' likelihood and adjoint contractions over the batch time)",
+                     "peak_source": tensor_peak_burst()[1]},
     }
-    print(json.dumps(line), flush=True)
     batch.close()
     for g in regs:
         g.close()
+    if not emit:
+        return line
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -454,6 +462,161 @@ def matched_error(args):
     return 0
 
 
+def out_buffers(dev, T, p):
+    """Device-resident per-scale outputs of one sweep (the spa_result arrays)."""
+    import torch
+
+    return {
+        "mean": torch.empty((T, p), dtype=torch.float64, device=dev),
+        "quantile": torch.empty((T, p, 3), dtype=torch.float64, device=dev),
+        "conc": torch.empty((T, p, 2), dtype=torch.float64, device=dev),
+        "ess": torch.empty(T, dtype=torch.float64, device=dev),
+        "log_z_inc": torch.empty(T, dtype=torch.float64, device=dev),
+        "accept_rate": torch.empty(T, dtype=torch.float64, device=dev),
+        "resampled": torch.empty(T, dtype=torch.uint8, device=dev),
+    }
+
+
+def time_sweeps(reg, sched_d, w, steps, warmup, stream, flush, out_d, seed0):
+    """Device time (CUDA events on the sweep's stream) of `steps` sweeps after `warmup`
+    untimed ones, with L2 flushed before each timed sweep (outside the events)."""
+    import torch
+
+    for k in range(warmup):
+        reg.run_device(sched_d, w["N"], w["M"], seed0 + k, out_d)
+    reg.sync()
+    torch.cuda.synchronize()
+    times = []
+    for k in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reg.run_device(sched_d, w["N"], w["M"], seed0 + warmup + k, out_d)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    reg.sync()
+    return times
+
+
+def grad_roofline(reg, w, stream):
+    """MALA's per-move tensor-core kernels (residual likelihood pass, adjoint GEMM, gradient
+    finish) timed alone with CUDA events, 100 back-to-back groups, against the burst BF16
+    peak: 2 N n p multiply-adds per group (the forward contraction and the adjoint)."""
+    import torch
+
+    reps = 100
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reg.grad_repeat(w["N"], 5, stream.cuda_stream)
+    e0.record(stream)
+    reg.grad_repeat(w["N"], reps, stream.cuda_stream)
+    e1.record(stream)
+    e1.synchronize()
+    reg.sync()
+    ms = e0.elapsed_time(e1) / reps
+    flop = 2.0 * 2.0 * w["N"] * w["n"] * w["p"]
+    achieved = flop / (ms / 1e3) / 1e12
+    peak, src = tensor_peak_burst()
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_loglik_tc<resid> + k_adjoint_tc + k_grad_finish", "launch_ms": ms,
+            "peak_source": src, "algorithmic_flop_per_launch": flop}
+
+
+def workload_line(name, args, stream, flush, dev, steps=3, warmup=2):
+    """A compact line for another workload (its own sweep time, throughput and roofline)."""
+    import paper_1106_0322_gb300 as spa
+    import torch
+    from paper_1106_0322_gb300 import synth
+
+    w = dict(synth.WORKLOADS[name], name=name)
+    region = synth.workload_region(name)
+    sched_d = torch.tensor(synth.workload_schedule(name), dtype=torch.float64, device=dev)
+    cfg = spa.make_config(move=w["move"], precision="split_bf16", stream=stream.cuda_stream)
+    reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
+    out_d = out_buffers(dev, w["T"], w["p"])
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    times = time_sweeps(reg, sched_d, w, steps, warmup, stream, flush, out_d, 300)
+    clocks = sampler.stop()
+    ms = sum(times) / len(times)
+    # MALA's per-move work counts the adjoint's N n p multiply-adds as well
+    mult = 2 if w["move"] == "mala" else 1
+    gmac = mult * algorithmic_gmac(w)
+    if w["move"] == "mala":
+        roof = grad_roofline(reg, w, stream)
+    else:
+        roof = loglik_roofline(reg, w, argparse.Namespace(precision="split_bf16", workload=name), stream)
+    line = {"workload": workload_desc(w), "precision": "split_bf16", "steps": steps, "warmup": warmup,
+            "ms_per_step": ms, "value": gmac / (ms / 1e3), "unit": "GMAC/s",
+            "metric_note": "N n p (T M + 1) algorithmic multiply-adds" + (" x 2 (likelihood + adjoint)" if mult == 2
+                                                                            else "") + " / sweep time",
+            "roofline": roof, "gpu_launches": int(reg.last_launch_count() * steps), "clocks": clocks}
+    reg.close()
+    return line
+
+
+def matched_error_compact(w, region, sched_d, stream, flush, dev, seeds=4, gold_seeds=8):
+    """Split-BF16 against plain FP32 at matched posterior-mean error, compact: gold = the mean
+    of gold_seeds FP32 sweeps at 4N; each path's error = RMSE over (t, j) of one sweep's
+    posterior means against the gold, averaged over `seeds` sweeps; the split path at N/2,
+    N and 2N, its sweep time interpolated (log-log) at the FP32 path's error at N."""
+    import numpy as np
+    import paper_1106_0322_gb300 as spa
+    import torch
+
+    T, p = w["T"], w["p"]
+
+    def runs(precision, N, seed_list):
+        cfg = spa.make_config(move=w["move"], precision=precision, stream=stream.cuda_stream)
+        reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
+        out = out_buffers(dev, T, p)
+        reg.run_device(sched_d, N, w["M"], 1, out)
+        means, ms = [], []
+        for s in seed_list:
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            reg.run_device(sched_d, N, w["M"], s, out)
+            e1.record(stream)
+            e1.synchronize()
+            reg.sync()
+            ms.append(e0.elapsed_time(e1))
+            means.append(out["mean"].cpu().numpy().copy())
+        reg.close()
+        return np.array(means), float(np.median(ms))
+
+    N = w["N"]
+    gold = runs("fp32", 4 * N, list(range(9000, 9000 + gold_seeds)))[0].mean(axis=0)
+
+    def rmse(m):
+        return float(np.mean([np.sqrt(np.mean((mi - gold) ** 2)) for mi in m]))
+
+    m32, ms32 = runs("fp32", N, list(range(100, 100 + seeds)))
+    e32 = rmse(m32)
+    table = []
+    for f in (0.5, 1.0, 2.0):
+        m, ms = runs("split_bf16", int(N * f), list(range(100, 100 + seeds)))
+        table.append({"N": int(N * f), "rmse": rmse(m), "ms": ms})
+    le = np.log([r["rmse"] for r in table])
+    lt = np.log([r["ms"] for r in table])
+    order = np.argsort(le)
+    t_at = float(np.exp(np.interp(np.log(e32), le[order], lt[order])))
+    split_at_N = next(r for r in table if r["N"] == N)
+    return {"gold": f"mean of {gold_seeds} FP32 sweeps at 4N", "seeds": seeds,
+            "fp32": {"N": N, "rmse": e32, "ms": ms32}, "split_bf16_at_N": split_at_N, "split_bf16_table": table,
+            "split_bf16_ms_at_fp32_error": t_at, "speedup_at_matched_error": ms32 / t_at,
+            "note": "errors flatten at the gold's own Monte Carlo error above N = 4096"}
+
+
+def batched_line(args, stream, dev, warmup=1, steps=2):
+    """The batched workload, compact (see batched_bench): one spa_batch of 64 regions."""
+    ns = argparse.Namespace(precision="split_bf16", warmup=warmup, steps=steps)
+    return batched_bench(ns, emit=False)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,6 +627,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the compact split-large / mala / batched / matched-error keys of the default line")
     ap.add_argument("--matched-error", action="store_true",
                     help="split-BF16 vs plain FP32 wall time at matched posterior-mean error (one JSON line)")
     args = ap.parse_args()
@@ -515,15 +680,7 @@ def main():
     cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream, **init)
     reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
     T, p = w["T"], w["p"]
-    out_d = {
-        "mean": torch.empty((T, p), dtype=torch.float64, device=dev),
-        "quantile": torch.empty((T, p, 3), dtype=torch.float64, device=dev),
-        "conc": torch.empty((T, p, 2), dtype=torch.float64, device=dev),
-        "ess": torch.empty(T, dtype=torch.float64, device=dev),
-        "log_z_inc": torch.empty(T, dtype=torch.float64, device=dev),
-        "accept_rate": torch.empty(T, dtype=torch.float64, device=dev),
-        "resampled": torch.empty(T, dtype=torch.uint8, device=dev),
-    }
+    out_d = out_buffers(dev, T, p)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed_base = replica_seed_base(rank)
 
@@ -571,26 +728,37 @@ def main():
     # ----------------------------------- dominant kernel: the likelihood GEMM + epilogue
     if w["move"] == "site":
         roofline = site_roofline(w, ms_per_step, clocks)
+    elif w["move"] == "mala" and args.precision == "split_bf16":
+        roofline = grad_roofline(reg, w, stream)
     else:
         roofline = loglik_roofline(reg, w, args, stream)
 
     # --------------------------------- plain FP32 comparator sweep on the same workload
+    # (the same K timed sweeps and warm-up rule as the split path, with its own clock record)
     plain = None
     if args.precision == "split_bf16" and rank == 0 and w["move"] != "site":
         reg32 = spa.Region(region.G, region.y, w["nu"],
                            config=spa.make_config(move=w["move"], precision="fp32", stream=stream.cuda_stream, **init))
-        reg32.run_device(sched_d, w["N"], w["M"], 7, out_d)
-        reg32.sync()
-        flush.zero_()
-        e0.record(stream)
-        reg32.run_device(sched_d, w["N"], w["M"], 8, out_d)
-        e1.record(stream)
-        e1.synchronize()
-        reg32.sync()
-        pms = e0.elapsed_time(e1)
-        plain = {"ms_per_step": pms, "value": gmac / (pms / 1e3), "unit": "GMAC/s",
-                 "speedup_of_split_bf16": pms / ms_per_step}
+        s32 = ClockSampler(torch.cuda.current_device())
+        s32.start()
+        t32 = time_sweeps(reg32, sched_d, w, args.steps, args.warmup, stream, flush, out_d, 7000)
+        c32 = s32.stop()
+        pms = sum(t32) / len(t32)
+        plain = {"ms_per_step": pms, "steps": args.steps, "warmup": args.warmup, "value": gmac / (pms / 1e3),
+                 "unit": "GMAC/s", "speedup_of_split_bf16": pms / ms_per_step, "clocks": c32,
+                 "roofline": loglik_roofline(reg32, w, argparse.Namespace(precision="fp32", workload=args.workload),
+                                             stream)}
         reg32.close()
+
+    # ---------------- the other configurations of the chosen form, compact (rank 0, N = 1)
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.precision == "split_bf16" and \
+            args.workload == "hit-region":
+        extras = {"split-large": workload_line("split-large", args, stream, flush, dev),
+                  "mala": workload_line("mala", args, stream, flush, dev),
+                  "batched": batched_line(args, stream, dev)}
+        extras["matched_error"] = matched_error_compact(w, region, sched_d, stream, flush, dev)
+        torch.cuda.set_stream(stream)
 
     # ------------------------------------------ end to end through the C ABI, host buffers
     e2e = None
@@ -645,6 +813,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks,
             "plain_fp32": plain,
+            "workloads": extras,
         }
         print(json.dumps(line), flush=True)
     reg.close()

@@ -225,6 +225,13 @@ int spa_loglik_tile_width(const spa_ctx* ctx);
  * SPA_EINVAL if no workspace of N particles exists. */
 int spa_loglik_repeat(spa_ctx* ctx, int64_t N, int32_t reps, void* stream);
 
+/* The same for MALA's per-move gradient kernels on the tensor cores: `reps` times the
+ * residual likelihood pass (softplus partials and r = y - logit^{-1}(eta) as BF16 hi | lo),
+ * the adjoint GEMM C = R G and the gradient finish, over the proposals last packed for N, in
+ * the sweep's launch configuration. SPA_EINVAL unless the context's last sweep was a
+ * split-BF16 MALA sweep of N particles. */
+int spa_grad_repeat(spa_ctx* ctx, int64_t N, int32_t reps, void* stream);
+
 /* Scale-marginalised summaries (Section 4, eq. all_particles). With a uniform prior on
  * log b and a log-spaced schedule (as spa_run's geometric schedules are), the particle
  * systems of all steps mix with weights proportional to Z_t / Z_1, each estimated by the

@@ -93,6 +93,7 @@ _SIGS = {
     "spa_map_path_given": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p,
                                      C.c_void_p]),
     "spa_loglik_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
+    "spa_grad_repeat": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p]),
     "spa_loglik": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "spa_loglik_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "spa_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_void_p, C.c_void_p]),
@@ -308,6 +309,9 @@ class Region:
 
     def loglik_repeat(self, N: int, reps: int, stream: int = 0):
         _check(load().spa_loglik_repeat(self._h, int(N), int(reps), stream or None), self._h)
+
+    def grad_repeat(self, N: int, reps: int, stream: int = 0):
+        _check(load().spa_grad_repeat(self._h, int(N), int(reps), stream or None), self._h)
 
     def loglik(self, B) -> np.ndarray:
         B = np.ascontiguousarray(B, dtype=np.float32)

@@ -168,14 +168,145 @@ __device__ __forceinline__ void tc_unit_range(bool ar, int m_tiles, int n_tiles,
     }
 }
 
-template <int BN, int STAGES, bool RESID, bool AR>
-__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
-    k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt, int tw,
-                int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
-                int64_t N_pad,
-                uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
-                int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns, int stall)
+// What the pipeline needs about one unit: a particle tile (128 rows of A) against an n-tile
+// (BN rows of G) of one region. `key` names the particle tile: consecutive units with the same
+// key share the resident A.
+struct TcUnit {
+    const CUtensorMap* A;   // particle operand (64-column boxes) and, for a narrow last
+    const CUtensorMap* At;  //   k-block, the tw-column boxes
+    const CUtensorMap* B;   // genotype operand, likewise
+    const CUtensorMap* Bt;
+    int tw, kblocks, ksteps, Kp, n, mt, nt;
+    int64_t key;
+    float* partial;
+    int64_t N_pad;
+    const uint32_t* ybits;
+    __nv_bfloat16* R;
+    int64_t n_r;
+    float* rsum_part;
+};
+
+// One region, its maps passed as kernel parameters: the units of CTA b are tc_unit_range's.
+struct TcSingleSource {
+    const CUtensorMap *A, *B, *At, *Bt;
+    int tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n;
+    float* partial;
+    int64_t N_pad;
+    const uint32_t* ybits;
+    __nv_bfloat16* R;
+    int64_t n_r;
+    float* rsum_part;
+
+    __device__ __forceinline__ void range(bool ar, int b, int G, int64_t& ub, int64_t& ue) const
+    {
+        tc_unit_range(ar, m_tiles, n_tiles, b, G, ub, ue);
+    }
+    __device__ __forceinline__ int64_t key(int64_t u) const { return u / n_tiles; }
+    __device__ __forceinline__ TcUnit unit(int64_t u) const
+    {
+        TcUnit t;
+        t.A = A;
+        t.At = At;
+        t.B = B;
+        t.Bt = Bt;
+        t.tw = tw;
+        t.kblocks = kblocks;
+        t.ksteps = ksteps;
+        t.Kp = Kp;
+        t.n = n;
+        t.mt = (int)(u / n_tiles);
+        t.nt = (int)(u % n_tiles);
+        t.key = t.mt;
+        t.partial = partial;
+        t.N_pad = N_pad;
+        t.ybits = ybits;
+        t.R = R;
+        t.n_r = n_r;
+        t.rsum_part = rsum_part;
+        return t;
+    }
+    __device__ __forceinline__ void prefetch(int64_t) const
+    {
+        tma_prefetch_desc(A);
+        tma_prefetch_desc(B);
+        if (tw) {
+            tma_prefetch_desc(At);
+            tma_prefetch_desc(Bt);
+        }
+    }
+};
+
+// Many regions in one launch: regs[r] holds region r's maps and sizes, its units are the
+// global units [regs[r].unit0, regs[r + 1].unit0), and CTA b takes the global units
+// [cta_units[b], cta_units[b + 1]) (split by the host in proportion to the work).
+struct TcGroupedSource {
+    const TcRegion* regs;
+    int R;
+    const int64_t* cta_units;
+
+    __device__ __forceinline__ void range(bool, int b, int, int64_t& ub, int64_t& ue) const
+    {
+        ub = cta_units[b];
+        ue = cta_units[b + 1];
+    }
+    __device__ __forceinline__ int region_of(int64_t u) const
+    {
+        int lo = 0, hi = R - 1;  // the last region whose first unit is <= u
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (regs[mid].unit0 <= u)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        return lo;
+    }
+    __device__ __forceinline__ int64_t key(int64_t u) const
+    {
+        const int r = region_of(u);
+        return ((int64_t)r << 32) | ((u - regs[r].unit0) / regs[r].n_tiles);
+    }
+    __device__ __forceinline__ TcUnit unit(int64_t u) const
+    {
+        const int r = region_of(u);
+        const TcRegion& g = regs[r];
+        const int64_t lu = u - g.unit0;
+        TcUnit t;
+        t.A = &g.A;
+        t.At = &g.At;
+        t.B = &g.B;
+        t.Bt = &g.Bt;
+        t.tw = g.tw;
+        t.kblocks = g.kblocks;
+        t.ksteps = g.ksteps;
+        t.Kp = g.Kp;
+        t.n = g.n;
+        t.mt = (int)(lu / g.n_tiles);
+        t.nt = (int)(lu % g.n_tiles);
+        t.key = ((int64_t)r << 32) | t.mt;
+        t.partial = g.partial;
+        t.N_pad = g.N_pad;
+        t.ybits = g.ybits;
+        t.R = g.R;
+        t.n_r = g.n_r;
+        t.rsum_part = g.rsum_part;
+        return t;
+    }
+    __device__ __forceinline__ void prefetch(int64_t u) const
+    {
+        const TcRegion& g = regs[region_of(u)];
+        tma_prefetch_desc(&g.A);
+        tma_prefetch_desc(&g.B);
+        if (g.tw) {
+            tma_prefetch_desc(&g.At);
+            tma_prefetch_desc(&g.Bt);
+        }
+    }
+};
+
+// The pipeline of one CTA over units [u_begin, u_end) of `src`.
+template <int BN, int STAGES, bool RESID, bool AR, class Src>
+__device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restrict__ err, uint64_t wait_ns, int stall)
 {
     using C = TcCfg<BN, STAGES, AR>;
     extern __shared__ uint8_t smem_raw[];
@@ -196,7 +327,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
 #define AFULL_BAR(kb) (bar0 + 8u * (uint32_t)(2 * STAGES + 6 + (kb)))
 
     int64_t u_begin, u_end;
-    tc_unit_range(AR, m_tiles, n_tiles, (int)blockIdx.x, (int)gridDim.x, u_begin, u_end);
+    src.range(AR, (int)blockIdx.x, (int)gridDim.x, u_begin, u_end);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -212,20 +343,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
         for (int kb = 0; kb < KB_RES; ++kb) mbar_init(AFULL_BAR(kb), 1);
         mbar_fence_init();
     }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
-        if (tw) {
-            tma_prefetch_desc(&mapAt);
-            tma_prefetch_desc(&mapBt);
-        }
-    }
-    // The last k-block is `tw` (16 or 32) columns wide when the K extent does not fill it:
-    // its tiles come from the narrow maps (32- or 64-byte swizzle) and carry fewer bytes.
-    const int kb_last = kblocks - 1;
-    const uint32_t a_tail = tw ? (uint32_t)(BM * tw * 2) : (uint32_t)C::A_TILE;
-    const uint32_t b_tail = tw ? (uint32_t)(BN * tw * 2) : (uint32_t)C::B_TILE;
-    const uint32_t tail_row = tw ? (uint32_t)(tw * 2) : 128u;
+    if (warp == 0 && lane == 0 && u_begin < u_end) src.prefetch(u_begin);
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), C::TMEM_COLS);
         tmem_relinquish();
@@ -239,35 +357,45 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
     grid_dependency_wait();
     grid_launch_dependents();
 
+    // The last k-block of a unit is `tw` (16 or 32) columns wide when the K extent does not
+    // fill it: its tiles come from the narrow maps (32- or 64-byte swizzle) and carry fewer bytes.
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            int epoch = -1, cur_mt = -1;  // A-resident: one epoch per run of units with the same m-tile
-            int a_issued = 0;             // k-blocks of the current epoch's A sent out
+            int epoch = -1;         // A-resident: one epoch per run of units with the same key
+            int64_t cur_key = -1;
+            int a_issued = 0;       // k-blocks of the current epoch's A sent out
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
-                const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+                const TcUnit t = src.unit(u);
+                const int kb_last = t.kblocks - 1;
+                const uint32_t a_tail = t.tw ? (uint32_t)(BM * t.tw * 2) : (uint32_t)C::A_TILE;
+                const uint32_t b_tail = t.tw ? (uint32_t)(BN * t.tw * 2) : (uint32_t)C::B_TILE;
                 bool a_first = false;  // the epoch's first unit: A's k-blocks go out between its G stages
-                if (AR && mt != cur_mt) {
+                if (AR && t.key != cur_key) {
                     ++epoch;
                     // the previous epoch's MMAs must be done with the resident A
                     if (epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((epoch - 1) & 1), err, wait_ns)) {
                         ok = false;
                         break;
                     }
+                    if (epoch > 0 && (t.key >> 32) != (cur_key >> 32)) src.prefetch(u);  // a new region
                     a_first = true;
                     a_issued = 0;
-                    cur_mt = mt;
+                    cur_key = t.key;
+                } else if (!AR && u > u_begin && (t.key >> 32) != (cur_key >> 32)) {
+                    src.prefetch(u);
                 }
-                for (int kb = 0; kb < kblocks; ++kb) {
+                if (!AR) cur_key = t.key;
+                for (int kb = 0; kb < t.kblocks; ++kb) {
                     if (AR && a_first) {
                         const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
-                        const bool tail = tw && kb == kb_last;
-                        const CUtensorMap* ma = tail ? &mapAt : &mapA;
+                        const bool tail = t.tw && kb == kb_last;
+                        const CUtensorMap* ma = tail ? t.At : t.A;
                         mbar_arrive_expect_tx(AFULL_BAR(kb), tail ? 2u * a_tail : 2u * (uint32_t)C::A_TILE);
-                        tma_load_2d(a, ma, AFULL_BAR(kb), kb * BK, mt * BM);
-                        tma_load_2d(a + C::A_TILE, ma, AFULL_BAR(kb), Kp + kb * BK, mt * BM);
+                        tma_load_2d(a, ma, AFULL_BAR(kb), kb * BK, t.mt * BM);
+                        tma_load_2d(a + C::A_TILE, ma, AFULL_BAR(kb), t.Kp + kb * BK, t.mt * BM);
                         ++a_issued;
                     }
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
@@ -276,18 +404,18 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                         break;
                     }
                     const uint32_t st = stage0 + s * C::STAGE;
-                    const bool tail = tw && kb == kb_last;
-                    const CUtensorMap* ma = tail ? &mapAt : &mapA;
-                    const CUtensorMap* mb = tail ? &mapBt : &mapB;
+                    const bool tail = t.tw && kb == kb_last;
+                    const CUtensorMap* ma = tail ? t.At : t.A;
+                    const CUtensorMap* mb = tail ? t.Bt : t.B;
                     const uint32_t bytes = AR ? (tail ? b_tail : (uint32_t)C::B_TILE)
                                               : (tail ? 2u * a_tail + b_tail : (uint32_t)C::STAGE);
                     mbar_arrive_expect_tx(FULL_BAR(s), bytes);
                     if (AR) {
-                        tma_load_2d(st, mb, FULL_BAR(s), kb * BK, nt * BN);
+                        tma_load_2d(st, mb, FULL_BAR(s), kb * BK, t.nt * BN);
                     } else {
-                        tma_load_2d(st, ma, FULL_BAR(s), kb * BK, mt * BM);
-                        tma_load_2d(st + C::A_TILE, ma, FULL_BAR(s), Kp + kb * BK, mt * BM);
-                        tma_load_2d(st + 2 * C::A_TILE, mb, FULL_BAR(s), kb * BK, nt * BN);
+                        tma_load_2d(st, ma, FULL_BAR(s), kb * BK, t.mt * BM);
+                        tma_load_2d(st + C::A_TILE, ma, FULL_BAR(s), t.Kp + kb * BK, t.mt * BM);
+                        tma_load_2d(st + 2 * C::A_TILE, mb, FULL_BAR(s), kb * BK, t.nt * BN);
                     }
                     ++it;
                 }
@@ -310,28 +438,31 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
             uint32_t it = 0;
             int lt = 0;
             bool ok = true;
-            int epoch = -1, cur_mt = -1;
+            int epoch = -1;
+            int64_t cur_key = -1;
             // Injected stall (tests of the timeout path): wait first on the drain barrier,
             // which nothing arrives at before this thread's own final commit, so the wait
             // runs out after wait_ns; no MMA has been issued, and the other roles give up and
             // drain as after any timeout.
             if (stall && !mbar_wait_bounded(drain_bar, 0u, err, wait_ns)) ok = false;
             for (int64_t u = u_begin; u < u_end && ok; ++u, ++lt) {
-                const int mt = (int)(u / n_tiles);
+                const TcUnit t = src.unit(u);
+                const int kb_last = t.kblocks - 1;
+                const uint32_t tail_row = t.tw ? (uint32_t)(t.tw * 2) : 128u;
                 const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
                 if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err, wait_ns)) {
                     ok = false;
                     break;
                 }
                 bool a_first = false;  // the epoch's first unit waits for each k-block of A
-                if (AR && mt != cur_mt) {
+                if (AR && t.key != cur_key) {
                     ++epoch;
                     a_first = true;
-                    cur_mt = mt;
+                    cur_key = t.key;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
-                for (int kb = 0; kb < kblocks; ++kb) {
+                for (int kb = 0; kb < t.kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
                     if (AR && a_first && !mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err, wait_ns)) {
                         ok = false;
@@ -344,11 +475,11 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                     tc_fence_after();
                     const uint32_t st = stage0 + s * C::STAGE;
                     const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
-                    const uint32_t rb = (tw && kb == kb_last) ? tail_row : 128u;
+                    const uint32_t rb = (t.tw && kb == kb_last) ? tail_row : 128u;
                     const uint64_t ahi = sdesc_swz(a, rb);
                     const uint64_t alo = sdesc_swz(a + C::A_TILE, rb);
                     const uint64_t bg = sdesc_swz(AR ? st : st + 2 * C::A_TILE, rb);
-                    const int nks = (ksteps - 4 * kb) < 4 ? (ksteps - 4 * kb) : 4;
+                    const int nks = (t.ksteps - 4 * kb) < 4 ? (t.ksteps - 4 * kb) : 4;
                     for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
                         umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
                     for (int ks = 0; ks < nks; ++ks) umma_bf16(d, alo + 2u * ks, bg + 2u * ks, IDESC, 1u);
@@ -359,7 +490,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 umma_commit(ACCF_BAR(b));
                 // the resident A is free once this unit's MMAs are done, if the next unit
                 // belongs to another particle tile
-                if (AR && u + 1 < u_end && (int)((u + 1) / n_tiles) != mt) umma_commit(aempty_bar);
+                if (AR && u + 1 < u_end && src.key(u + 1) != t.key) umma_commit(aempty_bar);
             }
             // Wait for every MMA this thread issued before TMEM can be released.
             umma_commit(drain_bar);
@@ -376,14 +507,15 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
         const int col0 = grp * CPW * 32;
         int lt = 0;
         for (int64_t u = u_begin; u < u_end; ++u, ++lt) {
-            const int mt = (int)(u / n_tiles), nt = (int)(u % n_tiles);
+            const TcUnit t = src.unit(u);
             const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
             if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
             tc_fence_after();
-            const int valid0 = n - nt * BN - col0;  // valid columns from col0 on
+            const int valid0 = t.n - t.nt * BN - col0;  // valid columns from col0 on
             const uint32_t tbase = tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)col0;
-            const int64_t prow = (int64_t)mt * BM + row;
-            const int64_t gc0 = ((int64_t)nt * BN + col0) >> 5;  // global index of the first chunk
+            const int64_t prow = (int64_t)t.mt * BM + row;
+            const int64_t gc0 = ((int64_t)t.nt * BN + col0) >> 5;  // global index of the first chunk
+            float* __restrict__ partial = t.partial;
             if (!RESID) {
                 // all of this warp's chunks in flight at once, then the buffer goes back to the MMA
                 uint32_t r[CPW][32];
@@ -398,7 +530,7 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                 for (int ch = 0; ch < CPW; ++ch) {
                     const int valid = valid0 - 32 * ch;
                     if (valid <= 0) break;
-                    partial[(gc0 + ch) * N_pad + prow] = -sum_sp2_32(r[ch], valid);
+                    partial[(gc0 + ch) * t.N_pad + prow] = -sum_sp2_32(r[ch], valid);
                 }
             } else {
                 for (int ch = 0; ch < CPW; ++ch) {
@@ -410,11 +542,12 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
                     float v[32];
 #pragma unroll
                     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-                    const int64_t i0 = (int64_t)nt * BN + col0 + 32 * ch;
+                    const int64_t i0 = (int64_t)t.nt * BN + col0 + 32 * ch;
                     float rs;
-                    const float sp = resid_chunk(v, valid, __ldg(ybits + (i0 >> 5)), R + prow * 2 * n_r + i0, n_r, rs);
-                    partial[(gc0 + ch) * N_pad + prow] = -sp;
-                    rsum_part[(gc0 + ch) * N_pad + prow] = rs;
+                    const float sp =
+                        resid_chunk(v, valid, __ldg(t.ybits + (i0 >> 5)), t.R + prow * 2 * t.n_r + i0, t.n_r, rs);
+                    partial[(gc0 + ch) * t.N_pad + prow] = -sp;
+                    t.rsum_part[(gc0 + ch) * t.N_pad + prow] = rs;
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -434,6 +567,31 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
         tc_fence_after();
         tmem_dealloc(tmem_base, C::TMEM_COLS);
     }
+}
+
+template <int BN, int STAGES, bool RESID, bool AR>
+__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
+    k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt, int tw,
+                int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
+                int64_t N_pad,
+                uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
+                int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns, int stall)
+{
+    const TcSingleSource src{&mapA, &mapB, &mapAt, &mapBt, tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n,
+                             partial, N_pad, ybits, R, n_r, rsum_part};
+    loglik_tc_body<BN, STAGES, RESID, AR>(src, err, wait_ns, stall);
+}
+
+// The same pipeline over the units of many regions (a batched sweep's move): region tables
+// and per-CTA unit ranges in global memory.
+template <int BN, int STAGES, bool RESID, bool AR>
+__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
+    k_loglik_tc_grouped(const TcRegion* __restrict__ regs, int R, const int64_t* __restrict__ cta_units,
+                        uint32_t* __restrict__ err, uint64_t wait_ns)
+{
+    const TcGroupedSource src{regs, R, cta_units};
+    loglik_tc_body<BN, STAGES, RESID, AR>(src, err, wait_ns, 0);
 }
 
 // ----------------------------------------------------------------------- adjoint
@@ -582,20 +740,46 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 }
 
 // grad l_kj = (sum_s C_s[k, j] - m_j sum_i r_ki) / s_j (+ the prior gradient at scale c > 0).
-// One warp per particle, FP32: the K-split partials and the residual chunk sums are added
-// with compensation, and C - m_j sum r is formed by one fused multiply-add.
-__global__ void k_grad_finish(const float* __restrict__ gpart, int ksplit, const float* __restrict__ rsum_part,
-                              int n_parts, int64_t N_pad, int64_t N, int p, const float* __restrict__ mean_f,
-                              const float* __restrict__ inv_sd, const float* __restrict__ B, PriorArgs pr, double c,
-                              float* __restrict__ grad)
+// A block of 8 warps takes 8 particles, one warp each. First the residual sums sum_i r_ki from
+// the chunk sums rsum_part[q][k]: thread t adds chunks q = t/8, t/8 + 32, ... of particle t % 8,
+// so the 8 threads of a group read one 32-byte sector per chunk (with one lane per chunk, as a
+// warp per particle would, each load touches its own sector), and the 32 compensated partial
+// sums of a particle are combined in slice order. Then each warp finishes its particle's row
+// (lane j reads marker j of every K-split partial), C - m_j sum r by one fused multiply-add.
+constexpr int GF_PARTICLES = 8;
+
+__global__ void __launch_bounds__(256) k_grad_finish(const float* __restrict__ gpart, int ksplit,
+                                                     const float* __restrict__ rsum_part, int n_parts, int64_t N_pad,
+                                                     int64_t N, int p, const float* __restrict__ mean_f,
+                                                     const float* __restrict__ inv_sd, const float* __restrict__ B,
+                                                     PriorArgs pr, double c, float* __restrict__ grad)
 {
-    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    __shared__ float2 part[32][GF_PARTICLES];
+    __shared__ float rsum[GF_PARTICLES];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t k0 = (int64_t)blockIdx.x * GF_PARTICLES;
+    {
+        const int kk = threadIdx.x % GF_PARTICLES, slice = threadIdx.x / GF_PARTICLES;
+        const int64_t k = k0 + kk;
+        FSum rq;
+        if (k < N)
+            for (int q = slice; q < n_parts; q += 32) rq.add(rsum_part[(int64_t)q * N_pad + k]);
+        part[slice][kk] = make_float2(rq.s, rq.c);
+    }
+    __syncthreads();
+    if (threadIdx.x < GF_PARTICLES) {
+        FSum rq;
+        for (int s2 = 0; s2 < 32; ++s2) {
+            const float2 v = part[s2][threadIdx.x];
+            rq.add(v.x);
+            rq.c += v.y;
+        }
+        rsum[threadIdx.x] = (float)rq.value();
+    }
+    __syncthreads();
+    const int64_t k = k0 + w;
     if (k >= N) return;
-    FSum rq;
-    for (int q = lane; q < n_parts; q += 32) rq.add(rsum_part[(int64_t)q * N_pad + k]);
-    rq = warp_sum(rq);
-    const float rs = rq.value();
+    const float rs = rsum[w];
     const float a1 = pr.a + 1.0f, ac = (float)((double)pr.a * c), inv_c = c > 0.0 ? (float)(1.0 / c) : 0.0f;
     for (int j = lane; j < p; j += 32) {
         FSum g;
@@ -683,6 +867,14 @@ cudaError_t tc_init_attributes()
     SET_SMEM((k_loglik_tc<128, 4, false, true>), (TcCfg<128, 4, true>::SMEM));
     SET_SMEM((k_loglik_tc<256, 3, true, true>), (TcCfg<256, 3, true>::SMEM));
     SET_SMEM((k_loglik_tc<128, 4, true, true>), (TcCfg<128, 4, true>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<256, 3, false, false>), (TcCfg<256, 3, false>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<128, 4, false, false>), (TcCfg<128, 4, false>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<256, 3, true, false>), (TcCfg<256, 3, false>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<128, 4, true, false>), (TcCfg<128, 4, false>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<256, 3, false, true>), (TcCfg<256, 3, true>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<128, 4, false, true>), (TcCfg<128, 4, true>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<256, 3, true, true>), (TcCfg<256, 3, true>::SMEM));
+    SET_SMEM((k_loglik_tc_grouped<128, 4, true, true>), (TcCfg<128, 4, true>::SMEM));
     SET_SMEM((k_adjoint_tc<ADJ_BN_SMALL, 3>), (AdjCfg<ADJ_BN_SMALL, 3>::SMEM));
     SET_SMEM((k_adjoint_tc<256, 3>), (AdjCfg<256, 3>::SMEM));
 #undef SET_SMEM
@@ -755,6 +947,48 @@ cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, 
 #undef TC_CASE
 }
 
+bool tc_plan_resident(const TcPlan& plan) { return plan.kblocks <= KB_RES; }
+
+template <int BN, int STAGES, bool RESID, bool AR>
+static cudaError_t launch_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, uint32_t* err,
+                                  cudaStream_t st, uint64_t wait_ns)
+{
+    using C = TcCfg<BN, STAGES, AR>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(Epi<RESID>::THREADS);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_loglik_tc_grouped<BN, STAGES, RESID, AR>, regs, R, cta_units, err, wait_ns);
+}
+
+cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int BN, bool ar,
+                                     bool resid, uint32_t* err, cudaStream_t st, uint64_t wait_ns)
+{
+    if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
+#define G_CASE(BN_, S_, R_, AR_) return launch_grouped<BN_, S_, R_, AR_>(regs, R, cta_units, grid, err, st, wait_ns)
+    if (resid) {
+        if (BN == 256) {
+            if (ar) G_CASE(256, 3, true, true);
+            G_CASE(256, 3, true, false);
+        }
+        if (ar) G_CASE(128, 4, true, true);
+        G_CASE(128, 4, true, false);
+    }
+    if (BN == 256) {
+        if (ar) G_CASE(256, 3, false, true);
+        G_CASE(256, 3, false, false);
+    }
+    if (ar) G_CASE(128, 4, false, true);
+    G_CASE(128, 4, false, false);
+#undef G_CASE
+}
+
 AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms)
 {
     AdjPlan a;
@@ -802,8 +1036,8 @@ cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum
                                int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st)
 {
-    k_grad_finish<<<(unsigned)((N + 7) / 8), 256, 0, st>>>(gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd,
-                                                           B, pr, c, grad);
+    k_grad_finish<<<(unsigned)((N + GF_PARTICLES - 1) / GF_PARTICLES), 256, 0, st>>>(
+        gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd, B, pr, c, grad);
     return cudaGetLastError();
 }
 

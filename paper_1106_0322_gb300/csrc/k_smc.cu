@@ -40,10 +40,13 @@ __device__ __forceinline__ float prior_term(float b, float inv_ac, int de)
 }
 __device__ __forceinline__ double prior_coef(PriorArgs pr, double c) { return pr.de ? -1.0 / c : -((double)pr.a + 1.0); }
 
+// The prior's gradient in MALA's drift. The drift can be any fixed function of the state:
+// the MH test evaluates the forward and reverse proposal densities with this same function,
+// so the fast quotient (within 2 ulp) keeps each step's kernel exactly pi_t-invariant.
 __device__ __forceinline__ float dlogprior(float b, float a1, float ac, float inv_c, int de)
 {
     const float sg = (b > 0.0f) ? 1.0f : ((b < 0.0f) ? -1.0f : 0.0f);
-    return de ? -sg * inv_c : -a1 * sg / (ac + fabsf(b));
+    return de ? -sg * inv_c : __fdividef(-a1 * sg, ac + fabsf(b));
 }
 
 // ------------------------------------------------------------------- init (t = 0)
@@ -330,10 +333,9 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             const float* b1 = a.beta_p + i * p;
             const float* g1 = a.gl_p + i * p;
             for (int j = lane; j < p; j += 32) {
-                const float Dj = D[j];
-                const float drift = h2 * Dj * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
+                const float drift = h2 * D[j] * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
                 const float d = (b0[j] - b1[j]) - drift;
-                bwd.add(d * d / Dj);
+                bwd.add(d * d * a.inv_D[j]);
             }
             bwd = warp_sum(bwd);
             const float2 fw = a.fwd[i];
@@ -361,12 +363,11 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                         cur[j] = b0;
                         gcur[j] = g0;
                     }
-                    const float Dj = D[j];
-                    const float drift = h2 * Dj * (g0 + dlogprior(b0, a1, ac, inv_c, pr.de));
-                    const float b = (b0 + drift) + h * sqrtf(Dj) * comp(z4, k);
+                    const float drift = h2 * D[j] * (g0 + dlogprior(b0, a1, ac, inv_c, pr.de));
+                    const float b = (b0 + drift) + h * a.sqrt_D[j] * comp(z4, k);
                     dst[j] = b;
                     const float d = (b - b0) - drift;
-                    fw.add(d * d / Dj);
+                    fw.add(d * d * a.inv_D[j]);
                     lt.add(prior_term(b, sk.w, pr.de));
                     yd = fmaf(b, a.vy[j], yd);
                     if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
@@ -531,10 +532,9 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
             const float* b1 = a.beta_p + i * p;
             const float* g1 = a.gl_p + i * p;
             for (int j = lane; j < p; j += 32) {
-                const float Dj = a.sigma[j];
-                const float drift = h2 * Dj * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
+                const float drift = h2 * a.sigma[j] * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
                 const float d = (b0[j] - b1[j]) - drift;
-                bwd.add(d * d / Dj);
+                bwd.add(d * d * a.inv_D[j]);
             }
             bwd = warp_sum(bwd);
             const float2 fw = a.fwd[i];
@@ -988,7 +988,11 @@ __global__ void k_colstats_finish(const float4* __restrict__ part, int p, int sp
     if (kind == 0) {
         scale_out[j] = (float)(lam / sqrt((double)p) * fmax(sqrt(var), fl));
     } else {
-        scale_out[j] = (float)fmax(var, fl * fl);
+        // MALA's D_j, and beside it sqrt(D_j) and 1/D_j for the proposal and its densities
+        const double D = fmax(var, fl * fl);
+        scale_out[j] = (float)D;
+        scale_out[p + j] = (float)sqrt(D);
+        scale_out[2 * p + j] = (float)(1.0 / D);
     }
 }
 

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -387,7 +388,7 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     if (e == cudaSuccess) e = dalloc(&w.ptr, (size_t)(cnt))
     WA(beta, N * p);
     WA(beta_p, N * p);
-    WA(scale, p);
+    WA(scale, 3 * p);  // RW: sigma; MALA: D, sqrt(D), 1/D
     WA(A, N_pad * 2 * c->Kp);
     WA(lpt_p, N); WA(ydq, N); WA(llq, N); WA(lpq, N); WA(llq_tmp, N); WA(lpq_tmp, N);
     WA(ll, N); WA(logw, N); WA(W, N); WA(Wf, N); WA(wfix, N);
@@ -527,18 +528,27 @@ TcMaps maps_of(const spa_ctx* c)
     return m;
 }
 
-void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
+// The adjoint's second half after a residual likelihood pass: C = R G, then the gradient.
+void enq_grad_tail(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
 {
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     const TcPlan plan = plan_of(c);
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
-    ResidArgs ra{w.R, a.n_r, w.rsum};
-    q.ck(launch_loglik_tc(maps_of(c), plan, c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra,
-                          c->wait_ns, c->fault & FAULT_STALL));
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st, c->wait_ns));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
                             c->pr, cs, out, q.st));
+}
+
+void enq_grad_tc(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
+    ResidArgs ra{w.R, a.n_r, w.rsum};
+    q.ck(launch_loglik_tc(maps_of(c), plan_of(c), c->n, c->Kp, c->ybits, w.partial, w.N_pad, c->d_err, q.st, &ra,
+                          c->wait_ns, c->fault & FAULT_STALL));
+    enq_grad_tail(q, out, Bsrc, cs, N);
 }
 
 // log-likelihood of the current proposals (beta_p) into the partial sums
@@ -589,6 +599,8 @@ MoveArgs move_args(spa_ctx* c, unsigned long long* acc)
     a.lpt_p = w.lpt_p;
     a.ydq = w.ydq;
     a.sigma = w.scale;
+    a.sqrt_D = w.scale + c->p;
+    a.inv_D = w.scale + 2 * c->p;
     a.l2e_over_s = c->l2e_s;
     a.mean_f = c->mean_f;
     a.vy = c->colf + (tc ? 2 : 1) * c->p;
@@ -598,49 +610,6 @@ MoveArgs move_args(spa_ctx* c, unsigned long long* acc)
     a.fwd = w.fwd;
     a.h = w.h;
     return a;
-}
-
-// The proposals' log-likelihood partials (and, for MALA, their gradients into gl_p).
-void enq_proposal_likelihood(Enq& q, bool mala)
-{
-    spa_ctx* c = q.c;
-    Workspace& w = c->ws;
-    if (!mala) {
-        enq_loglik(q);
-    } else if (c->cfg.precision == SPA_PREC_SPLIT_BF16) {
-        enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
-    } else {
-        enq_loglik(q);
-        q.ck(launch_grad_simt(w.beta_p, c->Xf, c->y, w.N, c->n, (int)c->p, w.eta, w.gl_p, nullptr, c->pr, 0.0, q.st));
-        ++q.launches;  // the plain adjoint is two kernels
-    }
-}
-
-// M moves at step t with move indices m0 .. m0+M-1: the MH test of move m runs inside the
-// proposal kernel of move m+1, the last one in the commit kernel.
-void enq_moves(Enq& q, int t, uint32_t m0, int M, unsigned long long* acc)
-{
-    if (M <= 0) return;
-    spa_ctx* c = q.c;
-    Workspace& w = c->ws;
-    if (c->cfg.move_kind == SPA_MOVE_SITE) {  // all M cycles in one launch
-        const float inv_sp = c->cfg.precision == SPA_PREC_SPLIT_BF16 ? (float)LOG2E : 1.0f;
-        const SiteArgs sa{w.beta, w.llq, w.lpq, inv_sp, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
-        q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.stepk, t, m0, M, c->rb.seed, q.st));
-        return;
-    }
-    const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
-    const MoveArgs a = move_args(c, acc);
-    const int p = (int)c->p;
-    for (int mm = 0; mm < M; ++mm) {
-        const uint32_t m = m0 + (uint32_t)mm;
-        if (mala)
-            q.ck(launch_move_mala(a, mm > 0, w.N, p, c->pr, c->rb.stepk, t, m, m - 1u, c->rb.seed, c->d_err, q.st));
-        else
-            q.ck(launch_move_rw(a, mm > 0, w.N, p, c->pr, c->rb.stepk, t, m, m - 1u, c->rb.seed, 1, c->d_err, q.st));
-        enq_proposal_likelihood(q, mala);
-    }
-    q.ck(launch_move_commit(a, mala, w.N, p, c->pr, c->rb.stepk, t, m0 + (uint32_t)(M - 1), c->rb.seed, c->d_err, q.st));
 }
 
 void enq_resample(Enq& q, int t)
@@ -667,102 +636,249 @@ void enq_colstats(Enq& q, int t)
     ++q.launches;  // two kernels
 }
 
+// A likelihood evaluation inside a sweep: of the initial prior draws (t = 0) or of a move's
+// proposals. Both are of the packed particles (beta_p and the GEMM rows A); on the MALA path
+// they also give the log-likelihood gradient, into gl (the draws) or gl_p (the proposals).
+struct LikPoint {
+    bool init;
+};
+
+// The single-region way to evaluate one: the context's own kernels on its stream.
+void enq_likelihood(Enq& q, const LikPoint& lp)
+{
+    spa_ctx* c = q.c;
+    Workspace& w = c->ws;
+    const bool mala = c->cfg.move_kind == SPA_MOVE_MALA;
+    float* out = lp.init ? w.gl : w.gl_p;
+    const float* src = lp.init ? w.beta : w.beta_p;
+    if (mala && c->cfg.precision == SPA_PREC_SPLIT_BF16) {
+        enq_grad_tc(q, out, src, 0.0, w.N);  // also leaves the softplus partials
+        return;
+    }
+    enq_loglik(q);
+    if (mala) {
+        q.ck(launch_grad_simt(src, c->Xf, c->y, w.N, c->n, (int)c->p, w.eta, out, nullptr, c->pr, 0.0, q.st));
+        ++q.launches;  // the plain adjoint is two kernels
+    }
+}
+
+// One sweep of one context, enqueued piecewise: next() enqueues everything up to the sweep's
+// next likelihood evaluation and stops there, so that a batch can evaluate the likelihoods of
+// many regions' particles in one grouped launch before any region goes on. Between two
+// stops the work is in the order of Section 4: init; then per scale step reweight,
+// log-sum-exp / ESS, conditional resampling, proposal scales, M x (the MH test of the pending
+// proposal fused with the next proposal, its likelihood), the last MH test with its commit,
+// the summaries. A move's MH test runs at the start of the next move's proposal kernel.
+class SweepGen {
+public:
+    SweepGen(spa_ctx* c, int64_t T, int M) : c_(c), T_(T), M_(M)
+    {
+        const spa_config& cfg = c->cfg;
+        mala_ = cfg.move_kind == SPA_MOVE_MALA;
+        site_ = cfg.move_kind == SPA_MOVE_SITE;
+        // The step's summaries overlap the next step when that step is many short kernels
+        // (RW, MALA). The single-coordinate cycle is one long launch per step whose blocks fill
+        // the SMs: the summaries would only take SMs from it (measured 2% slower), so they stay
+        // inline.
+        fork_sum_ = !site_;
+        // acceptance is per proposal: per coordinate update for the single-coordinate cycle
+        denom_ = (double)c->ws.N * (double)M * (site_ ? (double)c->p : 1.0);
+        sa_.nq = cfg.n_quantiles;
+        sa_.nd = cfg.n_deltas;
+        for (int k = 0; k < 8; ++k) {
+            sa_.q[k] = cfg.quantiles[k];
+            sa_.delta[k] = cfg.deltas[k];
+        }
+    }
+
+    // Enqueue up to the next likelihood evaluation; true with *lp set if stopped at one (the
+    // caller enqueues it, then calls next again), false when the sweep is complete.
+    bool next(Enq& q, LikPoint* lp)
+    {
+        spa_ctx* c = c_;
+        Workspace& w = c->ws;
+        RunBufs& r = c->rb;
+        const spa_config& cfg = c->cfg;
+        const int p = (int)c->p;
+        const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
+        for (;;) {
+            switch (st_) {
+            case START: {
+                if (q.e == cudaSuccess) q.e = cudaMemsetAsync(r.acc, 0, sizeof(unsigned long long) * (size_t)(T_ + 1), q.st);
+                if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
+                if (mala_) q.ck(launch_set_f64(w.lambda, cfg.mala_h, q.st));
+                q.ck(launch_step_constants(c->pr, r.sched, (int)T_, p, r.stepk, r.rk, q.st));
+                // t = 0: prior draws, their log-likelihoods, importance weights
+                q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
+                const MoveArgs a0 = move_args(c, nullptr);
+                q.ck(launch_move_rw(a0, false, w.N, p, c->pr, r.stepk, 0, 0u, 0u, r.seed, 0, c->d_err, q.st));
+                st_ = AFTER_INIT;
+                lp->init = true;
+                return true;
+            }
+            case AFTER_INIT: {
+                q.ck(launch_finish_loglik(mh_state(c, nullptr), w.N, w.logw, nullptr, c->d_err, q.st));
+                if (c->fault & FAULT_NAN_WEIGHT) q.ck(launch_set_f64(w.logw, std::nan(""), q.st));
+                const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
+                q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz,
+                                    r.res, w.flag, c->d_err, q.st));
+                ++q.launches;  // log-sum-exp is two kernels
+                if (rm) {
+                    enq_resample(q, 0);
+                    b_ = 0;
+                    st_ = BURN_BEGIN;
+                } else {
+                    t_ = 0;
+                    st_ = STEP_BEGIN;
+                }
+                break;
+            }
+            case BURN_BEGIN: {
+                if (b_ == cfg.burn_in_steps) {
+                    q.ck(launch_mark_uniform(w.N, 0, r.ess, r.res, w.flag, q.st));
+                    t_ = 0;
+                    st_ = STEP_BEGIN;
+                    break;
+                }
+                unsigned long long* scratch = r.acc + T_;
+                if (q.e == cudaSuccess) q.e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), q.st);
+                if (!site_) enq_colstats(q, 0);
+                begin_moves(q, 0, m_base_, scratch, BURN_MOVE, BURN_END);
+                break;
+            }
+            case BURN_END: {
+                if (mala_) q.ck(launch_adapt_lambda(w.lambda, r.acc + T_, denom_, q.st));
+                m_base_ += (uint32_t)M_;
+                ++b_;
+                st_ = BURN_BEGIN;
+                break;
+            }
+            case STEP_BEGIN: {
+                if (t_ == T_) {
+                    // the last summaries
+                    if (fork_sum_ && T_ > 0 && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_join, 0);
+                    q.ck(launch_accept_rate(r.acc, (int)T_, denom_, r.accrate, q.st));
+                    st_ = DONE;
+                    break;
+                }
+                const int t = (int)t_;
+                if (t > 0) {
+                    q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.rk, t, c->d_err, q.st));
+                    // the previous step's transpose has read beta and the weights (forked runs)
+                    if (fork_sum_ && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_keys, 0);
+                    q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, t, 0, cfg.ess_frac, r.ess, r.logz, r.res,
+                                        w.flag, c->d_err, q.st));
+                    ++q.launches;
+                }
+                enq_resample(q, t);
+                if (!site_) enq_colstats(q, t);
+                begin_moves(q, t, t == 0 ? m_base_ : 0u, r.acc + t, STEP_MOVE, STEP_END);
+                break;
+            }
+            case BURN_MOVE:
+            case STEP_MOVE: {
+                if (mm_ == M_) {
+                    // the last MH test of the block, with the commit of its accepted rows
+                    const MoveArgs a = move_args(c, acc_);
+                    q.ck(launch_move_commit(a, mala_, w.N, p, c->pr, r.stepk, mt_, m0_ + (uint32_t)(M_ - 1), r.seed,
+                                            c->d_err, q.st));
+                    st_ = after_moves_;
+                    break;
+                }
+                const MoveArgs a = move_args(c, acc_);
+                const uint32_t m = m0_ + (uint32_t)mm_;
+                if (mala_)
+                    q.ck(launch_move_mala(a, mm_ > 0, w.N, p, c->pr, r.stepk, mt_, m, m - 1u, r.seed, c->d_err, q.st));
+                else
+                    q.ck(launch_move_rw(a, mm_ > 0, w.N, p, c->pr, r.stepk, mt_, m, m - 1u, r.seed, 1, c->d_err, q.st));
+                ++mm_;
+                lp->init = false;
+                return true;
+            }
+            case STEP_END: {
+                const int t = (int)t_;
+                if (fork_sum_) {
+                    // The key transpose and the summaries of step t run on the side stream beside
+                    // step t + 1. The transpose reads beta and the weights, which step t + 1 first
+                    // rewrites in its normalisation (it waits for ev_keys before); it copies the
+                    // weights for the summaries, which then read nothing that the main stream writes.
+                    if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_fork, q.st);
+                    if (q.e == cudaSuccess) q.e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
+                    q.ck(launch_keys(w.beta, w.Wf, w.wfix, w.N, p, w.keysT, w.WfS, w.wfixS, false, c->side_stream));
+                    if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_keys, c->side_stream);
+                    q.ck(launch_summaries_keys(w.keysT, w.WfS, w.wfixS, w.N, p, sa_, t, r.mean, r.quant, r.conc, false,
+                                               c->side_stream));
+                    if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_join, c->side_stream);
+                } else {
+                    q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa_, t, r.mean, r.quant, r.conc, w.keysT, q.st));
+                    ++q.launches;  // the key transpose and the summaries
+                }
+                if (cfg.map_path)
+                    q.ck(launch_best_particle(mh_state(c, nullptr), w.beta, w.N, p, c->pr, r.sched, t, r.best, q.st));
+                if (mala_) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom_, q.st));
+                ++t_;
+                st_ = STEP_BEGIN;
+                break;
+            }
+            case DONE:
+                return false;
+            }
+        }
+    }
+
+private:
+    enum Stage { START, AFTER_INIT, BURN_BEGIN, BURN_MOVE, BURN_END, STEP_BEGIN, STEP_MOVE, STEP_END, DONE };
+
+    // M moves at step t with move indices m0 .. m0+M-1 (all M cycles in one launch for the
+    // single-coordinate kernel, which needs no likelihood evaluations), then `after`.
+    void begin_moves(Enq& q, int t, uint32_t m0, unsigned long long* acc, Stage moves, Stage after)
+    {
+        spa_ctx* c = c_;
+        Workspace& w = c->ws;
+        if (M_ <= 0) {
+            st_ = after;
+            return;
+        }
+        if (site_) {
+            const float inv_sp = c->cfg.precision == SPA_PREC_SPLIT_BF16 ? (float)LOG2E : 1.0f;
+            const SiteArgs sa{w.beta, w.llq, w.lpq, inv_sp, c->XT2, c->colf + c->p, (float)c->cfg.site_sd, acc};
+            q.ck(launch_move_site(sa, w.N, (int)c->p, c->n, c->pr, c->rb.stepk, t, m0, M_, c->rb.seed, q.st));
+            st_ = after;
+            return;
+        }
+        mt_ = t;
+        m0_ = m0;
+        acc_ = acc;
+        mm_ = 0;
+        after_moves_ = after;
+        st_ = moves;
+    }
+
+    spa_ctx* c_;
+    int64_t T_;
+    int M_;
+    bool mala_ = false, site_ = false, fork_sum_ = true;
+    double denom_ = 0.0;
+    SummaryArgs sa_;
+    Stage st_ = START;
+    int64_t t_ = 0;
+    int b_ = 0;
+    uint32_t m_base_ = 0;
+    // the current block of moves
+    int mt_ = 0, mm_ = 0;
+    uint32_t m0_ = 0;
+    unsigned long long* acc_ = nullptr;
+    Stage after_moves_ = STEP_END;
+};
+
 int64_t enqueue_sweep(spa_ctx* c, int64_t T, int M, cudaError_t* err_out)
 {
     Enq q;
     q.c = c;
     q.st = c->stream();
-    Workspace& w = c->ws;
-    RunBufs& r = c->rb;
-    const spa_config& cfg = c->cfg;
-    const bool tc = cfg.precision == SPA_PREC_SPLIT_BF16;
-    const bool mala = cfg.move_kind == SPA_MOVE_MALA;
-    const int p = (int)c->p;
-    const bool site = cfg.move_kind == SPA_MOVE_SITE;
-    // The step's summaries overlap the next step when that step is many short kernels (RW,
-    // MALA). The single-coordinate cycle is one long launch per step whose blocks fill the
-    // SMs: the summaries would only take SMs from it (measured 2% slower), so they stay inline.
-    const bool fork_sum = !site;
-    // acceptance is per proposal: per coordinate update for the single-coordinate cycle
-    const double denom = (double)w.N * (double)M * (site ? (double)p : 1.0);
-    SummaryArgs sa;
-    sa.nq = cfg.n_quantiles;
-    sa.nd = cfg.n_deltas;
-    for (int k = 0; k < 8; ++k) {
-        sa.q[k] = cfg.quantiles[k];
-        sa.delta[k] = cfg.deltas[k];
-    }
-    if (q.e == cudaSuccess) q.e = cudaMemsetAsync(r.acc, 0, sizeof(unsigned long long) * (size_t)(T + 1), q.st);
-    if (q.e == cudaSuccess) q.e = cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), q.st);
-    if (mala) q.ck(launch_set_f64(w.lambda, cfg.mala_h, q.st));
-    const WeightArrays wa{w.logw, w.W, w.Wf, w.wfix};
-    q.ck(launch_step_constants(c->pr, r.sched, (int)T, p, r.stepk, r.rk, q.st));
-    // t = 0: prior draws, their log-likelihoods, importance weights
-    q.ck(launch_init_prior(w.beta, w.N, p, c->pr, r.sched, 0, r.seed, q.st));
-    const MoveArgs a0 = move_args(c, nullptr);
-    q.ck(launch_move_rw(a0, false, w.N, p, c->pr, r.stepk, 0, 0u, 0u, r.seed, 0, c->d_err, q.st));
-    if (mala && tc) {
-        enq_grad_tc(q, w.gl, w.beta, 0.0, w.N);  // also leaves the softplus partials of the draws
-    } else {
-        enq_loglik(q);
-        if (mala) {
-            q.ck(launch_grad_simt(w.beta, c->Xf, c->y, w.N, c->n, p, w.eta, w.gl, nullptr, c->pr, 0.0, q.st));
-            ++q.launches;
-        }
-    }
-    q.ck(launch_finish_loglik(a0.mh, w.N, w.logw, nullptr, c->d_err, q.st));
-    if (c->fault & FAULT_NAN_WEIGHT) q.ck(launch_set_f64(w.logw, std::nan(""), q.st));
-    const bool rm = cfg.init_mode == SPA_INIT_RESAMPLE_MOVE;
-    q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, 0, rm ? 2 : 1, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
-                        c->d_err, q.st));
-    ++q.launches;  // log-sum-exp is two kernels
-    uint32_t m_base = 0;
-    if (rm) {
-        enq_resample(q, 0);
-        for (int b = 0; b < cfg.burn_in_steps; ++b) {
-            unsigned long long* scratch = r.acc + T;
-            if (q.e == cudaSuccess) q.e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), q.st);
-            if (!site) enq_colstats(q, 0);
-            enq_moves(q, 0, m_base, M, scratch);
-            if (mala) q.ck(launch_adapt_lambda(w.lambda, scratch, denom, q.st));
-            m_base += (uint32_t)M;
-        }
-        q.ck(launch_mark_uniform(w.N, 0, r.ess, r.res, w.flag, q.st));
-    }
-    for (int64_t t = 0; t < T; ++t) {
-        if (t > 0) {
-            q.ck(launch_reweight(w.beta, w.logw, w.lpq, w.N, p, c->pr, r.rk, (int)t, c->d_err, q.st));
-            // the previous step's transpose has read beta and the weights (forked runs)
-            if (fork_sum && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_keys, 0);
-            q.ck(launch_lse_ess(wa, w.N, w.lse_scratch, w.lse_counter, (int)t, 0, cfg.ess_frac, r.ess, r.logz, r.res, w.flag,
-                                c->d_err, q.st));
-            ++q.launches;
-        }
-        enq_resample(q, (int)t);
-        if (!site) enq_colstats(q, (int)t);
-        enq_moves(q, (int)t, t == 0 ? m_base : 0u, M, r.acc + t);
-        if (fork_sum) {
-            // The key transpose and the summaries of step t run on the side stream beside step
-            // t + 1. The transpose reads beta and the weights, which step t + 1 first rewrites
-            // in its normalisation (it waits for ev_keys before); it copies the weights for the
-            // summaries, which then read nothing that the main stream writes.
-            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_fork, q.st);
-            if (q.e == cudaSuccess) q.e = cudaStreamWaitEvent(c->side_stream, c->ev_fork, 0);
-            q.ck(launch_keys(w.beta, w.Wf, w.wfix, w.N, p, w.keysT, w.WfS, w.wfixS, false, c->side_stream));
-            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_keys, c->side_stream);
-            q.ck(launch_summaries_keys(w.keysT, w.WfS, w.wfixS, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, false,
-                                       c->side_stream));
-            if (q.e == cudaSuccess) q.e = cudaEventRecord(c->ev_join, c->side_stream);
-        } else {
-            q.ck(launch_summaries(w.beta, w.Wf, w.wfix, w.N, p, sa, (int)t, r.mean, r.quant, r.conc, w.keysT, q.st));
-            ++q.launches;  // the key transpose and the summaries
-        }
-        if (cfg.map_path)
-            q.ck(launch_best_particle(mh_state(c, nullptr), w.beta, w.N, p, c->pr, r.sched, (int)t, r.best, q.st));
-        if (mala) q.ck(launch_adapt_lambda(w.lambda, r.acc + t, denom, q.st));
-    }
-    if (fork_sum && T > 0 && q.e == cudaSuccess) q.e = cudaStreamWaitEvent(q.st, c->ev_join, 0);  // the last summaries
-    q.ck(launch_accept_rate(r.acc, (int)T, denom, r.accrate, q.st));
+    SweepGen gen(c, T, M);
+    LikPoint lp;
+    while (gen.next(q, &lp)) enq_likelihood(q, lp);
     *err_out = q.e;
     return q.launches;
 }
@@ -829,6 +945,18 @@ void destroy(spa_ctx* c)
 }  // namespace
 
 // ------------------------------------------------------------------ batches
+// One grouped likelihood launch of a lock-step batch: the regions whose likelihood kernels
+// share a tile class (n-tile width, resident particle operand), their table and the CTAs'
+// unit ranges, in device memory.
+struct BatchClass {
+    int BN = 0;
+    bool ar = false;
+    int R = 0;
+    int grid = 0;
+    TcRegion* regs = nullptr;
+    int64_t* cta_units = nullptr;
+};
+
 struct spa_batch {
     std::vector<spa_ctx*> ctxs;
     std::vector<uint64_t> gens, seeds;
@@ -838,6 +966,13 @@ struct spa_batch {
     std::vector<cudaEvent_t> joins;
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
+    // lock-step mode: every region stops at each likelihood evaluation, and one grouped launch
+    // per tile class evaluates all regions' particles
+    bool grouped = false;
+    std::vector<BatchClass> classes;
+    std::vector<cudaEvent_t> ev_lik;
+    cudaEvent_t ev_grouped = nullptr;
+    uint32_t* d_err = nullptr;  // the grouped launches' device error word
 };
 
 namespace {
@@ -846,11 +981,178 @@ void batch_free(spa_batch* b)
 {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (BatchClass& k : b->classes) {
+        dfree(k.regs);
+        dfree(k.cta_units);
+    }
+    dfree(b->d_err);
+    for (cudaEvent_t ev : b->ev_lik)
+        if (ev) cudaEventDestroy(ev);
+    if (b->ev_grouped) cudaEventDestroy(b->ev_grouped);
     for (cudaEvent_t ev : b->joins)
         if (ev) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->st) cudaStreamDestroy(b->st);
     delete b;
+}
+
+// Lock-step batching needs every region's sweep to stop at the same likelihood evaluations:
+// the same T, N, M, move kind (random walk or MALA), start and burn-in, all on the tensor
+// cores. SPA_BATCH_MODE=branches keeps the one-branch-per-region graph instead.
+bool batch_lockstep(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args)
+{
+    if (const char* env = std::getenv("SPA_BATCH_MODE"))
+        if (std::strcmp(env, "branches") == 0) return false;
+    if (R < 2) return false;
+    const spa_config& k0 = ctxs[0]->cfg;
+    for (int32_t r = 0; r < R; ++r) {
+        const spa_config& k = ctxs[r]->cfg;
+        if (k.precision != SPA_PREC_SPLIT_BF16 || k.move_kind == SPA_MOVE_SITE) return false;
+        if (k.move_kind != k0.move_kind || k.init_mode != k0.init_mode || k.burn_in_steps != k0.burn_in_steps)
+            return false;
+        if (args->T[r] != args->T[0] || args->N[r] != args->N[0] || args->moves_per_step[r] != args->moves_per_step[0])
+            return false;
+    }
+    return true;
+}
+
+// The grouped launches' tables: regions by tile class, each class's units in region order,
+// and CTA b's units [cta_units[b], cta_units[b + 1]) split by work (a unit of region r costs
+// its kblocks_r k-blocks of the same 128 x BN tile).
+int batch_build_classes(spa_batch* b)
+{
+    const int32_t R = (int32_t)b->ctxs.size();
+    std::map<std::pair<int, bool>, std::vector<int32_t>> by_class;
+    for (int32_t r = 0; r < R; ++r) {
+        const TcPlan plan = plan_of(b->ctxs[r]);
+        by_class[{plan.BN, tc_plan_resident(plan)}].push_back(r);
+    }
+    const bool mala = b->ctxs[0]->cfg.move_kind == SPA_MOVE_MALA;
+    for (const auto& kv : by_class) {
+        BatchClass k;
+        k.BN = kv.first.first;
+        k.ar = kv.first.second;
+        k.R = (int)kv.second.size();
+        std::vector<TcRegion> regs((size_t)k.R);
+        std::vector<double> cum((size_t)k.R + 1, 0.0);
+        int64_t units = 0;
+        for (int i = 0; i < k.R; ++i) {
+            spa_ctx* c = b->ctxs[kv.second[(size_t)i]];
+            const Workspace& w = c->ws;
+            const TcPlan plan = plan_of(c);
+            TcRegion& g = regs[(size_t)i];
+            std::memset(&g, 0, sizeof(g));
+            g.A = w.mapA;
+            g.At = plan.tw ? w.mapAt : w.mapA;
+            g.B = c->mapB;
+            g.Bt = plan.tw ? c->mapBt : c->mapB;
+            g.partial = w.partial;
+            g.ybits = c->ybits;
+            if (mala) {
+                const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
+                g.R = w.R;
+                g.n_r = a.n_r;
+                g.rsum_part = w.rsum;
+            }
+            g.N_pad = w.N_pad;
+            g.unit0 = units;
+            g.tw = plan.tw;
+            g.n_tiles = plan.n_tiles;
+            g.m_tiles = plan.m_tiles;
+            g.kblocks = plan.kblocks;
+            g.ksteps = plan.ksteps;
+            g.Kp = c->Kp;
+            g.n = (int)c->n;
+            const int64_t u_r = (int64_t)plan.m_tiles * plan.n_tiles;
+            units += u_r;
+            cum[(size_t)i + 1] = cum[(size_t)i] + (double)u_r * plan.kblocks;
+        }
+        const int num_sms = b->ctxs[0]->num_sms;
+        k.grid = (int)std::min<int64_t>(units, num_sms);
+        std::vector<int64_t> cu((size_t)k.grid + 1);
+        int i = 0;
+        for (int cb = 0; cb <= k.grid; ++cb) {
+            const double target = cum[(size_t)k.R] * cb / k.grid;
+            while (i < k.R - 1 && cum[(size_t)i + 1] <= target) ++i;
+            const double inside = (target - cum[(size_t)i]) / regs[(size_t)i].kblocks;
+            int64_t u = regs[(size_t)i].unit0 + (int64_t)std::ceil(inside - 1e-9);
+            if (cb == k.grid) u = units;
+            if (cb > 0 && u < cu[(size_t)cb - 1]) u = cu[(size_t)cb - 1];
+            cu[(size_t)cb] = u < units ? u : units;
+        }
+        cudaError_t e = dalloc(&k.regs, regs.size());
+        if (e == cudaSuccess) e = dalloc(&k.cta_units, cu.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(k.regs, regs.data(), sizeof(TcRegion) * regs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(k.cta_units, cu.data(), sizeof(int64_t) * cu.size(), cudaMemcpyHostToDevice);
+        b->classes.push_back(k);
+        if (e != cudaSuccess) {
+            set_thread_error_str(std::string("batch: grouped tables: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA;
+        }
+    }
+    return SPA_OK;
+}
+
+// Capture of a lock-step batch: each region's sweep runs on its own stream up to its next
+// likelihood evaluation; then the batch stream waits for all of them, one grouped launch per
+// tile class evaluates every region's packed particles (in the residual mode on the MALA
+// path), and each region goes on after it (with its adjoint and gradient on the MALA path).
+cudaError_t batch_capture_lockstep(spa_batch* b, const spa_batch_args* args)
+{
+    const int32_t R = (int32_t)b->ctxs.size();
+    const bool mala = b->ctxs[0]->cfg.move_kind == SPA_MOVE_MALA;
+    const uint64_t wait_ns = b->ctxs[0]->wait_ns;
+    std::vector<SweepGen> gens;
+    std::vector<Enq> qs((size_t)R);
+    gens.reserve((size_t)R);
+    for (int32_t r = 0; r < R; ++r) {
+        gens.emplace_back(b->ctxs[r], b->T[r], args->moves_per_step[r]);
+        qs[(size_t)r].c = b->ctxs[r];
+        qs[(size_t)r].st = b->ctxs[r]->stream();
+    }
+    cudaError_t e = cudaSuccess;
+    for (;;) {
+        int stopped = 0;
+        LikPoint lp{};
+        for (int32_t r = 0; r < R; ++r) {
+            LikPoint l{};
+            if (gens[(size_t)r].next(qs[(size_t)r], &l)) {
+                ++stopped;
+                lp = l;
+            }
+            if (qs[(size_t)r].e != cudaSuccess) return qs[(size_t)r].e;
+        }
+        if (stopped == 0) break;
+        if (stopped != R) return cudaErrorInvalidValue;  // the regions' sweeps are not in lock step
+        for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+            e = cudaEventRecord(b->ev_lik[(size_t)r], qs[(size_t)r].st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->ev_lik[(size_t)r], 0);
+        }
+        for (const BatchClass& k : b->classes) {
+            if (e == cudaSuccess)
+                e = launch_loglik_tc_grouped(k.regs, k.R, k.cta_units, k.grid, k.BN, k.ar, mala, b->d_err, b->st,
+                                             wait_ns);
+            ++b->launches;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_grouped, b->st);
+        for (int32_t r = 0; r < R && e == cudaSuccess; ++r) {
+            e = cudaStreamWaitEvent(qs[(size_t)r].st, b->ev_grouped, 0);
+            if (e == cudaSuccess && mala) {
+                Workspace& w = b->ctxs[r]->ws;
+                enq_grad_tail(qs[(size_t)r], lp.init ? w.gl : w.gl_p, lp.init ? w.beta : w.beta_p, 0.0, w.N);
+                e = qs[(size_t)r].e;
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    for (int32_t r = 0; r < R; ++r) {
+        b->per_ctx_launches.push_back(qs[(size_t)r].launches);
+        b->launches += qs[(size_t)r].launches;
+        if (e == cudaSuccess) e = cudaEventRecord(b->joins[(size_t)r], qs[(size_t)r].st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->joins[(size_t)r], 0);
+    }
+    return e;
 }
 
 // Prepare every context (buffers, schedule, seed), then capture all sweeps into one graph:
@@ -900,19 +1202,36 @@ int batch_build(spa_batch* b, spa_ctx* const* ctxs, int32_t R, const spa_batch_a
     b->joins.assign((size_t)R, nullptr);
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r) e = cudaEventCreateWithFlags(&b->joins[r], cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_err(e, "stream and events");
+    b->grouped = batch_lockstep(ctxs, R, args);
+    if (b->grouped) {
+        b->ev_lik.assign((size_t)R, nullptr);
+        for (int32_t r = 0; r < R && e == cudaSuccess; ++r)
+            e = cudaEventCreateWithFlags(&b->ev_lik[(size_t)r], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_grouped, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = dalloc(&b->d_err, 1);
+        if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_err(e, "lock-step events");
+        const int rc = batch_build_classes(b);
+        if (rc != SPA_OK) return rc;
+    }
     e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_err(e, "begin capture");
     cudaError_t ee = cudaEventRecord(b->fork, b->st);
     b->launches = 0;
-    for (int32_t r = 0; r < R && ee == cudaSuccess; ++r) {
-        spa_ctx* c = b->ctxs[r];
-        ee = cudaStreamWaitEvent(c->stream(), b->fork, 0);
-        if (ee != cudaSuccess) break;
-        const int64_t n = enqueue_sweep(c, b->T[r], args->moves_per_step[r], &ee);
-        b->per_ctx_launches.push_back(n);
-        b->launches += n;
-        if (ee == cudaSuccess) ee = cudaEventRecord(b->joins[r], c->stream());
-        if (ee == cudaSuccess) ee = cudaStreamWaitEvent(b->st, b->joins[r], 0);
+    if (b->grouped) {
+        for (int32_t r = 0; r < R && ee == cudaSuccess; ++r) ee = cudaStreamWaitEvent(b->ctxs[r]->stream(), b->fork, 0);
+        if (ee == cudaSuccess) ee = batch_capture_lockstep(b, args);
+    } else {
+        for (int32_t r = 0; r < R && ee == cudaSuccess; ++r) {
+            spa_ctx* c = b->ctxs[r];
+            ee = cudaStreamWaitEvent(c->stream(), b->fork, 0);
+            if (ee != cudaSuccess) break;
+            const int64_t n = enqueue_sweep(c, b->T[r], args->moves_per_step[r], &ee);
+            b->per_ctx_launches.push_back(n);
+            b->launches += n;
+            if (ee == cudaSuccess) ee = cudaEventRecord(b->joins[r], c->stream());
+            if (ee == cudaSuccess) ee = cudaStreamWaitEvent(b->st, b->joins[r], 0);
+        }
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(b->st, &g);
@@ -1217,6 +1536,7 @@ int spa_batch_run(spa_batch* b, const uint64_t* seeds, spa_result* outs)
         for (int32_t r = 0; r < R; ++r) b->seeds[r] = seeds[r];
     cudaStream_t st = b->st;
     cudaError_t e = cudaSuccess;
+    if (b->d_err) e = cudaMemsetAsync(b->d_err, 0, sizeof(uint32_t), st);
     for (int32_t r = 0; r < R && e == cudaSuccess; ++r)
         e = cudaMemcpyAsync(b->ctxs[r]->rb.seed, &b->seeds[r], sizeof(uint64_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st);
@@ -1237,9 +1557,17 @@ int spa_batch_run(spa_batch* b, const uint64_t* seeds, spa_result* outs)
         d2h(o->accept_rate, rb.accrate, sizeof(double) * (size_t)T);
         d2h(o->resampled, rb.res, (size_t)T);
     }
+    uint32_t grouped_err = 0;
+    if (b->d_err && e == cudaSuccess)
+        e = cudaMemcpyAsync(&grouped_err, b->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return fail(nullptr, e == cudaErrorMemoryAllocation ? SPA_ENOMEM : SPA_ECUDA,
                                       std::string("batch run: ") + cudaGetErrorString(e));
+    if (grouped_err) {
+        const int rc = map_device_error(nullptr, grouped_err);
+        set_thread_error_str(std::string("grouped likelihood launches: ") + g_thread_error);
+        return rc;
+    }
     for (int32_t r = 0; r < R; ++r) {
         spa_ctx* c = b->ctxs[r];
         c->last_launches = b->per_ctx_launches[r];
@@ -1313,6 +1641,21 @@ int spa_loglik_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
             CK(launch_loglik_simt(w.beta_p, c->Xf, c->y, N, c->n, (int)c->p, w.partial, w.N_pad, st), "loglik simt");
         }
     }
+    return SPA_OK;
+}
+
+int spa_grad_repeat(spa_ctx* c, int64_t N, int32_t reps, void* stream)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (c->ws.N != N || N < 1 || reps < 0) return fail(c, SPA_EINVAL, "no workspace of N particles");
+    if (c->cfg.precision != SPA_PREC_SPLIT_BF16 || c->cfg.move_kind != SPA_MOVE_MALA || !c->ws.R)
+        return fail(c, SPA_EINVAL, "no split-BF16 MALA workspace (run a MALA sweep of N particles first)");
+    Enq q;
+    q.c = c;
+    q.st = stream ? static_cast<cudaStream_t>(stream) : c->stream();
+    Workspace& w = c->ws;
+    for (int32_t k = 0; k < reps && q.e == cudaSuccess; ++k) enq_grad_tc(q, w.gl_p, w.beta_p, 0.0, w.N);
+    if (q.e != cudaSuccess) return cuda_fail(c, q.e, "gradient kernels");
     return SPA_OK;
 }
 

@@ -95,6 +95,8 @@ struct MoveArgs {
     float2* lpt_p;
     float2* ydq;
     const float* sigma;          // RW: per-coordinate step; MALA: D_j
+    const float* sqrt_D;         // MALA: sqrt(D_j) and 1/D_j (written beside D_j)
+    const float* inv_D;
     const float* l2e_over_s;
     const float* mean_f;
     const float* vy;             // v_j in partial units (y . eta = beta . v)
@@ -183,7 +185,8 @@ cudaError_t launch_copyback(float* beta, const float* beta_tmp, float2* llq, flo
                             const int* flag, cudaStream_t st);
 
 // Weighted column moments -> per-coordinate proposal scales. kind 0 (RW):
-// sigma_j = lam/sqrt(p) max(sd_j, floor c); kind 1 (MALA): D_j = max(var_j, (floor c)^2).
+// sigma_j = lam/sqrt(p) max(sd_j, floor c) into scale_out [p]; kind 1 (MALA):
+// D_j = max(var_j, (floor c)^2), sqrt(D_j) and 1/D_j into scale_out [3p].
 constexpr int COLSTAT_SPLITS = 128;
 // With lam_dev (MALA) it also writes h = lambda p^{-1/6} to h_out.
 cudaError_t launch_colstats(const float* beta, const float* Wf, int64_t N, int p, float4* part, float* scale_out,
@@ -310,6 +313,27 @@ struct ResidArgs {
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp, const uint32_t* ybits,
                              float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
                              const ResidArgs* resid = nullptr, uint64_t wait_ns = 0, int stall = 0);
+
+// One region's entry in a grouped likelihood launch (many regions' units in one persistent
+// launch). The table lives in device memory; CUtensorMap is aligned to 64 bytes or more, so
+// every entry and each of its maps keeps that alignment.
+struct TcRegion {
+    CUtensorMap A, B, At, Bt;  // as TcMaps, for this region's buffers and its plan's BN
+    float* partial;            // [n_parts][N_pad] softplus partials
+    const uint32_t* ybits;
+    __nv_bfloat16* R;          // residual mode: [N_pad][2 n_r]
+    float* rsum_part;
+    int64_t N_pad, n_r;
+    int64_t unit0;             // global index of the region's first unit
+    int tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n;
+};
+// Units of region r: m_tiles x n_tiles in row-major order, global indices from unit0. CTA b
+// of `grid` takes the global units [cta_units[b], cta_units[b + 1]). All regions of one launch
+// share BN (128 or 256), the residual mode and the A-resident mode (kblocks <= 4).
+cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int BN, bool ar,
+                                     bool resid, uint32_t* err, cudaStream_t st, uint64_t wait_ns = 0);
+// Whether a plan's particle operand stays resident in shared memory (K <= 256).
+bool tc_plan_resident(const TcPlan& plan);
 
 // The adjoint's second half: C = R G (tcgen05, split-BF16 R, exact G^T [p][n_r]) into
 // gpart[ksplit][N_pad][p], then grad l = (sum C - m_j sum r) / s_j (+ prior gradient).

@@ -91,3 +91,44 @@ def test_batch_argument_errors(spa):
     finally:
         for r in regs:
             r.close()
+
+
+# Regions that share T, N, M and the move kind run in lock step: every likelihood evaluation
+# of all regions is one grouped launch per tile class (n-tile width, resident particle operand
+# or not). Uneven n and p, p on both sides of the resident limit (K <= 256).
+LOCKSTEP = [(300, 7, 1.0), (1200, 64, 2.0), (2000, 130, 4.0), (1000, 300, float("inf")), (700, 33, 16.0),
+            (500, 260, 1.0)]
+
+
+@pytest.mark.parametrize("move", ["rw", "mala"])
+def test_lockstep_batch_matches_individual_runs(spa, move, monkeypatch):
+    regs = []
+    for k, (n, p, nu) in enumerate(LOCKSTEP):
+        g = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=800 + k)
+        regs.append(spa.Region(g.G, g.y, nu, config=spa.make_config(move=move)))
+    R = len(regs)
+    sched = synth.geometric_schedule(5)
+    N, M = 512, 2
+    try:
+        b = spa.Batch(regs, [sched] * R, [N] * R, [M] * R, list(range(31, 31 + R)))
+        first = b.run()
+        second = b.run(seeds=list(range(41, 41 + R)))
+        n_lock = b.launch_count()
+        b.close()
+        monkeypatch.setenv("SPA_BATCH_MODE", "branches")
+        bb = spa.Batch(regs, [sched] * R, [N] * R, [M] * R, list(range(31, 31 + R)))
+        branch = bb.run()
+        n_branch = bb.launch_count()
+        bb.close()
+        # one grouped launch per tile class replaces R likelihood launches per evaluation
+        assert n_lock < n_branch
+        for k, r in enumerate(regs):
+            for seed, outs in ((31 + k, first), (41 + k, second)):
+                ind = r.run(sched, N, M, seed)
+                for key in ind:
+                    assert np.array_equal(ind[key], outs[k][key]), (k, seed, key)
+            for key in branch[k]:
+                assert np.array_equal(branch[k][key], first[k][key]), (k, key)
+    finally:
+        for r in regs:
+            r.close()
