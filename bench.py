@@ -627,6 +627,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ess-frac", type=float, default=0.75,
+                    help="resample when ESS < ess_frac * N (1.0 resamples at every step; for profiling the resampling kernels)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the compact split-large / mala / batched / matched-error keys of the default line")
     ap.add_argument("--matched-error", action="store_true",
@@ -677,7 +679,8 @@ def main():
     torch.cuda.set_stream(stream)
     assert stream.cuda_stream != 0
     init = dict(init="resample_move", burn_in_steps=w["burn_in"]) if w.get("burn_in") else {}
-    cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream, **init)
+    cfg = spa.make_config(move=w["move"], precision=args.precision, stream=stream.cuda_stream,
+                          ess_frac=args.ess_frac, **init)
     reg = spa.Region(region.G, region.y, w["nu"], config=cfg)
     T, p = w["T"], w["p"]
     out_d = out_buffers(dev, T, p)

@@ -367,6 +367,10 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
             int epoch = -1;         // A-resident: one epoch per run of units with the same key
             int64_t cur_key = -1;
             int a_issued = 0;       // k-blocks of the current epoch's A sent out
+            // bit kb: the parity of AFULL(kb)'s current phase. Each barrier keeps its own phase,
+            // because regions of one grouped launch can have different numbers of k-blocks,
+            // so not every epoch uses every AFULL(kb).
+            uint32_t a_par = 0;
             for (int64_t u = u_begin; u < u_end && ok; ++u) {
                 const TcUnit t = src.unit(u);
                 const int kb_last = t.kblocks - 1;
@@ -396,6 +400,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                         mbar_arrive_expect_tx(AFULL_BAR(kb), tail ? 2u * a_tail : 2u * (uint32_t)C::A_TILE);
                         tma_load_2d(a, ma, AFULL_BAR(kb), kb * BK, t.mt * BM);
                         tma_load_2d(a + C::A_TILE, ma, AFULL_BAR(kb), t.Kp + kb * BK, t.mt * BM);
+                        a_par ^= 1u << kb;
                         ++a_issued;
                     }
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
@@ -427,9 +432,8 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const uint32_t i2 = it - k;
                 mbar_drain(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err);
             }
-            if (AR && epoch >= 0)
-                for (int kb = 0; kb < a_issued; ++kb)
-                    mbar_drain(AFULL_BAR(kb), (uint32_t)(epoch & 1), err);
+            if (AR && epoch >= 0)  // the phases last armed (their parity bits were flipped since)
+                for (int kb = 0; kb < a_issued; ++kb) mbar_drain(AFULL_BAR(kb), ((a_par >> kb) & 1u) ^ 1u, err);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------- MMA issuer
@@ -438,8 +442,8 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
             uint32_t it = 0;
             int lt = 0;
             bool ok = true;
-            int epoch = -1;
             int64_t cur_key = -1;
+            uint32_t a_par = 0;  // bit kb: the parity of AFULL(kb)'s phase to wait for next
             // Injected stall (tests of the timeout path): wait first on the drain barrier,
             // which nothing arrives at before this thread's own final commit, so the wait
             // runs out after wait_ns; no MMA has been issued, and the other roles give up and
@@ -456,7 +460,6 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 }
                 bool a_first = false;  // the epoch's first unit waits for each k-block of A
                 if (AR && t.key != cur_key) {
-                    ++epoch;
                     a_first = true;
                     cur_key = t.key;
                 }
@@ -464,9 +467,12 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
                 for (int kb = 0; kb < t.kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                    if (AR && a_first && !mbar_wait_bounded(AFULL_BAR(kb), (uint32_t)(epoch & 1), err, wait_ns)) {
-                        ok = false;
-                        break;
+                    if (AR && a_first) {
+                        if (!mbar_wait_bounded(AFULL_BAR(kb), (a_par >> kb) & 1u, err, wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        a_par ^= 1u << kb;
                     }
                     if (!mbar_wait_bounded(FULL_BAR(s), ph, err, wait_ns)) {
                         ok = false;

@@ -755,20 +755,58 @@ __global__ void k_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* res_o
 }
 
 // ------------------------------------------------------------ systematic resampling
-constexpr int RS_THREADS = 1024;
-constexpr int RS_BLOCK = 256;  // cumulative-sum block of the specified association order
-
 // The cumulative sum C of W in the specified order: a running sum inside each 256-block
-// in index order, a running sum of the block totals, C_i = carry(block) + local_i.
-// cum holds N + ceil(N/256) + 1 doubles: C, then one carry per block, then u. Block totals
-// pass through shared memory (RS_TOT at a time), so the sequential carry sum reads no
-// global memory.
-constexpr int RS_TOT = 4096;
+// in index order, a running sum of the block totals, C_i = carry(block) + local_i. cum holds
+// N + ceil(N/256) + 1 doubles: the block-local running sums, then one carry per block, then u.
+// Three kernels spread it over the SMs: the local sums (16 blocks of 256 per CTA, staged in
+// shared memory with coalesced loads and stores; lane l of warp 0 runs block l's additions),
+// the carries (one thread, in block order), and the search, which forms C_i = carry + local_i
+// as it reads it. The association order, and so every bit of C, is that of the definition.
+constexpr int RS_BLOCK = 256;         // cumulative-sum block of the specified association order
+constexpr int RS_CHUNKS = 16;         // 256-blocks per CTA of the local pass (33 KB of shared memory)
+constexpr int RS_PAD = RS_BLOCK + 1;  // shared-memory row of one 256-block (odd stride: no bank conflicts)
+constexpr int RS_LOCAL_THREADS = 256;
+constexpr size_t RS_LOCAL_SMEM = sizeof(double) * RS_CHUNKS * RS_PAD;
+constexpr int RS_CARRY_THREADS = 1024;
+constexpr int RS_TOT = 4096;  // block totals staged per pass of the carry kernel
 
-__global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __restrict__ W, int64_t N,
-                                                               double* __restrict__ cum, const int* __restrict__ flag,
-                                                               int t, const uint64_t* __restrict__ seedp,
-                                                               double u_override)
+__global__ void __launch_bounds__(RS_LOCAL_THREADS) k_resample_local(const double* __restrict__ W, int64_t N,
+                                                                     double* __restrict__ cum,
+                                                                     const int* __restrict__ flag)
+{
+    grid_dependency_wait();
+    if (flag && *flag == 0) return;
+    extern __shared__ double rs_sm[];
+    const int64_t i0 = (int64_t)blockIdx.x * RS_CHUNKS * RS_BLOCK;
+    const int64_t len = (N - i0 < (int64_t)RS_CHUNKS * RS_BLOCK) ? N - i0 : (int64_t)RS_CHUNKS * RS_BLOCK;
+    for (int64_t e = threadIdx.x; e < len; e += RS_LOCAL_THREADS)
+        rs_sm[(e / RS_BLOCK) * RS_PAD + (e % RS_BLOCK)] = W[i0 + e];
+    __syncthreads();
+    if (threadIdx.x < RS_CHUNKS) {
+        const int c = threadIdx.x;
+        const int64_t c0 = (int64_t)c * RS_BLOCK;
+        if (c0 < len) {
+            const int cl = (len - c0 < RS_BLOCK) ? (int)(len - c0) : RS_BLOCK;
+            double* row = rs_sm + c * RS_PAD;
+            double local = 0.0;
+            for (int k = 0; k < cl; ++k) {
+                local = __dadd_rn(local, row[k]);
+                row[k] = local;
+            }
+            // the block total, turned into the block's carry by k_resample_carry
+            cum[N + (i0 / RS_BLOCK) + c] = local;
+        }
+    }
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < len; e += RS_LOCAL_THREADS) cum[i0 + e] = rs_sm[(e / RS_BLOCK) * RS_PAD + (e % RS_BLOCK)];
+}
+
+// carry[b] = total_0 + ... + total_{b-1} in block order (the totals are read from the carry
+// slots and replaced), then the resampling uniform after the carries.
+__global__ void __launch_bounds__(RS_CARRY_THREADS) k_resample_carry(int64_t N, double* __restrict__ cum,
+                                                                     const int* __restrict__ flag, int t,
+                                                                     const uint64_t* __restrict__ seedp,
+                                                                     double u_override)
 {
     grid_dependency_wait();
     if (flag && *flag == 0) return;
@@ -779,26 +817,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __re
     double run = 0.0;  // thread 0's running sum of block totals
     for (int64_t b0 = 0; b0 < nblk; b0 += RS_TOT) {
         const int64_t b1 = (b0 + RS_TOT < nblk) ? b0 + RS_TOT : nblk;
-        for (int64_t b = b0 + tid; b < b1; b += RS_THREADS) {
-            const int64_t i0 = b * RS_BLOCK, i1 = (i0 + RS_BLOCK < N) ? i0 + RS_BLOCK : N;
-            double local = 0.0;
-            int64_t i = i0;
-            for (; i + 8 <= i1; i += 8) {  // loads ahead of the dependent additions
-                double w[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) w[k] = W[i + k];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    local = __dadd_rn(local, w[k]);
-                    cum[i + k] = local;
-                }
-            }
-            for (; i < i1; ++i) {
-                local = __dadd_rn(local, W[i]);
-                cum[i] = local;
-            }
-            tot[b - b0] = local;
-        }
+        for (int64_t b = b0 + tid; b < b1; b += RS_CARRY_THREADS) tot[b - b0] = carry[b];
         __syncthreads();
         if (tid == 0)
             for (int64_t b = b0; b < b1; ++b) {
@@ -815,13 +834,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_resample_scan(const double* __re
             carry[nblk] = u_override;
         }
     }
-    __syncthreads();
-    for (int64_t e = RS_BLOCK + tid; e < N; e += RS_THREADS) cum[e] = __dadd_rn(carry[e / RS_BLOCK], cum[e]);
 }
 
-// A_k = min{i : C_i > (k + u)/N}, clamped to N - 1. C is non-negative and non-decreasing,
-// and for non-negative doubles the order of the bit patterns as signed integers is the
-// numeric order, so the search compares integers.
+// A_k = min{i : C_i > (k + u)/N}, clamped to N - 1, with C_i = carry(i / 256) + local_i (the
+// first block's carry is 0 and its C_i is local_i, as in the definition). C is non-negative
+// and non-decreasing, and for non-negative doubles the order of the bit patterns as signed
+// integers is the numeric order, so the search compares integers.
+__device__ __forceinline__ long long resample_c_bits(const double* __restrict__ cum, int64_t N, int64_t i)
+{
+    const double c = (i < RS_BLOCK) ? cum[i] : __dadd_rn(cum[N + i / RS_BLOCK], cum[i]);
+    return __double_as_longlong(c);
+}
+
 __global__ void k_resample_search(const double* __restrict__ cum, int64_t N, int32_t* __restrict__ idx,
                                   const int* __restrict__ flag)
 {
@@ -829,13 +853,12 @@ __global__ void k_resample_search(const double* __restrict__ cum, int64_t N, int
     if (flag && *flag == 0) return;
     const int64_t nblk = (N + RS_BLOCK - 1) / RS_BLOCK;
     const double u = cum[N + nblk];
-    const long long* ci = reinterpret_cast<const long long*>(cum);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
         const long long target = __double_as_longlong(__ddiv_rn(__dadd_rn((double)k, u), (double)N));
         int64_t lo = 0, hi = N;
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (ci[mid] > target)
+            if (resample_c_bits(cum, N, mid) > target)
                 hi = mid;
             else
                 lo = mid + 1;
@@ -1558,10 +1581,16 @@ cudaError_t launch_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* resa
 cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32_t* idx, const int* flag, int t,
                                   const uint64_t* seed, double u_override, cudaStream_t st)
 {
-    { const cudaError_t e_ = launch_pdl(k_resample_scan, dim3(1), dim3(RS_THREADS), (size_t)(0), st, W, N, cum, flag, t, seed, u_override); if (e_ != cudaSuccess) return e_; }
-    cudaError_t e = cudaGetLastError();
+    const int64_t chunks = (N + RS_BLOCK - 1) / RS_BLOCK;
+    const unsigned local_grid = (unsigned)((chunks + RS_CHUNKS - 1) / RS_CHUNKS);
+    cudaError_t e = launch_pdl(k_resample_local, dim3(local_grid), dim3(RS_LOCAL_THREADS), RS_LOCAL_SMEM, st, W, N, cum,
+                               flag);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_resample_carry, dim3(1), dim3(RS_CARRY_THREADS), (size_t)0, st, N, cum, flag, t, seed,
+                       u_override);
+    if (e == cudaSuccess)
+        e = launch_pdl(k_resample_search, dim3(elem_grid(N)), dim3(256), (size_t)0, st, cum, N, idx, flag);
     if (e != cudaSuccess) return e;
-    { const cudaError_t e_ = launch_pdl(k_resample_search, dim3(elem_grid(N)), dim3(256), (size_t)(0), st, cum, N, idx, flag); if (e_ != cudaSuccess) return e_; }
     return cudaGetLastError();
 }
 

@@ -172,9 +172,10 @@ cudaError_t launch_weight_forms(const double* W, int64_t N, float* Wf, uint32_t*
 
 cudaError_t launch_mark_uniform(int64_t N, int t, double* ess_out, uint8_t* resampled_out, int* flag, cudaStream_t st);
 
-// Systematic resampling: ancestor indices (bit-exact blocked cumulative sum, then a parallel
-// binary search), gather of particle rows into scratch and copy back. All no-ops when
-// *flag == 0. cum holds N + ceil(N/256) + 1 doubles.
+// Systematic resampling: ancestor indices (bit-exact blocked cumulative sum: block-local sums
+// over the SMs, the carries in block order, then a parallel binary search that adds them),
+// gather of particle rows into scratch and copy back. All no-ops when *flag == 0. cum holds
+// N + ceil(N/256) + 1 doubles (local sums, carries, u).
 cudaError_t launch_resample_index(const double* W, int64_t N, double* cum, int32_t* idx, const int* flag,
                                   int t, const uint64_t* seed, double u_override, cudaStream_t st);
 cudaError_t launch_gather(const int32_t* idx, const float* beta, float* beta_tmp, const float2* llq, const float2* lpq,

@@ -93,15 +93,17 @@ def test_batch_argument_errors(spa):
             r.close()
 
 
-# Regions that share T, N, M and the move kind run in lock step: every likelihood evaluation
-# of all regions is one grouped launch per tile class (n-tile width, resident particle operand
-# or not). Uneven n and p, p on both sides of the resident limit (K <= 256).
+# Regions that share T, N, M and the move kind can run in lock step (SPA_BATCH_MODE=lockstep):
+# every likelihood evaluation of all regions is one grouped launch per tile class (n-tile width,
+# resident particle operand or not). Uneven n and p, p on both sides of the resident limit
+# (K <= 256).
 LOCKSTEP = [(300, 7, 1.0), (1200, 64, 2.0), (2000, 130, 4.0), (1000, 300, float("inf")), (700, 33, 16.0),
             (500, 260, 1.0)]
 
 
 @pytest.mark.parametrize("move", ["rw", "mala"])
 def test_lockstep_batch_matches_individual_runs(spa, move, monkeypatch):
+    monkeypatch.setenv("SPA_BATCH_MODE", "lockstep")
     regs = []
     for k, (n, p, nu) in enumerate(LOCKSTEP):
         g = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=800 + k)
