@@ -341,9 +341,11 @@ def loglik_roofline(reg, w, args, stream):
         peak, peak_src = fp32_simt_peak()
         bound = "alu"
         kernel = "k_eta_tile"
+    cfg, src = reg.tile_config()
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": profile_traffic(args.workload) if bound == "tensor" else None,
                 "kernel": kernel, "tile_bn": reg.loglik_tile_width(),
+                "tile_config": cfg, "tile_source": {0: "fixed", 1: "table", 2: "timed"}.get(src),
                 "launch_ms": kern_ms, "peak_source": peak_src,
                 "algorithmic_flop_per_launch": flop}
     return roofline

@@ -219,11 +219,26 @@ int64_t spa_last_launch_count(const spa_ctx* ctx);
 int spa_set_wait_limit(spa_ctx* ctx, uint64_t limit_ns);
 
 /* Individuals per n-tile (128 or 256) of the tensor-core likelihood kernel for the
- * context's current workspace, or 0 before the first run. The library times both widths
- * once per shape (device, N, n, p) and keeps the faster; the environment variable
- * SPA_LOGLIK_BN=128|256, read when a workspace is created, fixes it instead. The width
- * does not change any result (partial sums are per 32 individuals either way). */
+ * context's current workspace (its tile configuration's, below), or 0 before the first run.
+ * The environment variable SPA_LOGLIK_BN=128|256, read when a workspace is created, fixes
+ * it. The width does not change any result (partial sums are per 32 individuals either way). */
 int spa_loglik_tile_width(const spa_ctx* ctx);
+
+/* The likelihood kernel's tile configuration for the context's current workspace (-1 before
+ * the first run), and where it came from (*source, may be NULL): 0 fixed (the environment,
+ * spa_set_tile_config, or n <= 128), 1 the tile table, 2 timed by the tuner. Configurations:
+ *   0: n-tiles of 256, 3 G stages, 16 epilogue warps   1: 128, 4 stages, 16 warps
+ *   2: 256, 3 stages, 8 warps                          3: 128, 6 stages, 16 warps (p <= 255)
+ * A shape takes SPA_TILE_CONFIG=0..3 (or SPA_LOGLIK_BN) from the environment, else the value
+ * fixed by spa_set_tile_config, else the nearest shape of the tile table (a JSON file written
+ * by the package's tune_tiles.py on a GB300: SPA_TILE_TABLE, else tuning/loglik_tiles.json
+ * beside the package), else the tuner times every valid configuration once per process. No
+ * configuration changes any result: the partial sums are per 32 individuals whatever the tile. */
+int spa_loglik_tile_config(const spa_ctx* ctx, int32_t* source);
+/* Fix the tile configuration (0..3; -1 returns to the table and tuner) for later runs of the
+ * context: it replaces the context's workspace and captured graph. An invalid configuration
+ * for the shape (3 with p > 255) is ignored at the next run. SPA_EINVAL if out of range. */
+int spa_set_tile_config(spa_ctx* ctx, int32_t cfg);
 
 /* Enqueue `reps` launches of the context's likelihood kernel (split-BF16 tcgen05 or
  * FP32 SIMT, per the configuration) on `stream` over the particles last packed for

@@ -86,6 +86,8 @@ _SIGS = {
     "spa_last_launch_count": (C.c_int64, [C.c_void_p]),
     "spa_set_wait_limit": (C.c_int, [C.c_void_p, C.c_uint64]),
     "spa_loglik_tile_width": (C.c_int, [C.c_void_p]),
+    "spa_loglik_tile_config": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "spa_set_tile_config": (C.c_int, [C.c_void_p, C.c_int32]),
     "spa_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32, C.c_double, C.c_void_p,
                           C.c_void_p]),
     "spa_map_path": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
@@ -306,6 +308,16 @@ class Region:
     def loglik_tile_width(self) -> int:
         """n-tile width of the tensor-core likelihood kernel (0 before the first run)."""
         return int(load().spa_loglik_tile_width(self._h))
+
+    def tile_config(self):
+        """(configuration 0..3 or -1 before the first run, source: 0 fixed, 1 table, 2 timed)."""
+        src = C.c_int32(0)
+        cfg = int(load().spa_loglik_tile_config(self._h, C.byref(src)))
+        return cfg, int(src.value)
+
+    def set_tile_config(self, cfg: int):
+        """Fix the likelihood kernel's tile configuration (-1: the table and tuner decide)."""
+        _check(load().spa_set_tile_config(self._h, int(cfg)), self._h)
 
     def loglik_repeat(self, N: int, reps: int, stream: int = 0):
         _check(load().spa_loglik_repeat(self._h, int(N), int(reps), stream or None), self._h)

@@ -30,11 +30,12 @@ namespace {
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // BF16 per 128-byte swizzle row
-// epilogue warps: 16 for the log-likelihood (4 per TMEM lane quadrant, to hide the SFU and
-// TMEM latencies), 8 for the residual variant, whose per-chunk state is larger
-template <bool RESID>
+// epilogue warps EW: 16 or 8 for the log-likelihood (the tile configuration's choice; 4 per
+// TMEM lane quadrant hide the SFU and TMEM latencies best on most shapes), 8 for the residual
+// variant, whose per-chunk state is larger
+template <int EW>
 struct Epi {
-    static constexpr int WARPS = RESID ? 8 : 16;
+    static constexpr int WARPS = EW;
     static constexpr int THREADS = 64 + 32 * WARPS;
     static constexpr int GROUPS = WARPS / 4;  // column groups per tile
 };
@@ -305,7 +306,7 @@ struct TcGroupedSource {
 };
 
 // The pipeline of one CTA over units [u_begin, u_end) of `src`.
-template <int BN, int STAGES, bool RESID, bool AR, class Src>
+template <int BN, int STAGES, bool RESID, bool AR, int EW, class Src>
 __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restrict__ err, uint64_t wait_ns, int stall)
 {
     using C = TcCfg<BN, STAGES, AR>;
@@ -336,7 +337,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(ACCF_BAR(b), 1);
-            mbar_init(ACCE_BAR(b), Epi<RESID>::WARPS);
+            mbar_init(ACCE_BAR(b), Epi<EW>::WARPS);
         }
         mbar_init(drain_bar, 1);
         mbar_init(aempty_bar, 1);
@@ -504,7 +505,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
         }
     } else {
         // --------------------------------------------------------------- epilogue
-        using E = Epi<RESID>;
+        using E = Epi<EW>;
         constexpr int CPW = BN / 32 / E::GROUPS;  // 32-column chunks per warp and tile
         const int quad = warp & 3;                // TMEM lane quadrant this warp may access
         const int grp = (warp - 2) >> 2;          // column group
@@ -575,8 +576,8 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
     }
 }
 
-template <int BN, int STAGES, bool RESID, bool AR>
-__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
+template <int BN, int STAGES, bool RESID, bool AR, int EW>
+__global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                 const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt, int tw,
                 int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
@@ -586,18 +587,18 @@ __global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
 {
     const TcSingleSource src{&mapA, &mapB, &mapAt, &mapBt, tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n,
                              partial, N_pad, ybits, R, n_r, rsum_part};
-    loglik_tc_body<BN, STAGES, RESID, AR>(src, err, wait_ns, stall);
+    loglik_tc_body<BN, STAGES, RESID, AR, EW>(src, err, wait_ns, stall);
 }
 
 // The same pipeline over the units of many regions (a batched sweep's move): region tables
 // and per-CTA unit ranges in global memory.
-template <int BN, int STAGES, bool RESID, bool AR>
-__global__ void __launch_bounds__(Epi<RESID>::THREADS, 1)
+template <int BN, int STAGES, bool RESID, bool AR, int EW>
+__global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
     k_loglik_tc_grouped(const TcRegion* __restrict__ regs, int R, const int64_t* __restrict__ cta_units,
                         uint32_t* __restrict__ err, uint64_t wait_ns)
 {
     const TcGroupedSource src{regs, R, cta_units};
-    loglik_tc_body<BN, STAGES, RESID, AR>(src, err, wait_ns, 0);
+    loglik_tc_body<BN, STAGES, RESID, AR, EW>(src, err, wait_ns, 0);
 }
 
 // ----------------------------------------------------------------------- adjoint
@@ -833,7 +834,7 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool RESID, bool AR>
+template <int BN, int STAGES, bool RESID, bool AR, int EW>
 cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
                       uint64_t wait_ns, int stall, cudaStream_t st)
@@ -843,7 +844,7 @@ cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
     // overlaps the previous kernel's tail; the kernel waits for it before touching data
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(plan.grid);
-    cfg.blockDim = dim3(Epi<RESID>::THREADS);
+    cfg.blockDim = dim3(Epi<EW>::THREADS);
     cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -852,7 +853,7 @@ cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const bool tail = plan.tw != 0;
-    return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
+    return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR, EW>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
                               plan.tw, plan.n_tiles, plan.m_tiles,
                               plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
                               ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr, wait_ns, stall);
@@ -865,32 +866,36 @@ cudaError_t tc_init_attributes()
     cudaError_t e = cudaSuccess;
 #define SET_SMEM(kern, bytes) \
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-    SET_SMEM((k_loglik_tc<256, 3, false, false>), (TcCfg<256, 3, false>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, false, false>), (TcCfg<128, 4, false>::SMEM));
-    SET_SMEM((k_loglik_tc<256, 3, true, false>), (TcCfg<256, 3, false>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, true, false>), (TcCfg<128, 4, false>::SMEM));
-    SET_SMEM((k_loglik_tc<256, 3, false, true>), (TcCfg<256, 3, true>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, false, true>), (TcCfg<128, 4, true>::SMEM));
-    SET_SMEM((k_loglik_tc<256, 3, true, true>), (TcCfg<256, 3, true>::SMEM));
-    SET_SMEM((k_loglik_tc<128, 4, true, true>), (TcCfg<128, 4, true>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<256, 3, false, false>), (TcCfg<256, 3, false>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<128, 4, false, false>), (TcCfg<128, 4, false>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<256, 3, true, false>), (TcCfg<256, 3, false>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<128, 4, true, false>), (TcCfg<128, 4, false>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<256, 3, false, true>), (TcCfg<256, 3, true>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<128, 4, false, true>), (TcCfg<128, 4, true>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<256, 3, true, true>), (TcCfg<256, 3, true>::SMEM));
-    SET_SMEM((k_loglik_tc_grouped<128, 4, true, true>), (TcCfg<128, 4, true>::SMEM));
+#define SET_TC(BN_, S_, R_, AR_, EW_)                                                          \
+    SET_SMEM((k_loglik_tc<BN_, S_, R_, AR_, EW_>), (TcCfg<BN_, S_, AR_>::SMEM));                \
+    SET_SMEM((k_loglik_tc_grouped<BN_, S_, R_, AR_, EW_>), (TcCfg<BN_, S_, AR_>::SMEM))
+    SET_TC(256, 3, false, true, 16);
+    SET_TC(256, 3, false, false, 16);
+    SET_TC(128, 4, false, true, 16);
+    SET_TC(128, 4, false, false, 16);
+    SET_TC(256, 3, false, true, 8);
+    SET_TC(256, 3, false, false, 8);
+    SET_TC(128, 6, false, true, 16);
+    SET_TC(256, 3, true, true, 8);
+    SET_TC(256, 3, true, false, 8);
+    SET_TC(128, 4, true, true, 8);
+    SET_TC(128, 4, true, false, 8);
+#undef SET_TC
     SET_SMEM((k_adjoint_tc<ADJ_BN_SMALL, 3>), (AdjCfg<ADJ_BN_SMALL, 3>::SMEM));
     SET_SMEM((k_adjoint_tc<256, 3>), (AdjCfg<256, 3>::SMEM));
 #undef SET_SMEM
     return e;
 }
 
-TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN)
+int tc_config_bn(int cfg) { return (cfg == 1 || cfg == 3) ? 128 : 256; }
+
+bool tc_config_valid(int cfg, bool resident) { return cfg >= 0 && cfg < TC_CONFIGS && (cfg != 3 || resident); }
+
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int cfg)
 {
     TcPlan pl;
-    pl.BN = (BN == 128 || BN == 256) ? BN : ((n <= 128) ? 128 : 256);
+    pl.cfg = (cfg >= 0 && cfg < TC_CONFIGS) ? cfg : ((n <= 128) ? 1 : 0);
+    pl.BN = tc_config_bn(pl.cfg);
     pl.n_tiles = (int)((n + pl.BN - 1) / pl.BN);
     pl.m_tiles = (int)(N_pad / BM);
     pl.ksteps = (p + 1 + 15) / 16;
@@ -927,6 +932,35 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
     return make_map_2d(map, Gbf, (uint64_t)Kp, (uint64_t)n, (uint32_t)tw, (uint32_t)BN, tail_swizzle(tw));
 }
 
+// Every kernel a tile configuration and mode launches: VISIT(BN, STAGES, RESID, AR, EW).
+// The residual variant always has 8 epilogue warps; configuration 3's 6 stages fit only with
+// the particle operand resident (the streaming variant falls back to 4).
+#define TC_FOR_CONFIG(cfg, resid, ar, VISIT)                                          \
+    do {                                                                              \
+        if (resid) {                                                                  \
+            if (tc_config_bn(cfg) == 256) {                                           \
+                if (ar) VISIT(256, 3, true, true, 8);                                 \
+                VISIT(256, 3, true, false, 8);                                        \
+            }                                                                         \
+            if (ar) VISIT(128, 4, true, true, 8);                                     \
+            VISIT(128, 4, true, false, 8);                                            \
+        }                                                                             \
+        switch (cfg) {                                                                \
+        case 2:                                                                       \
+            if (ar) VISIT(256, 3, false, true, 8);                                    \
+            VISIT(256, 3, false, false, 8);                                           \
+        case 1:                                                                       \
+            if (ar) VISIT(128, 4, false, true, 16);                                   \
+            VISIT(128, 4, false, false, 16);                                          \
+        case 3:                                                                       \
+            if (ar) VISIT(128, 6, false, true, 16);                                   \
+            VISIT(128, 4, false, false, 16);                                          \
+        default:                                                                      \
+            if (ar) VISIT(256, 3, false, true, 16);                                   \
+            VISIT(256, 3, false, false, 16);                                          \
+        }                                                                             \
+    } while (0)
+
 cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, int Kp,
                              const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, cudaStream_t st,
                              const ResidArgs* ra, uint64_t wait_ns, int stall)
@@ -934,35 +968,22 @@ cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, 
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     // A stays resident when all its k-blocks fit (K <= 256)
     const bool ar = plan.kblocks <= KB_RES;
-#define TC_CASE(BN_, S_, R_, AR_) \
-    return launch_tc<BN_, S_, R_, AR_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, stall, st)
-    if (ra) {
-        if (plan.BN == 256) {
-            if (ar) TC_CASE(256, 3, true, true);
-            TC_CASE(256, 3, true, false);
-        }
-        if (ar) TC_CASE(128, 4, true, true);
-        TC_CASE(128, 4, true, false);
-    }
-    if (plan.BN == 256) {
-        if (ar) TC_CASE(256, 3, false, true);
-        TC_CASE(256, 3, false, false);
-    }
-    if (ar) TC_CASE(128, 4, false, true);
-    TC_CASE(128, 4, false, false);
-#undef TC_CASE
+#define TC_LAUNCH(BN_, S_, R_, AR_, EW_) \
+    return launch_tc<BN_, S_, R_, AR_, EW_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, stall, st)
+    TC_FOR_CONFIG(plan.cfg, ra != nullptr, ar, TC_LAUNCH);
+#undef TC_LAUNCH
 }
 
 bool tc_plan_resident(const TcPlan& plan) { return plan.kblocks <= KB_RES; }
 
-template <int BN, int STAGES, bool RESID, bool AR>
+template <int BN, int STAGES, bool RESID, bool AR, int EW>
 static cudaError_t launch_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, uint32_t* err,
                                   cudaStream_t st, uint64_t wait_ns)
 {
     using C = TcCfg<BN, STAGES, AR>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(Epi<RESID>::THREADS);
+    cfg.blockDim = dim3(Epi<EW>::THREADS);
     cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -970,29 +991,17 @@ static cudaError_t launch_grouped(const TcRegion* regs, int R, const int64_t* ct
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_loglik_tc_grouped<BN, STAGES, RESID, AR>, regs, R, cta_units, err, wait_ns);
+    return cudaLaunchKernelEx(&cfg, k_loglik_tc_grouped<BN, STAGES, RESID, AR, EW>, regs, R, cta_units, err, wait_ns);
 }
 
-cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int BN, bool ar,
+cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int cfg, bool ar,
                                      bool resid, uint32_t* err, cudaStream_t st, uint64_t wait_ns)
 {
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
-#define G_CASE(BN_, S_, R_, AR_) return launch_grouped<BN_, S_, R_, AR_>(regs, R, cta_units, grid, err, st, wait_ns)
-    if (resid) {
-        if (BN == 256) {
-            if (ar) G_CASE(256, 3, true, true);
-            G_CASE(256, 3, true, false);
-        }
-        if (ar) G_CASE(128, 4, true, true);
-        G_CASE(128, 4, true, false);
-    }
-    if (BN == 256) {
-        if (ar) G_CASE(256, 3, false, true);
-        G_CASE(256, 3, false, false);
-    }
-    if (ar) G_CASE(128, 4, false, true);
-    G_CASE(128, 4, false, false);
-#undef G_CASE
+#define G_LAUNCH(BN_, S_, R_, AR_, EW_) \
+    return launch_grouped<BN_, S_, R_, AR_, EW_>(regs, R, cta_units, grid, err, st, wait_ns)
+    TC_FOR_CONFIG(cfg, resid, ar, G_LAUNCH);
+#undef G_LAUNCH
 }
 
 AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms)

@@ -8,6 +8,8 @@
 // schedule and the seed live in device memory, so a replay only re-uploads them.
 // Decisions that depend on data (resample or not) are taken on the device (a flag the
 // resampling kernels read), so the host never waits inside a sweep.
+#include <dlfcn.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -88,7 +90,9 @@ struct Workspace {
     float *beta = nullptr, *beta_p = nullptr, *scale = nullptr;
     __nv_bfloat16* A = nullptr;
     CUtensorMap mapA, mapAt;  // the particle operand (64-column boxes; narrow last k-block)
-    int BN = 0;               // n-tile width of the likelihood kernel (tuned per shape)
+    int BN = 0;               // n-tile width of the likelihood kernel's tile configuration
+    int cfg = -1;             // the likelihood kernel's tile configuration (tuned per shape)
+    int cfg_source = 0;       // where it came from: 0 fixed (environment, context, small n), 1 table, 2 timed
     float2* lpt_p = nullptr;  // compensated log-prior term sums of the proposals
     float2* ydq = nullptr;    // the proposals' linear log-likelihood term beta' . v
     float2 *llq = nullptr, *lpq = nullptr, *llq_tmp = nullptr, *lpq_tmp = nullptr;  // MH state pairs
@@ -202,6 +206,7 @@ struct spa_ctx {
     float* lip = nullptr;      // ||X||_2^2 / 4 for the MAP solver
     bool lip_ok = false;
     uint64_t wait_ns = 0;      // limit of the tensor-core kernels' bounded waits (0: the default)
+    int tile_cfg = -1;         // likelihood tile configuration fixed by spa_set_tile_config (-1: tuned)
     int fault = 0;             // faults injected into the current sweep graph (SPA_FAULT)
 
     cudaStream_t stream() const { return cfg.stream ? static_cast<cudaStream_t>(cfg.stream) : own_stream; }
@@ -277,6 +282,7 @@ void free_workspace(Workspace& w)
     dfree(w.gl); dfree(w.gl_p); dfree(w.fwd); dfree(w.R); dfree(w.rsum); dfree(w.gpart);
     w.N = w.N_pad = 0;
     w.BN = 0;
+    w.cfg = -1;
 }
 
 void free_runbufs(RunBufs& r)
@@ -299,7 +305,7 @@ void drop_graph(spa_ctx* c, bool bump = true)
 int ensure_mapB(spa_ctx* c, int BN)
 {
     if (c->mapB_BN == BN) return SPA_OK;
-    const int tw = tc_plan(c->n, (int)c->p, 128, c->num_sms, BN).tw;
+    const int tw = tc_plan(c->n, (int)c->p, 128, c->num_sms, BN == 128 ? 1 : 0).tw;  // tw depends on p only
     if (!tc_make_map_B(&c->mapB, c->Gbf, c->n, c->Kp, BN) ||
         !tc_make_map_B_tail(&c->mapBt, c->Gbf, c->n, c->Kp, BN, tw))
         return fail(c, SPA_ECUDA, "cuTensorMapEncodeTiled failed for the genotype operand");
@@ -308,21 +314,123 @@ int ensure_mapB(spa_ctx* c, int BN)
 }
 
 // ----------------------------------------------------------- likelihood tile tuner
-// The n-tile width of the likelihood kernel (128 or 256 individuals) sets how evenly the
-// (particle-tile, n-tile) units spread over the SMs and how often each particle tile is
-// streamed again. Each shape (device, N_pad, n, p) is timed once per process with both
-// widths on the context's stream (3 warm-up and 10 timed launches each, CUDA events) and
-// the faster one is kept. The result does not depend on the choice: the partial sums are
-// per 32-individual chunk whatever the width.
-int tune_bn(spa_ctx* c)
+// The tile configuration of the likelihood kernel (n-tile width, G stages, epilogue warps)
+// sets how evenly the (particle-tile, n-tile) units spread over the SMs, how often each
+// particle tile is streamed again and how the epilogue hides its latencies. The result does
+// not depend on it: the partial sums are per 32-individual chunk whatever the tile. A shape
+// (device, N_pad, n, p) takes, in this order: SPA_TILE_CONFIG=0..3 (or SPA_LOGLIK_BN=256|128,
+// configurations 0|1) from the environment; a configuration fixed on the context
+// (spa_set_tile_config); the nearest entry of the tile table, a JSON file written by the
+// library's tuning script on a GB300 (SPA_TILE_TABLE, else tuning/loglik_tiles.json beside the
+// package); else every valid configuration is timed once per process on the context's
+// stream (3 warm-up and 10 timed launches each, CUDA events) and the fastest is kept.
+struct TileEntry {
+    int64_t n, p, N_pad;
+    int cfg;
+};
+
+std::string library_dir()
+{
+    Dl_info info;
+    if (dladdr(reinterpret_cast<void*>(&spa_config_default), &info) == 0 || !info.dli_fname) return ".";
+    std::string f(info.dli_fname);
+    const size_t k = f.find_last_of('/');
+    return k == std::string::npos ? "." : f.substr(0, k);
+}
+
+// The integer after "key": inside [b, e) of s, or -1.
+int64_t json_int(const std::string& s, size_t b, size_t e, const char* key)
+{
+    const std::string k = std::string("\"") + key + "\"";
+    size_t i = s.find(k, b);
+    if (i == std::string::npos || i >= e) return -1;
+    i = s.find(':', i + k.size());
+    if (i == std::string::npos || i >= e) return -1;
+    return std::strtoll(s.c_str() + i + 1, nullptr, 10);
+}
+
+// The table's entries: the objects of its "entries" list with integer n, p, N_pad and config.
+const std::vector<TileEntry>& tile_table()
+{
+    static std::vector<TileEntry> table;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* env = std::getenv("SPA_TILE_TABLE");
+        const std::string path = env ? std::string(env) : library_dir() + "/../tuning/loglik_tiles.json";
+        FILE* f = std::fopen(path.c_str(), "rb");
+        if (!f) return;
+        std::string s;
+        char buf[4096];
+        size_t got;
+        while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) s.append(buf, got);
+        std::fclose(f);
+        size_t i = s.find("\"entries\"");
+        while (i != std::string::npos) {
+            const size_t b = s.find('{', i);
+            if (b == std::string::npos) break;
+            const size_t e = s.find('}', b);
+            if (e == std::string::npos) break;
+            TileEntry t{json_int(s, b, e, "n"), json_int(s, b, e, "p"), json_int(s, b, e, "N_pad"),
+                        (int)json_int(s, b, e, "config")};
+            if (t.n > 0 && t.p > 0 && t.N_pad > 0 && t.cfg >= 0 && t.cfg < TC_CONFIGS) table.push_back(t);
+            i = e + 1;
+        }
+    });
+    return table;
+}
+
+// The table's configuration for the nearest shape (sum of the absolute log ratios of n, p + 1
+// and N_pad at most 0.75), if it is valid for this shape's kernel mode; else -1.
+int table_config(int64_t n, int64_t p, int64_t N_pad, bool resident)
+{
+    const std::vector<TileEntry>& t = tile_table();
+    double best = 1e30;
+    int cfg = -1;
+    for (const TileEntry& e : t) {
+        if ((e.p + 1 <= 256) != resident) continue;  // the same kernel mode
+        const double d = std::fabs(std::log((double)n / (double)e.n)) +
+                         std::fabs(std::log((double)(p + 1) / (double)(e.p + 1))) +
+                         std::fabs(std::log((double)N_pad / (double)e.N_pad));
+        if (d < best) {
+            best = d;
+            cfg = e.cfg;
+        }
+    }
+    return (best <= 0.75 && tc_config_valid(cfg, resident)) ? cfg : -1;
+}
+
+int tune_tile(spa_ctx* c)
 {
     Workspace& w = c->ws;
-    if (c->n <= 128) return 128;
-    // SPA_LOGLIK_BN=128|256 fixes the width instead (reproducible profiles and comparisons)
+    const bool resident = tc_plan_resident(tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, 0));
+    if (const char* env = std::getenv("SPA_TILE_CONFIG")) {
+        const int v = std::atoi(env);
+        if (tc_config_valid(v, resident)) {
+            w.cfg_source = 0;
+            return v;
+        }
+    }
     if (const char* env = std::getenv("SPA_LOGLIK_BN")) {
         const int v = std::atoi(env);
-        if (v == 128 || v == 256) return v;
+        if (v == 128 || v == 256) {
+            w.cfg_source = 0;
+            return v == 128 ? 1 : 0;
+        }
     }
+    if (tc_config_valid(c->tile_cfg, resident)) {
+        w.cfg_source = 0;
+        return c->tile_cfg;
+    }
+    if (c->n <= 128) {
+        w.cfg_source = 0;
+        return 1;
+    }
+    const int tab = table_config(c->n, c->p, w.N_pad, resident);
+    if (tab >= 0) {
+        w.cfg_source = 1;
+        return tab;
+    }
+    w.cfg_source = 2;
     static std::mutex mu;
     static std::map<std::tuple<int, int64_t, int64_t, int64_t>, int> cache;
     const auto key = std::make_tuple(c->device, w.N_pad, c->n, c->p);
@@ -333,20 +441,22 @@ int tune_bn(spa_ctx* c)
     }
     cudaStream_t st = c->stream();
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 256;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         if (e0) cudaEventDestroy(e0);
-        return 256;
+        return 0;
     }
-    int best = 256;
+    int best = 0;
     float best_ms = -1.0f;
-    for (int BN : {128, 256}) {
-        const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, BN);
+    for (int cfg = 0; cfg < TC_CONFIGS; ++cfg) {
+        if (!tc_config_valid(cfg, resident)) continue;
+        const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, cfg);
         TcMaps m;
         m.A = w.mapA;
         m.At = w.mapAt;
-        if (!tc_make_map_B(&m.B, c->Gbf, c->n, c->Kp, BN) || !tc_make_map_B_tail(&m.Bt, c->Gbf, c->n, c->Kp, BN, plan.tw))
+        if (!tc_make_map_B(&m.B, c->Gbf, c->n, c->Kp, plan.BN) ||
+            !tc_make_map_B_tail(&m.Bt, c->Gbf, c->n, c->Kp, plan.BN, plan.tw))
             continue;
         cudaError_t e = cudaSuccess;
         for (int k = 0; k < 3 && e == cudaSuccess; ++k)
@@ -361,7 +471,7 @@ int tune_bn(spa_ctx* c)
         if (e != cudaSuccess) continue;
         if (best_ms < 0.0f || ms < best_ms) {
             best_ms = ms;
-            best = BN;
+            best = cfg;
         }
     }
     cudaEventDestroy(e0);
@@ -420,7 +530,8 @@ int ensure_workspace(spa_ctx* c, int64_t N)
     }
     w.N = N;
     w.N_pad = N_pad;
-    w.BN = tune_bn(c);
+    w.cfg = tune_tile(c);
+    w.BN = tc_config_bn(w.cfg);
     return ensure_mapB(c, w.BN);
 }
 
@@ -516,7 +627,7 @@ struct Enq {
 // gradient of the log-likelihood at the packed particles (beta_p / A) into out, on the
 // tensor cores: residual likelihood pass, C = R G, finish. Also leaves the softplus
 // partials of those particles in w.partial.
-TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, c->num_sms, c->ws.BN); }
+TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, c->num_sms, c->ws.cfg); }
 
 TcMaps maps_of(const spa_ctx* c)
 {
@@ -949,7 +1060,7 @@ void destroy(spa_ctx* c)
 // share a tile class (n-tile width, resident particle operand), their table and the CTAs'
 // unit ranges, in device memory.
 struct BatchClass {
-    int BN = 0;
+    int cfg = 0;
     bool ar = false;
     int R = 0;
     int grid = 0;
@@ -1027,12 +1138,12 @@ int batch_build_classes(spa_batch* b)
     std::map<std::pair<int, bool>, std::vector<int32_t>> by_class;
     for (int32_t r = 0; r < R; ++r) {
         const TcPlan plan = plan_of(b->ctxs[r]);
-        by_class[{plan.BN, tc_plan_resident(plan)}].push_back(r);
+        by_class[{plan.cfg, tc_plan_resident(plan)}].push_back(r);
     }
     const bool mala = b->ctxs[0]->cfg.move_kind == SPA_MOVE_MALA;
     for (const auto& kv : by_class) {
         BatchClass k;
-        k.BN = kv.first.first;
+        k.cfg = kv.first.first;
         k.ar = kv.first.second;
         k.R = (int)kv.second.size();
         std::vector<TcRegion> regs((size_t)k.R);
@@ -1133,7 +1244,7 @@ cudaError_t batch_capture_lockstep(spa_batch* b, const spa_batch_args* args)
         }
         for (const BatchClass& k : b->classes) {
             if (e == cudaSuccess)
-                e = launch_loglik_tc_grouped(k.regs, k.R, k.cta_units, k.grid, k.BN, k.ar, mala, b->d_err, b->st,
+                e = launch_loglik_tc_grouped(k.regs, k.R, k.cta_units, k.grid, k.cfg, k.ar, mala, b->d_err, b->st,
                                              wait_ns);
             ++b->launches;
         }
@@ -1392,6 +1503,24 @@ int spa_set_wait_limit(spa_ctx* c, uint64_t limit_ns)
 }
 
 int spa_loglik_tile_width(const spa_ctx* c) { return (c && c->ws.N > 0) ? c->ws.BN : 0; }
+
+int spa_loglik_tile_config(const spa_ctx* c, int32_t* source)
+{
+    if (!c || c->ws.N <= 0) return -1;
+    if (source) *source = c->ws.cfg_source;
+    return c->ws.cfg;
+}
+
+int spa_set_tile_config(spa_ctx* c, int32_t cfg)
+{
+    if (!c) return fail(nullptr, SPA_EINVAL, "ctx is NULL");
+    if (cfg < -1 || cfg >= TC_CONFIGS) return fail(c, SPA_EINVAL, "tile configuration out of range");
+    if (cfg == c->tile_cfg) return SPA_OK;
+    c->tile_cfg = cfg;
+    drop_graph(c);
+    free_workspace(c->ws);  // the next call builds the workspace with the new configuration
+    return SPA_OK;
+}
 
 static int run_common(spa_ctx* c, const double* sched, bool sched_on_device, int64_t T, int64_t N, int32_t M,
                       uint64_t seed)

@@ -277,7 +277,19 @@ cudaError_t launch_best_particle(const MhState& s, const float* beta, int64_t N,
 // tcgen05 split-BF16 GEMM with the fused softplus reduction: partial[c * N_pad + i] receives
 // -sum over the 32-individual chunk c of log2(1 + 2^eta2), eta2 = eta log2(e), so that
 // l = ln(2) * (sum of the partials + beta . v log2(e)) with v = X^T y.
+// Tile configurations of the likelihood kernel (the tuner chooses one per shape):
+//   config  n-tile width BN  G stages  epilogue warps
+//   0       256              3         16
+//   1       128              4         16
+//   2       256              3         8
+//   3       128              6         16     (resident particle operand only: K <= 256)
+// The residual (MALA) variant uses the configuration's BN with 3 or 4 stages and 8 epilogue
+// warps. Every configuration gives the same partial sums bit for bit (one per 32 individuals).
+constexpr int TC_CONFIGS = 4;
+int tc_config_bn(int cfg);
+bool tc_config_valid(int cfg, bool resident);
 struct TcPlan {
+    int cfg;         // tile configuration
     int BN;          // individuals per n-tile (128 or 256)
     int n_tiles;     // ceil(n / BN)
     int m_tiles;     // N_pad / 128
@@ -292,8 +304,8 @@ struct TcPlan {
 struct TcMaps {
     CUtensorMap A, B, At, Bt;
 };
-// BN = 128 or 256 picks the n-tile width (the tuner's choice); 0 picks by the size of n.
-TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int BN = 0);
+// cfg: the tile configuration (the tuner's choice); -1 picks by the size of n.
+TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int cfg = -1);
 // Opt the tensor-core kernels into their dynamic shared memory (once per device, before any capture).
 cudaError_t tc_init_attributes();
 bool tc_make_map_A(CUtensorMap* map, const __nv_bfloat16* A, int64_t N_pad, int Kp);
@@ -330,8 +342,8 @@ struct TcRegion {
 };
 // Units of region r: m_tiles x n_tiles in row-major order, global indices from unit0. CTA b
 // of `grid` takes the global units [cta_units[b], cta_units[b + 1]). All regions of one launch
-// share BN (128 or 256), the residual mode and the A-resident mode (kblocks <= 4).
-cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int BN, bool ar,
+// share the tile configuration, the residual mode and the A-resident mode (kblocks <= 4).
+cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, int cfg, bool ar,
                                      bool resid, uint32_t* err, cudaStream_t st, uint64_t wait_ns = 0);
 // Whether a plan's particle operand stays resident in shared memory (K <= 256).
 bool tc_plan_resident(const TcPlan& plan);

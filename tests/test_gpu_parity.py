@@ -5,6 +5,7 @@ floating point within the bounds stated in include/spa.h and below. Inputs are s
 and synthetic (paper_1106_0322_gb300.synth), shaped like the paper's hit regions.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -13,6 +14,7 @@ import oracle
 from paper_1106_0322_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -342,3 +344,48 @@ def test_invalid_inputs_rejected(spa):
             r.run([0.1], N=0, moves_per_step=1, seed=1)
         out = r.run([0.1, 0.2], N=16, moves_per_step=1, seed=1)  # still usable after errors
         assert np.all(np.isfinite(out["mean"]))
+
+
+@pytest.mark.parametrize("n,p,N", [(2000, 200, 1000), (777, 300, 300), (300, 37, 129)])
+def test_every_tile_configuration_gives_the_same_bits(spa, n, p, N):
+    """The tuner's search space: n-tile width, G stages and epilogue warps change how the work
+    is cut, never a result. Log-likelihoods and (residual mode) gradients are bit-identical
+    across every configuration valid for the shape (6 stages need the resident operand)."""
+    reg = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=53)
+    B = synth.random_particles(N, p, 0.05, seed=54)
+    lls, grads = {}, {}
+    with spa.Region(reg.G, reg.y, 2.0) as r:
+        for cfg in range(4):
+            r.set_tile_config(cfg)
+            lls[cfg] = r.loglik(B)
+            _, grads[cfg] = r.grad(B, 0.0)
+            got, src = r.tile_config()
+            if p + 1 <= 256 or cfg != 3:
+                assert (got, src) == (cfg, 0)
+    for cfg in range(1, 4):
+        assert np.array_equal(lls[0].view(np.uint64), lls[cfg].view(np.uint64)), cfg
+        assert np.array_equal(grads[0].view(np.uint32), grads[cfg].view(np.uint32)), cfg
+
+
+def test_tile_table_entry_is_used(tmp_path):
+    """A tile-table entry for a nearby shape decides the configuration without timing."""
+    import json
+    import subprocess
+    import sys
+
+    table = tmp_path / "tiles.json"
+    table.write_text(json.dumps({"entries": [{"n": 1900, "p": 190, "N_pad": 1024, "config": 2}]}))
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np, paper_1106_0322_gb300 as spa\n"
+        "from paper_1106_0322_gb300 import synth\n"
+        "reg = synth.make_region(2000, 200, 0.9, (0.4,), seed=55)\n"
+        "with spa.Region(reg.G, reg.y, 1.0) as r:\n"
+        "    r.loglik(synth.random_particles(1000, 200, 0.05, seed=56))\n"
+        "    print(r.tile_config())\n" % ROOT)
+    env = dict(os.environ, SPA_TILE_TABLE=str(table))
+    env.pop("SPA_TILE_CONFIG", None)
+    env.pop("SPA_LOGLIK_BN", None)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip().splitlines()[-1] == "(2, 1)"
