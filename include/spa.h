@@ -229,15 +229,17 @@ int spa_loglik_tile_width(const spa_ctx* ctx);
  * spa_set_tile_config, or n <= 128), 1 the tile table, 2 timed by the tuner. Configurations:
  *   0: n-tiles of 256, 3 G stages, 16 epilogue warps   1: 128, 4 stages, 16 warps
  *   2: 256, 3 stages, 8 warps                          3: 128, 6 stages, 16 warps (p <= 255)
- * A shape takes SPA_TILE_CONFIG=0..3 (or SPA_LOGLIK_BN) from the environment, else the value
+ *   4: 256, 6 stages, 8 warps, the particle operand held in tensor memory (p <= 255)
+ *   5: 128, 12 stages, 16 warps, the particle operand held in tensor memory (p <= 255)
+ * A shape takes SPA_TILE_CONFIG=0..5 (or SPA_LOGLIK_BN) from the environment, else the value
  * fixed by spa_set_tile_config, else the nearest shape of the tile table (a JSON file written
  * by the package's tune_tiles.py on a GB300: SPA_TILE_TABLE, else tuning/loglik_tiles.json
  * beside the package), else the tuner times every valid configuration once per process. No
  * configuration changes any result: the partial sums are per 32 individuals whatever the tile. */
 int spa_loglik_tile_config(const spa_ctx* ctx, int32_t* source);
-/* Fix the tile configuration (0..3; -1 returns to the table and tuner) for later runs of the
+/* Fix the tile configuration (0..5; -1 returns to the table and tuner) for later runs of the
  * context: it replaces the context's workspace and captured graph. An invalid configuration
- * for the shape (3 with p > 255) is ignored at the next run. SPA_EINVAL if out of range. */
+ * for the shape (3..5 with p > 255) is ignored at the next run. SPA_EINVAL if out of range. */
 int spa_set_tile_config(spa_ctx* ctx, int32_t cfg);
 
 /* Enqueue `reps` launches of the context's likelihood kernel (split-BF16 tcgen05 or

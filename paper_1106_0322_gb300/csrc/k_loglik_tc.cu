@@ -41,28 +41,39 @@ struct Epi {
 };
 constexpr int ADJ_BN_SMALL = 208;  // p + padding <= 208 covers the p = 200 workloads in one N tile
 
-// Shared-memory plan. Streaming (AR = false): every stage carries A_hi, A_lo and the G tile
-// of one k-block. A-resident (AR = true, K <= 256): the particle tile's A_hi | A_lo for all
-// k-blocks stays in shared memory while the CTA walks consecutive n-tiles of the same
-// particle tile, and the stages carry only G, halving what each SM pulls from L2.
+// Shared-memory and TMEM plan, by the particle operand's residence AR:
+//   0 streaming: every stage carries A_hi, A_lo and the G tile of one k-block;
+//   1 resident in shared memory (K <= 256): the particle tile's A_hi | A_lo for all k-blocks
+//     stays there while the CTA walks consecutive n-tiles of the same particle tile, and the
+//     stages carry only G, halving what each SM pulls from L2;
+//   2 resident in tensor memory (K <= 256): the epilogue warps copy the particle tile's rows
+//     into TMEM columns beside the accumulators and the MMAs read A from there, so that shared
+//     memory holds only G stages -- twice as many, which is what hides the G loads' latency.
+//     With BN = 256 the accumulator is single-buffered (256 + 256 columns): the epilogue moves
+//     it to registers and hands it back before doing its arithmetic.
 constexpr int KB_RES = 4;  // k-blocks of a resident A (Kp <= 256)
 
-template <int BN, int STAGES, bool AR = false>
+template <int BN, int STAGES, int AR = 0>
 struct TcCfg {
     static constexpr int A_TILE = BM * BK * 2;
     static constexpr int B_TILE = BN * BK * 2;
-    static constexpr int A_RES = AR ? KB_RES * 2 * A_TILE : 0;
+    static constexpr int A_RES = AR == 1 ? KB_RES * 2 * A_TILE : 0;
     static constexpr int STAGE = AR ? B_TILE : 2 * A_TILE + B_TILE;
+    // accumulator buffers, and the TMEM column of A (AR = 2): A_hi in 8 columns per K = 16
+    // step (two BF16 per 32-bit column), then A_lo
+    static constexpr int NACC = (AR == 2 && BN == 256) ? 1 : 2;
+    static constexpr uint32_t A_COL = (uint32_t)(NACC * BN);
     static constexpr int BAR_OFF = A_RES + STAGES * STAGE;
     // full[S], empty[S], acc_full[2], acc_empty[2], drain, a_empty, a_full[KB_RES]
     static constexpr int NBARS = 2 * STAGES + 6 + KB_RES;
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
     static constexpr int BYTES = SLOT_OFF + 16;
     static constexpr int SMEM = BYTES + 1024;  // slack for the 1024-byte alignment of the tiles
-    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    static constexpr uint32_t TMEM_COLS = AR == 2 ? 512u : (uint32_t)(2 * BN);
     static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
+    static_assert(AR != 2 || A_COL + 2 * KB_RES * 32 <= TMEM_COLS, "A_hi | A_lo must fit beside the accumulators");
 };
 
 // Sum over the first `valid` of 32 columns of softplus2(eta2) = log2(1 + 2^eta2): 32
@@ -177,6 +188,7 @@ struct TcUnit {
     const CUtensorMap* At;  //   k-block, the tw-column boxes
     const CUtensorMap* B;   // genotype operand, likewise
     const CUtensorMap* Bt;
+    const __nv_bfloat16* Araw;  // the particle operand itself (rows of 2 Kp), for a TMEM-resident A
     int tw, kblocks, ksteps, Kp, n, mt, nt;
     int64_t key;
     float* partial;
@@ -187,9 +199,35 @@ struct TcUnit {
     float* rsum_part;
 };
 
+// AR = 2: this warp's share of particle tile t.mt's operand rows, copied into TMEM. Row `row`
+// (one of the warp's own 32 lanes) takes the 16-byte chunks c of [A_hi | A_lo]: c < KC =
+// 2 ksteps is A_hi's BF16 columns 8c..8c+7, c >= KC A_lo's 8(c - KC)..; chunk c goes to TMEM
+// columns 4c..4c+3, and the GROUPS warps of one lane quadrant split the chunks between them.
+template <int GROUPS>
+__device__ __forceinline__ void ta_copy_A(const TcUnit& t, uint32_t taddr, int grp, int row)
+{
+    constexpr int BATCH = 8;  // 16-byte chunks in flight per thread
+    const int KC = 2 * t.ksteps;
+    const int c0 = (2 * KC * grp) / GROUPS, c1 = (2 * KC * (grp + 1)) / GROUPS;
+    const uint4* a = reinterpret_cast<const uint4*>(t.Araw + ((int64_t)t.mt * BM + row) * (int64_t)(2 * t.Kp));
+    const int lo_off = t.Kp / 8;  // chunks from A_hi's first column to A_lo's
+    for (int cb = c0; cb < c1; cb += BATCH) {
+        uint4 v[BATCH];
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int c = cb + k;
+            if (c < c1) v[k] = __ldg(a + (c < KC ? c : lo_off + (c - KC)));
+        }
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k)  // warp-uniform condition: the stores are warp-collective
+            if (cb + k < c1) tmem_st4(taddr + 4u * (uint32_t)(cb + k), v[k]);
+    }
+}
+
 // One region, its maps passed as kernel parameters: the units of CTA b are tc_unit_range's.
 struct TcSingleSource {
     const CUtensorMap *A, *B, *At, *Bt;
+    const __nv_bfloat16* Araw;
     int tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n;
     float* partial;
     int64_t N_pad;
@@ -210,6 +248,7 @@ struct TcSingleSource {
         t.At = At;
         t.B = B;
         t.Bt = Bt;
+        t.Araw = Araw;
         t.tw = tw;
         t.kblocks = kblocks;
         t.ksteps = ksteps;
@@ -277,6 +316,7 @@ struct TcGroupedSource {
         t.At = &g.At;
         t.B = &g.B;
         t.Bt = &g.Bt;
+        t.Araw = nullptr;  // grouped launches keep A in shared memory (AR < 2)
         t.tw = g.tw;
         t.kblocks = g.kblocks;
         t.ksteps = g.ksteps;
@@ -306,7 +346,7 @@ struct TcGroupedSource {
 };
 
 // The pipeline of one CTA over units [u_begin, u_end) of `src`.
-template <int BN, int STAGES, bool RESID, bool AR, int EW, class Src>
+template <int BN, int STAGES, bool RESID, int AR, int EW, class Src>
 __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restrict__ err, uint64_t wait_ns, int stall)
 {
     using C = TcCfg<BN, STAGES, AR>;
@@ -323,8 +363,9 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
 #define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
 #define ACCF_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
 #define ACCE_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
-// one per k-block of the resident A, so that the first MMAs of an epoch need only their own
-// k-block of A, not all of it
+// AR = 1: one per k-block of the resident A, so that the first MMAs of an epoch need only
+// their own k-block of A, not all of it. AR = 2: AFULL_BAR(0) alone, arrived at by every
+// epilogue warp once its share of A is in TMEM.
 #define AFULL_BAR(kb) (bar0 + 8u * (uint32_t)(2 * STAGES + 6 + (kb)))
 
     int64_t u_begin, u_end;
@@ -341,7 +382,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
         }
         mbar_init(drain_bar, 1);
         mbar_init(aempty_bar, 1);
-        for (int kb = 0; kb < KB_RES; ++kb) mbar_init(AFULL_BAR(kb), 1);
+        for (int kb = 0; kb < KB_RES; ++kb) mbar_init(AFULL_BAR(kb), (AR == 2 && kb == 0) ? Epi<EW>::WARPS : 1);
         mbar_fence_init();
     }
     if (warp == 0 && lane == 0 && u_begin < u_end) src.prefetch(u_begin);
@@ -378,7 +419,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const uint32_t a_tail = t.tw ? (uint32_t)(BM * t.tw * 2) : (uint32_t)C::A_TILE;
                 const uint32_t b_tail = t.tw ? (uint32_t)(BN * t.tw * 2) : (uint32_t)C::B_TILE;
                 bool a_first = false;  // the epoch's first unit: A's k-blocks go out between its G stages
-                if (AR && t.key != cur_key) {
+                if (AR == 1 && t.key != cur_key) {
                     ++epoch;
                     // the previous epoch's MMAs must be done with the resident A
                     if (epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((epoch - 1) & 1), err, wait_ns)) {
@@ -389,12 +430,12 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                     a_first = true;
                     a_issued = 0;
                     cur_key = t.key;
-                } else if (!AR && u > u_begin && (t.key >> 32) != (cur_key >> 32)) {
+                } else if (AR != 1 && u > u_begin && (t.key >> 32) != (cur_key >> 32)) {
                     src.prefetch(u);
                 }
-                if (!AR) cur_key = t.key;
+                if (AR != 1) cur_key = t.key;
                 for (int kb = 0; kb < t.kblocks; ++kb) {
-                    if (AR && a_first) {
+                    if (AR == 1 && a_first) {
                         const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
                         const bool tail = t.tw && kb == kb_last;
                         const CUtensorMap* ma = tail ? t.At : t.A;
@@ -433,7 +474,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const uint32_t i2 = it - k;
                 mbar_drain(FULL_BAR(i2 % STAGES), (i2 / STAGES) & 1u, err);
             }
-            if (AR && epoch >= 0)  // the phases last armed (their parity bits were flipped since)
+            if (AR == 1 && epoch >= 0)  // the phases last armed (their parity bits were flipped since)
                 for (int kb = 0; kb < a_issued; ++kb) mbar_drain(AFULL_BAR(kb), ((a_par >> kb) & 1u) ^ 1u, err);
         }
     } else if (warp == 1) {
@@ -445,6 +486,7 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
             bool ok = true;
             int64_t cur_key = -1;
             uint32_t a_par = 0;  // bit kb: the parity of AFULL(kb)'s phase to wait for next
+            int ta_epoch = 0;    // AR = 2: epochs whose A this thread has waited for
             // Injected stall (tests of the timeout path): wait first on the drain barrier,
             // which nothing arrives at before this thread's own final commit, so the wait
             // runs out after wait_ns; no MMA has been issued, and the other roles give up and
@@ -454,21 +496,28 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const TcUnit t = src.unit(u);
                 const int kb_last = t.kblocks - 1;
                 const uint32_t tail_row = t.tw ? (uint32_t)(t.tw * 2) : 128u;
-                const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+                const uint32_t b = (uint32_t)(lt % C::NACC), aph = (uint32_t)((lt / C::NACC) & 1);
                 if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err, wait_ns)) {
                     ok = false;
                     break;
                 }
-                bool a_first = false;  // the epoch's first unit waits for each k-block of A
+                bool a_first = false;  // the epoch's first unit waits for (each k-block of) A
                 if (AR && t.key != cur_key) {
                     a_first = true;
                     cur_key = t.key;
+                }
+                if (AR == 2 && a_first) {
+                    if (!mbar_wait_bounded(AFULL_BAR(0), (uint32_t)(ta_epoch & 1), err, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    ++ta_epoch;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem_base + b * (uint32_t)BN;
                 for (int kb = 0; kb < t.kblocks; ++kb) {
                     const uint32_t s = it % STAGES, ph = (it / STAGES) & 1u;
-                    if (AR && a_first) {
+                    if (AR == 1 && a_first) {
                         if (!mbar_wait_bounded(AFULL_BAR(kb), (a_par >> kb) & 1u, err, wait_ns)) {
                             ok = false;
                             break;
@@ -481,15 +530,24 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                     }
                     tc_fence_after();
                     const uint32_t st = stage0 + s * C::STAGE;
-                    const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
                     const uint32_t rb = (t.tw && kb == kb_last) ? tail_row : 128u;
-                    const uint64_t ahi = sdesc_swz(a, rb);
-                    const uint64_t alo = sdesc_swz(a + C::A_TILE, rb);
                     const uint64_t bg = sdesc_swz(AR ? st : st + 2 * C::A_TILE, rb);
                     const int nks = (t.ksteps - 4 * kb) < 4 ? (t.ksteps - 4 * kb) : 4;
-                    for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
-                        umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
-                    for (int ks = 0; ks < nks; ++ks) umma_bf16(d, alo + 2u * ks, bg + 2u * ks, IDESC, 1u);
+                    if (AR == 2) {
+                        // A_hi of k-step g in TMEM columns A_COL + 8 g, A_lo 8 ksteps further on
+                        const uint32_t ahi = tmem_base + C::A_COL + 32u * (uint32_t)kb;
+                        const uint32_t alo = ahi + 8u * (uint32_t)t.ksteps;
+                        for (int ks = 0; ks < nks; ++ks)
+                            umma_bf16_ta(d, ahi + 8u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
+                        for (int ks = 0; ks < nks; ++ks) umma_bf16_ta(d, alo + 8u * ks, bg + 2u * ks, IDESC, 1u);
+                    } else {
+                        const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
+                        const uint64_t ahi = sdesc_swz(a, rb);
+                        const uint64_t alo = sdesc_swz(a + C::A_TILE, rb);
+                        for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
+                            umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
+                        for (int ks = 0; ks < nks; ++ks) umma_bf16(d, alo + 2u * ks, bg + 2u * ks, IDESC, 1u);
+                    }
                     umma_commit(EMPTY_BAR(s));
                     ++it;
                 }
@@ -513,9 +571,24 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
         const uint32_t lane_addr = (uint32_t)(quad * 32) << 16;
         const int col0 = grp * CPW * 32;
         int lt = 0;
+        int64_t ta_key = -1;  // AR = 2: the particle tile whose A is in TMEM
+        int ta_epoch = 0;
         for (int64_t u = u_begin; u < u_end; ++u, ++lt) {
             const TcUnit t = src.unit(u);
-            const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+            if (AR == 2 && t.key != ta_key) {
+                // the previous epoch's MMAs are done with A (their commit); then this warp copies
+                // its share of the new particle tile's rows into TMEM and says so
+                if (ta_epoch > 0 && !mbar_wait_bounded(aempty_bar, (uint32_t)((ta_epoch - 1) & 1), err, wait_ns)) break;
+                tc_fence_after();
+                ta_copy_A<E::GROUPS>(t, tmem_base + C::A_COL + lane_addr, grp, row);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(AFULL_BAR(0));
+                ta_key = t.key;
+                ++ta_epoch;
+            }
+            const uint32_t b = (uint32_t)(lt % C::NACC), aph = (uint32_t)((lt / C::NACC) & 1);
             if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
             tc_fence_after();
             const int valid0 = t.n - t.nt * BN - col0;  // valid columns from col0 on
@@ -576,23 +649,24 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
     }
 }
 
-template <int BN, int STAGES, bool RESID, bool AR, int EW>
+template <int BN, int STAGES, bool RESID, int AR, int EW>
 __global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
     k_loglik_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt, int tw,
+                const __grid_constant__ CUtensorMap mapAt, const __grid_constant__ CUtensorMap mapBt,
+                const __nv_bfloat16* __restrict__ Araw, int tw,
                 int n_tiles, int m_tiles, int kblocks, int ksteps, int Kp, int n, float* __restrict__ partial,
                 int64_t N_pad,
                 uint32_t* __restrict__ err, const uint32_t* __restrict__ ybits, __nv_bfloat16* __restrict__ R,
                 int64_t n_r, float* __restrict__ rsum_part, uint64_t wait_ns, int stall)
 {
-    const TcSingleSource src{&mapA, &mapB, &mapAt, &mapBt, tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n,
+    const TcSingleSource src{&mapA, &mapB, &mapAt, &mapBt, Araw, tw, n_tiles, m_tiles, kblocks, ksteps, Kp, n,
                              partial, N_pad, ybits, R, n_r, rsum_part};
     loglik_tc_body<BN, STAGES, RESID, AR, EW>(src, err, wait_ns, stall);
 }
 
 // The same pipeline over the units of many regions (a batched sweep's move): region tables
 // and per-CTA unit ranges in global memory.
-template <int BN, int STAGES, bool RESID, bool AR, int EW>
+template <int BN, int STAGES, bool RESID, int AR, int EW>
 __global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
     k_loglik_tc_grouped(const TcRegion* __restrict__ regs, int R, const int64_t* __restrict__ cta_units,
                         uint32_t* __restrict__ err, uint64_t wait_ns)
@@ -834,7 +908,7 @@ bool make_map_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t ou
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES, bool RESID, bool AR, int EW>
+template <int BN, int STAGES, bool RESID, int AR, int EW>
 cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
                       const uint32_t* ybits, float* partial, int64_t N_pad, uint32_t* err, const ResidArgs* ra,
                       uint64_t wait_ns, int stall, cudaStream_t st)
@@ -854,7 +928,7 @@ cudaError_t launch_tc(const TcMaps& m, const TcPlan& plan, int64_t n, int Kp,
     cfg.numAttrs = 1;
     const bool tail = plan.tw != 0;
     return cudaLaunchKernelEx(&cfg, k_loglik_tc<BN, STAGES, RESID, AR, EW>, m.A, m.B, tail ? m.At : m.A, tail ? m.Bt : m.B,
-                              plan.tw, plan.n_tiles, plan.m_tiles,
+                              m.Araw, plan.tw, plan.n_tiles, plan.m_tiles,
                               plan.kblocks, plan.ksteps, Kp, (int)n, partial, N_pad, err, ybits, ra ? ra->R : nullptr,
                               ra ? ra->n_r : (int64_t)0, ra ? ra->rsum_part : nullptr, wait_ns, stall);
 }
@@ -880,6 +954,10 @@ cudaError_t tc_init_attributes()
     SET_TC(256, 3, true, false, 8);
     SET_TC(128, 4, true, true, 8);
     SET_TC(128, 4, true, false, 8);
+#define SET_TC1(BN_, S_, AR_, EW_) SET_SMEM((k_loglik_tc<BN_, S_, false, AR_, EW_>), (TcCfg<BN_, S_, AR_>::SMEM))
+    SET_TC1(256, 6, 2, 8);
+    SET_TC1(128, 12, 2, 16);
+#undef SET_TC1
 #undef SET_TC
     SET_SMEM((k_adjoint_tc<ADJ_BN_SMALL, 3>), (AdjCfg<ADJ_BN_SMALL, 3>::SMEM));
     SET_SMEM((k_adjoint_tc<256, 3>), (AdjCfg<256, 3>::SMEM));
@@ -887,9 +965,9 @@ cudaError_t tc_init_attributes()
     return e;
 }
 
-int tc_config_bn(int cfg) { return (cfg == 1 || cfg == 3) ? 128 : 256; }
+int tc_config_bn(int cfg) { return (cfg == 1 || cfg == 3 || cfg == 5) ? 128 : 256; }
 
-bool tc_config_valid(int cfg, bool resident) { return cfg >= 0 && cfg < TC_CONFIGS && (cfg != 3 || resident); }
+bool tc_config_valid(int cfg, bool resident) { return cfg >= 0 && cfg < TC_CONFIGS && (cfg < 3 || resident); }
 
 TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int cfg)
 {
@@ -932,10 +1010,12 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
     return make_map_2d(map, Gbf, (uint64_t)Kp, (uint64_t)n, (uint32_t)tw, (uint32_t)BN, tail_swizzle(tw));
 }
 
-// Every kernel a tile configuration and mode launches: VISIT(BN, STAGES, RESID, AR, EW).
-// The residual variant always has 8 epilogue warps; configuration 3's 6 stages fit only with
-// the particle operand resident (the streaming variant falls back to 4).
-#define TC_FOR_CONFIG(cfg, resid, ar, VISIT)                                          \
+// Every kernel a tile configuration and mode launches: VISIT(BN, STAGES, RESID, AR, EW), and
+// VISIT_TA(BN, STAGES, EW) for the TMEM-resident kernels (a no-op where those do not apply, so
+// that the next line's shared-memory-resident kernel runs instead). The residual variant always
+// has 8 epilogue warps and A in shared memory; configurations 3-5 exist only with the particle
+// operand resident (their streaming fallbacks are configuration 1's or 2's).
+#define TC_FOR_CONFIG(cfg, resid, ar, VISIT, VISIT_TA)                                \
     do {                                                                              \
         if (resid) {                                                                  \
             if (tc_config_bn(cfg) == 256) {                                           \
@@ -946,6 +1026,14 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
             VISIT(128, 4, true, false, 8);                                            \
         }                                                                             \
         switch (cfg) {                                                                \
+        case 4:                                                                       \
+            if (ar) VISIT_TA(256, 6, 8);                                              \
+            if (ar) VISIT(256, 3, false, true, 8);                                    \
+            VISIT(256, 3, false, false, 8);                                           \
+        case 5:                                                                       \
+            if (ar) VISIT_TA(128, 12, 16);                                            \
+            if (ar) VISIT(128, 6, false, true, 16);                                   \
+            VISIT(128, 4, false, false, 16);                                          \
         case 2:                                                                       \
             if (ar) VISIT(256, 3, false, true, 8);                                    \
             VISIT(256, 3, false, false, 8);                                           \
@@ -970,13 +1058,16 @@ cudaError_t launch_loglik_tc(const TcMaps& maps, const TcPlan& plan, int64_t n, 
     const bool ar = plan.kblocks <= KB_RES;
 #define TC_LAUNCH(BN_, S_, R_, AR_, EW_) \
     return launch_tc<BN_, S_, R_, AR_, EW_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, stall, st)
-    TC_FOR_CONFIG(plan.cfg, ra != nullptr, ar, TC_LAUNCH);
+#define TC_LAUNCH_TA(BN_, S_, EW_) \
+    return launch_tc<BN_, S_, false, 2, EW_>(maps, plan, n, Kp, ybits, partial, N_pad, err, ra, wait_ns, stall, st)
+    TC_FOR_CONFIG(plan.cfg, ra != nullptr, ar, TC_LAUNCH, TC_LAUNCH_TA);
+#undef TC_LAUNCH_TA
 #undef TC_LAUNCH
 }
 
 bool tc_plan_resident(const TcPlan& plan) { return plan.kblocks <= KB_RES; }
 
-template <int BN, int STAGES, bool RESID, bool AR, int EW>
+template <int BN, int STAGES, bool RESID, int AR, int EW>
 static cudaError_t launch_grouped(const TcRegion* regs, int R, const int64_t* cta_units, int grid, uint32_t* err,
                                   cudaStream_t st, uint64_t wait_ns)
 {
@@ -1000,7 +1091,9 @@ cudaError_t launch_loglik_tc_grouped(const TcRegion* regs, int R, const int64_t*
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
 #define G_LAUNCH(BN_, S_, R_, AR_, EW_) \
     return launch_grouped<BN_, S_, R_, AR_, EW_>(regs, R, cta_units, grid, err, st, wait_ns)
-    TC_FOR_CONFIG(cfg, resid, ar, G_LAUNCH);
+#define G_LAUNCH_TA(BN_, S_, EW_) (void)0  // grouped launches keep A in shared memory
+    TC_FOR_CONFIG(cfg, resid, ar, G_LAUNCH, G_LAUNCH_TA);
+#undef G_LAUNCH_TA
 #undef G_LAUNCH
 }
 

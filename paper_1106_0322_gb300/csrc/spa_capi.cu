@@ -318,7 +318,7 @@ int ensure_mapB(spa_ctx* c, int BN)
 // sets how evenly the (particle-tile, n-tile) units spread over the SMs, how often each
 // particle tile is streamed again and how the epilogue hides its latencies. The result does
 // not depend on it: the partial sums are per 32-individual chunk whatever the tile. A shape
-// (device, N_pad, n, p) takes, in this order: SPA_TILE_CONFIG=0..3 (or SPA_LOGLIK_BN=256|128,
+// (device, N_pad, n, p) takes, in this order: SPA_TILE_CONFIG=0..5 (or SPA_LOGLIK_BN=256|128,
 // configurations 0|1) from the environment; a configuration fixed on the context
 // (spa_set_tile_config); the nearest entry of the tile table, a JSON file written by the
 // library's tuning script on a GB300 (SPA_TILE_TABLE, else tuning/loglik_tiles.json beside the
@@ -455,6 +455,7 @@ int tune_tile(spa_ctx* c)
         TcMaps m;
         m.A = w.mapA;
         m.At = w.mapAt;
+        m.Araw = w.A;
         if (!tc_make_map_B(&m.B, c->Gbf, c->n, c->Kp, plan.BN) ||
             !tc_make_map_B_tail(&m.Bt, c->Gbf, c->n, c->Kp, plan.BN, plan.tw))
             continue;
@@ -634,6 +635,7 @@ TcMaps maps_of(const spa_ctx* c)
     TcMaps m;
     m.A = c->ws.mapA;
     m.At = c->ws.mapAt;
+    m.Araw = c->ws.A;
     m.B = c->mapB;
     m.Bt = c->mapBt;
     return m;

@@ -278,14 +278,17 @@ cudaError_t launch_best_particle(const MhState& s, const float* beta, int64_t N,
 // -sum over the 32-individual chunk c of log2(1 + 2^eta2), eta2 = eta log2(e), so that
 // l = ln(2) * (sum of the partials + beta . v log2(e)) with v = X^T y.
 // Tile configurations of the likelihood kernel (the tuner chooses one per shape):
-//   config  n-tile width BN  G stages  epilogue warps
-//   0       256              3         16
-//   1       128              4         16
-//   2       256              3         8
-//   3       128              6         16     (resident particle operand only: K <= 256)
-// The residual (MALA) variant uses the configuration's BN with 3 or 4 stages and 8 epilogue
-// warps. Every configuration gives the same partial sums bit for bit (one per 32 individuals).
-constexpr int TC_CONFIGS = 4;
+//   config  n-tile width BN  G stages  epilogue warps  particle operand (K <= 256)
+//   0       256              3         16              shared memory
+//   1       128              4         16              shared memory
+//   2       256              3         8               shared memory
+//   3       128              6         16              shared memory (resident only)
+//   4       256              6         8               tensor memory (resident only)
+//   5       128              12        16              tensor memory (resident only)
+// Configurations 3-5 need the particle operand resident (K <= 256). The residual (MALA)
+// variant uses the configuration's BN with 3 or 4 stages, 8 epilogue warps and A in shared
+// memory. Every configuration gives the same partial sums bit for bit (one per 32 individuals).
+constexpr int TC_CONFIGS = 6;
 int tc_config_bn(int cfg);
 bool tc_config_valid(int cfg, bool resident);
 struct TcPlan {
@@ -303,6 +306,7 @@ struct TcPlan {
 // when the plan has a narrow last k-block, the same with tw-column boxes.
 struct TcMaps {
     CUtensorMap A, B, At, Bt;
+    const __nv_bfloat16* Araw = nullptr;  // the particle operand the maps A, At describe
 };
 // cfg: the tile configuration (the tuner's choice); -1 picks by the size of n.
 TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int cfg = -1);

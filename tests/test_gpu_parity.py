@@ -194,6 +194,7 @@ def test_loglik_same_for_every_tile_width(spa, monkeypatch, n, p, N):
     streaming particle operand, ragged n and N)."""
     reg = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=51)
     B = synth.random_particles(N, p, 0.05, seed=52)
+    monkeypatch.delenv("SPA_TILE_CONFIG", raising=False)  # it would take precedence over the width
     out = {}
     for bn in ("128", "256", None):
         if bn is None:
@@ -347,22 +348,25 @@ def test_invalid_inputs_rejected(spa):
 
 
 @pytest.mark.parametrize("n,p,N", [(2000, 200, 1000), (777, 300, 300), (300, 37, 129)])
-def test_every_tile_configuration_gives_the_same_bits(spa, n, p, N):
-    """The tuner's search space: n-tile width, G stages and epilogue warps change how the work
-    is cut, never a result. Log-likelihoods and (residual mode) gradients are bit-identical
-    across every configuration valid for the shape (6 stages need the resident operand)."""
+def test_every_tile_configuration_gives_the_same_bits(spa, monkeypatch, n, p, N):
+    """The tuner's search space: n-tile width, G stages, epilogue warps and where the resident
+    particle operand lives (shared or tensor memory) change how the work is cut, never a
+    result. Log-likelihoods and (residual mode) gradients are bit-identical across every
+    configuration valid for the shape (configurations 3-5 need the resident operand)."""
     reg = synth.make_region(n, p, 0.9, (0.4, -0.3), seed=53)
     B = synth.random_particles(N, p, 0.05, seed=54)
+    monkeypatch.delenv("SPA_TILE_CONFIG", raising=False)  # would override spa_set_tile_config
+    monkeypatch.delenv("SPA_LOGLIK_BN", raising=False)
     lls, grads = {}, {}
     with spa.Region(reg.G, reg.y, 2.0) as r:
-        for cfg in range(4):
+        for cfg in range(6):
             r.set_tile_config(cfg)
             lls[cfg] = r.loglik(B)
             _, grads[cfg] = r.grad(B, 0.0)
             got, src = r.tile_config()
-            if p + 1 <= 256 or cfg != 3:
+            if p + 1 <= 256 or cfg < 3:
                 assert (got, src) == (cfg, 0)
-    for cfg in range(1, 4):
+    for cfg in range(1, 6):
         assert np.array_equal(lls[0].view(np.uint64), lls[cfg].view(np.uint64)), cfg
         assert np.array_equal(grads[0].view(np.uint32), grads[cfg].view(np.uint32)), cfg
 
