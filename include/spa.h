@@ -218,7 +218,7 @@ int64_t spa_last_launch_count(const spa_ctx* ctx);
  * None of these faults, traps or hangs the GPU. */
 int spa_set_wait_limit(spa_ctx* ctx, uint64_t limit_ns);
 
-/* Individuals per n-tile (128 or 256) of the tensor-core likelihood kernel for the
+/* Individuals per n-tile (128, 224 or 256) of the tensor-core likelihood kernel for the
  * context's current workspace (its tile configuration's, below), or 0 before the first run.
  * The environment variable SPA_LOGLIK_BN=128|256, read when a workspace is created, fixes
  * it. The width does not change any result (partial sums are per 32 individuals either way). */
@@ -231,15 +231,18 @@ int spa_loglik_tile_width(const spa_ctx* ctx);
  *   2: 256, 3 stages, 8 warps                          3: 128, 6 stages, 16 warps (p <= 255)
  *   4: 256, 6 stages, 8 warps, the particle operand held in tensor memory (p <= 255)
  *   5: 128, 12 stages, 16 warps, the particle operand held in tensor memory (p <= 255)
- * A shape takes SPA_TILE_CONFIG=0..5 (or SPA_LOGLIK_BN) from the environment, else the value
+ *   6: 224, 4 stages, 8 warps, a compact resident particle operand (p <= 255 with the last of
+ *      four k-blocks at most 32 columns wide: (p + 1) mod 64 in 1..32, or p < 192)
+ * A shape takes SPA_TILE_CONFIG=0..6 (or SPA_LOGLIK_BN) from the environment, else the value
  * fixed by spa_set_tile_config, else the nearest shape of the tile table (a JSON file written
  * by the package's tune_tiles.py on a GB300: SPA_TILE_TABLE, else tuning/loglik_tiles.json
  * beside the package), else the tuner times every valid configuration once per process. No
  * configuration changes any result: the partial sums are per 32 individuals whatever the tile. */
 int spa_loglik_tile_config(const spa_ctx* ctx, int32_t* source);
-/* Fix the tile configuration (0..5; -1 returns to the table and tuner) for later runs of the
+/* Fix the tile configuration (0..6; -1 returns to the table and tuner) for later runs of the
  * context: it replaces the context's workspace and captured graph. An invalid configuration
- * for the shape (3..5 with p > 255) is ignored at the next run. SPA_EINVAL if out of range. */
+ * for the shape (3..6 with p > 255, 6 with a wide last k-block) is ignored at the next run.
+ * SPA_EINVAL if out of range. */
 int spa_set_tile_config(spa_ctx* ctx, int32_t cfg);
 
 /* Enqueue `reps` launches of the context's likelihood kernel (split-BF16 tcgen05 or

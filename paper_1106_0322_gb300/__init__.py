@@ -310,7 +310,7 @@ class Region:
         return int(load().spa_loglik_tile_width(self._h))
 
     def tile_config(self):
-        """(configuration 0..5 or -1 before the first run, source: 0 fixed, 1 table, 2 timed)."""
+        """(configuration 0..6 or -1 before the first run, source: 0 fixed, 1 table, 2 timed)."""
         src = C.c_int32(0)
         cfg = int(load().spa_loglik_tile_config(self._h, C.byref(src)))
         return cfg, int(src.value)

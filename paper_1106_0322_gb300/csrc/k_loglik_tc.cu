@@ -57,7 +57,12 @@ template <int BN, int STAGES, int AR = 0>
 struct TcCfg {
     static constexpr int A_TILE = BM * BK * 2;
     static constexpr int B_TILE = BN * BK * 2;
-    static constexpr int A_RES = AR == 1 ? KB_RES * 2 * A_TILE : 0;
+    // A compact resident A (BN = 224, whose four G stages fill the rest of shared memory):
+    // three full k-blocks, then a last k-block at most 32 columns wide (A_hi, then A_lo
+    // 8 KB on). Only shapes whose fourth k-block is narrow (or absent) take it.
+    static constexpr bool COMPACT = AR == 1 && BN == 224;
+    static constexpr int TAIL_LO = COMPACT ? BM * 32 * 2 : A_TILE;  // A_lo's offset in the last k-block
+    static constexpr int A_RES = AR == 1 ? (COMPACT ? 3 * 2 * A_TILE + 2 * TAIL_LO : KB_RES * 2 * A_TILE) : 0;
     static constexpr int STAGE = AR ? B_TILE : 2 * A_TILE + B_TILE;
     // accumulator buffers, and the TMEM column of A (AR = 2): A_hi in 8 columns per K = 16
     // step (two BF16 per 32-bit column), then A_lo
@@ -69,7 +74,7 @@ struct TcCfg {
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
     static constexpr int BYTES = SLOT_OFF + 16;
     static constexpr int SMEM = BYTES + 1024;  // slack for the 1024-byte alignment of the tiles
-    static constexpr uint32_t TMEM_COLS = AR == 2 ? 512u : (uint32_t)(2 * BN);
+    static constexpr uint32_t TMEM_COLS = (AR == 2 || 2 * BN > 256) ? 512u : 256u;
     static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "TMEM allocation must be a power of two");
@@ -419,6 +424,11 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                 const uint32_t a_tail = t.tw ? (uint32_t)(BM * t.tw * 2) : (uint32_t)C::A_TILE;
                 const uint32_t b_tail = t.tw ? (uint32_t)(BN * t.tw * 2) : (uint32_t)C::B_TILE;
                 bool a_first = false;  // the epoch's first unit: A's k-blocks go out between its G stages
+                if (C::COMPACT && t.kblocks == KB_RES && t.tw == 0) {  // would overrun the compact A
+                    atomicOr(err, DERR_INPUT);
+                    ok = false;
+                    break;
+                }
                 if (AR == 1 && t.key != cur_key) {
                     ++epoch;
                     // the previous epoch's MMAs must be done with the resident A
@@ -439,9 +449,10 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                         const uint32_t a = sbase + (uint32_t)(kb * 2 * C::A_TILE);
                         const bool tail = t.tw && kb == kb_last;
                         const CUtensorMap* ma = tail ? t.At : t.A;
+                        const uint32_t lo = (tail || kb == 3) ? (uint32_t)C::TAIL_LO : (uint32_t)C::A_TILE;
                         mbar_arrive_expect_tx(AFULL_BAR(kb), tail ? 2u * a_tail : 2u * (uint32_t)C::A_TILE);
                         tma_load_2d(a, ma, AFULL_BAR(kb), kb * BK, t.mt * BM);
-                        tma_load_2d(a + C::A_TILE, ma, AFULL_BAR(kb), t.Kp + kb * BK, t.mt * BM);
+                        tma_load_2d(a + lo, ma, AFULL_BAR(kb), t.Kp + kb * BK, t.mt * BM);
                         a_par ^= 1u << kb;
                         ++a_issued;
                     }
@@ -542,8 +553,9 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                         for (int ks = 0; ks < nks; ++ks) umma_bf16_ta(d, alo + 8u * ks, bg + 2u * ks, IDESC, 1u);
                     } else {
                         const uint32_t a = AR ? sbase + (uint32_t)(kb * 2 * C::A_TILE) : st;
+                        const uint32_t lo = (AR && (rb != 128u || kb == 3)) ? (uint32_t)C::TAIL_LO : (uint32_t)C::A_TILE;
                         const uint64_t ahi = sdesc_swz(a, rb);
-                        const uint64_t alo = sdesc_swz(a + C::A_TILE, rb);
+                        const uint64_t alo = sdesc_swz(a + lo, rb);
                         for (int ks = 0; ks < nks; ++ks)  // +32 bytes per K = 16 step inside the swizzle row
                             umma_bf16(d, ahi + 2u * ks, bg + 2u * ks, IDESC, (kb | ks) != 0 ? 1u : 0u);
                         for (int ks = 0; ks < nks; ++ks) umma_bf16(d, alo + 2u * ks, bg + 2u * ks, IDESC, 1u);
@@ -564,7 +576,10 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
     } else {
         // --------------------------------------------------------------- epilogue
         using E = Epi<EW>;
-        constexpr int CPW = BN / 32 / E::GROUPS;  // 32-column chunks per warp and tile
+        // 32-column chunks per warp and tile, rounded up: with BN = 224 the second column group
+        // has 3 chunks, and its fourth load reads TMEM columns past the tile (inside the
+        // allocation), which the valid-column count then skips
+        constexpr int CPW = (BN / 32 + E::GROUPS - 1) / E::GROUPS;
         const int quad = warp & 3;                // TMEM lane quadrant this warp may access
         const int grp = (warp - 2) >> 2;          // column group
         const int row = quad * 32 + lane;
@@ -591,7 +606,9 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
             const uint32_t b = (uint32_t)(lt % C::NACC), aph = (uint32_t)((lt / C::NACC) & 1);
             if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
             tc_fence_after();
-            const int valid0 = t.n - t.nt * BN - col0;  // valid columns from col0 on
+            // valid columns from col0 on: up to the last individual and to the tile's edge (a
+            // rounded-up chunk count reaches past BN when BN / 32 is odd)
+            const int valid0 = min(t.n - t.nt * BN, BN) - col0;
             const uint32_t tbase = tmem_base + lane_addr + b * (uint32_t)BN + (uint32_t)col0;
             const int64_t prow = (int64_t)t.mt * BM + row;
             const int64_t gc0 = ((int64_t)t.nt * BN + col0) >> 5;  // global index of the first chunk
@@ -954,6 +971,8 @@ cudaError_t tc_init_attributes()
     SET_TC(256, 3, true, false, 8);
     SET_TC(128, 4, true, true, 8);
     SET_TC(128, 4, true, false, 8);
+    SET_TC(224, 4, false, true, 8);
+    SET_TC(224, 4, true, true, 8);
 #define SET_TC1(BN_, S_, AR_, EW_) SET_SMEM((k_loglik_tc<BN_, S_, false, AR_, EW_>), (TcCfg<BN_, S_, AR_>::SMEM))
     SET_TC1(256, 6, 2, 8);
     SET_TC1(128, 12, 2, 16);
@@ -965,14 +984,22 @@ cudaError_t tc_init_attributes()
     return e;
 }
 
-int tc_config_bn(int cfg) { return (cfg == 1 || cfg == 3 || cfg == 5) ? 128 : 256; }
+int tc_config_bn(int cfg) { return (cfg == 1 || cfg == 3 || cfg == 5) ? 128 : (cfg == 6 ? 224 : 256); }
 
-bool tc_config_valid(int cfg, bool resident) { return cfg >= 0 && cfg < TC_CONFIGS && (cfg < 3 || resident); }
+bool tc_config_valid(int cfg, int64_t p)
+{
+    const int ksteps = (int)((p + 1 + 15) / 16), kblocks = (ksteps + 3) / 4;
+    const bool resident = kblocks <= KB_RES;
+    const bool narrow_last = kblocks < KB_RES || ksteps - 4 * (kblocks - 1) <= 2;  // fits a compact A
+    if (cfg < 0 || cfg >= TC_CONFIGS) return false;
+    if (cfg >= 3 && !resident) return false;
+    return cfg != 6 || narrow_last;
+}
 
 TcPlan tc_plan(int64_t n, int p, int64_t N_pad, int num_sms, int cfg)
 {
     TcPlan pl;
-    pl.cfg = (cfg >= 0 && cfg < TC_CONFIGS) ? cfg : ((n <= 128) ? 1 : 0);
+    pl.cfg = tc_config_valid(cfg, p) ? cfg : ((n <= 128) ? 1 : 0);  // an invalid choice falls back
     pl.BN = tc_config_bn(pl.cfg);
     pl.n_tiles = (int)((n + pl.BN - 1) / pl.BN);
     pl.m_tiles = (int)(N_pad / BM);
@@ -1018,6 +1045,10 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
 #define TC_FOR_CONFIG(cfg, resid, ar, VISIT, VISIT_TA)                                \
     do {                                                                              \
         if (resid) {                                                                  \
+            if (tc_config_bn(cfg) == 224) {                                           \
+                if (ar) VISIT(224, 4, true, true, 8);                                 \
+                VISIT(256, 3, true, false, 8);                                        \
+            }                                                                         \
             if (tc_config_bn(cfg) == 256) {                                           \
                 if (ar) VISIT(256, 3, true, true, 8);                                 \
                 VISIT(256, 3, true, false, 8);                                        \
@@ -1026,6 +1057,9 @@ bool tc_make_map_B_tail(CUtensorMap* map, const __nv_bfloat16* Gbf, int64_t n, i
             VISIT(128, 4, true, false, 8);                                            \
         }                                                                             \
         switch (cfg) {                                                                \
+        case 6:                                                                       \
+            if (ar) VISIT(224, 4, false, true, 8);                                    \
+            VISIT(256, 3, false, false, 8);                                           \
         case 4:                                                                       \
             if (ar) VISIT_TA(256, 6, 8);                                              \
             if (ar) VISIT(256, 3, false, true, 8);                                    \

@@ -318,7 +318,7 @@ int ensure_mapB(spa_ctx* c, int BN)
 // sets how evenly the (particle-tile, n-tile) units spread over the SMs, how often each
 // particle tile is streamed again and how the epilogue hides its latencies. The result does
 // not depend on it: the partial sums are per 32-individual chunk whatever the tile. A shape
-// (device, N_pad, n, p) takes, in this order: SPA_TILE_CONFIG=0..5 (or SPA_LOGLIK_BN=256|128,
+// (device, N_pad, n, p) takes, in this order: SPA_TILE_CONFIG=0..6 (or SPA_LOGLIK_BN=256|128,
 // configurations 0|1) from the environment; a configuration fixed on the context
 // (spa_set_tile_config); the nearest entry of the tile table, a JSON file written by the
 // library's tuning script on a GB300 (SPA_TILE_TABLE, else tuning/loglik_tiles.json beside the
@@ -396,7 +396,7 @@ int table_config(int64_t n, int64_t p, int64_t N_pad, bool resident)
             cfg = e.cfg;
         }
     }
-    return (best <= 0.75 && tc_config_valid(cfg, resident)) ? cfg : -1;
+    return (best <= 0.75 && tc_config_valid(cfg, p)) ? cfg : -1;
 }
 
 int tune_tile(spa_ctx* c)
@@ -405,7 +405,7 @@ int tune_tile(spa_ctx* c)
     const bool resident = tc_plan_resident(tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, 0));
     if (const char* env = std::getenv("SPA_TILE_CONFIG")) {
         const int v = std::atoi(env);
-        if (tc_config_valid(v, resident)) {
+        if (tc_config_valid(v, c->p)) {
             w.cfg_source = 0;
             return v;
         }
@@ -417,7 +417,7 @@ int tune_tile(spa_ctx* c)
             return v == 128 ? 1 : 0;
         }
     }
-    if (tc_config_valid(c->tile_cfg, resident)) {
+    if (tc_config_valid(c->tile_cfg, c->p)) {
         w.cfg_source = 0;
         return c->tile_cfg;
     }
@@ -450,7 +450,7 @@ int tune_tile(spa_ctx* c)
     int best = 0;
     float best_ms = -1.0f;
     for (int cfg = 0; cfg < TC_CONFIGS; ++cfg) {
-        if (!tc_config_valid(cfg, resident)) continue;
+        if (!tc_config_valid(cfg, c->p)) continue;
         const TcPlan plan = tc_plan(c->n, (int)c->p, w.N_pad, c->num_sms, cfg);
         TcMaps m;
         m.A = w.mapA;

@@ -285,12 +285,15 @@ cudaError_t launch_best_particle(const MhState& s, const float* beta, int64_t N,
 //   3       128              6         16              shared memory (resident only)
 //   4       256              6         8               tensor memory (resident only)
 //   5       128              12        16              tensor memory (resident only)
-// Configurations 3-5 need the particle operand resident (K <= 256). The residual (MALA)
+//   6       224              4         8               shared memory, compact (resident, and the
+//                                                      last of four k-blocks at most 32 wide)
+// Configurations 3-6 need the particle operand resident (K <= 256). The residual (MALA)
 // variant uses the configuration's BN with 3 or 4 stages, 8 epilogue warps and A in shared
 // memory. Every configuration gives the same partial sums bit for bit (one per 32 individuals).
-constexpr int TC_CONFIGS = 6;
+constexpr int TC_CONFIGS = 7;
 int tc_config_bn(int cfg);
-bool tc_config_valid(int cfg, bool resident);
+// whether configuration cfg can run the kernel for p markers (K = p + 1)
+bool tc_config_valid(int cfg, int64_t p);
 struct TcPlan {
     int cfg;         // tile configuration
     int BN;          // individuals per n-tile (128 or 256)

@@ -27,7 +27,8 @@ PARTICLES = (4096, 8192, 16384)
 CONFIGS = {0: "BN 256, 3 stages, 16 epilogue warps", 1: "BN 128, 4 stages, 16 epilogue warps",
            2: "BN 256, 3 stages, 8 epilogue warps", 3: "BN 128, 6 stages, 16 epilogue warps (p <= 255)",
            4: "BN 256, 6 stages, 8 epilogue warps, particle operand in tensor memory (p <= 255)",
-           5: "BN 128, 12 stages, 16 epilogue warps, particle operand in tensor memory (p <= 255)"}
+           5: "BN 128, 12 stages, 16 epilogue warps, particle operand in tensor memory (p <= 255)",
+           6: "BN 224, 4 stages, 8 epilogue warps, compact resident particle operand (p <= 255, last k-block <= 32 wide)"}
 
 
 def time_config(spa, region, cfg, N, stream, sched):

@@ -47,7 +47,7 @@ def test_benchmarked_workload_prefix_matches_oracle(spa, name):
     with spa.Region(reg.G, reg.y, w["nu"], config=cfg) as r:
         g = [r.run(sched, w["N"], w["M"], s) for s in range(1, R + 1)]
         same = r.run(sched, w["N"], w["M"], 5)
-        assert r.loglik_tile_width() in (128, 256)
+        assert r.loglik_tile_width() in (128, 224, 256)
     ocfg = oracle.make_config(move=w["move"])
     o = [oracle.run(reg.G, reg.y, w["nu"], sched, w["N"], w["M"], seed=100 + s, cfg=ocfg) for s in range(R)]
     _check(_two_sample_z([x["mean"] for x in g], [x["mean"] for x in o], 2e-4), f"{name} mean")

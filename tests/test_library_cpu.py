@@ -149,8 +149,9 @@ def test_noalloc_resampling_rejects_unusable_buffers(monkeypatch):
 
 def test_committed_tile_table_is_well_formed():
     """The likelihood kernel's tile table (written on a GB300 by paper_1106_0322_gb300/tune_tiles.py)
-    lists, per shape, a configuration valid for that shape's kernel mode (configurations 3-5
-    only with the particle operand resident: p + 1 <= 256) and the times it chose from."""
+    lists, per shape, a configuration valid for that shape's kernel mode (configurations 3-6
+    only with the particle operand resident: p + 1 <= 256; 6 only with a last k-block at
+    most 32 columns wide) and the times it chose from."""
     import json
 
     path = os.path.join(ROOT, "paper_1106_0322_gb300", "tuning", "loglik_tiles.json")
@@ -159,7 +160,9 @@ def test_committed_tile_table_is_well_formed():
     assert len(doc["entries"]) > 0
     for e in doc["entries"]:
         assert e["n"] > 0 and e["p"] > 0 and e["N_pad"] % 128 == 0
-        assert 0 <= e["config"] <= 5
+        assert 0 <= e["config"] <= 6
         assert e["config"] < 3 or e["p"] + 1 <= 256
+        ksteps = (e["p"] + 1 + 15) // 16
+        assert e["config"] != 6 or ksteps <= 12 or ksteps % 4 in (1, 2)
         us = {int(k): v for k, v in e["us"].items()}
         assert e["config"] == min(us, key=us.get)
