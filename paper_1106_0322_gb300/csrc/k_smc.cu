@@ -40,6 +40,24 @@ __device__ __forceinline__ float prior_term(float b, float inv_ac, int de)
 }
 __device__ __forceinline__ double prior_coef(PriorArgs pr, double c) { return pr.de ? -1.0 / c : -((double)pr.a + 1.0); }
 
+// The Gt terms of four coordinates at once: log1p(x0) + ... + log1p(x3) with x = |b|/(a c),
+// as the logarithm of the product of the factors 1 + x_k (one logarithm instead of four).
+// Each factor and product carries a relative rounding of 2^-24, so the sum is accurate to
+// a few 1e-7 in absolute terms, about the same as four rounded log1p terms of moderate size.
+// Products beyond FP32 range (factors near 1e9) take the four logarithms instead. Every
+// kernel that forms a state's log-prior sum for the MH test (the moves, and the reweighting's
+// sum at the new scale) uses this grouping when p % 4 == 0, so that the test compares one
+// function of the state.
+__device__ __forceinline__ float prior_terms4(float4 b, float inv_ac)
+{
+    const float f0 = fmaf(fabsf(b.x), inv_ac, 1.0f), f1 = fmaf(fabsf(b.y), inv_ac, 1.0f);
+    const float f2 = fmaf(fabsf(b.z), inv_ac, 1.0f), f3 = fmaf(fabsf(b.w), inv_ac, 1.0f);
+    const float q = (f0 * f1) * (f2 * f3);
+    if (q <= FLT_MAX) return logf(q);
+    return log1pf(fabsf(b.x) * inv_ac) + log1pf(fabsf(b.y) * inv_ac) + log1pf(fabsf(b.z) * inv_ac) +
+           log1pf(fabsf(b.w) * inv_ac);
+}
+
 // The prior's gradient in MALA's drift. The drift can be any fixed function of the state:
 // the MH test evaluates the forward and reverse proposal densities with this same function,
 // so the fast quotient (within 2 ulp) keeps each step's kernel exactly pi_t-invariant.
@@ -108,11 +126,32 @@ __device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? 
 // of the MH ratio are between nearby values, so they are formed in FP32 from the pairs:
 // s' - s is exact when the two are within a factor of two, and the c parts carry the rest.
 
-// The proposal's log-likelihood pair: the warp sums the partials, then adds y . eta.
-__device__ __forceinline__ FSum proposal_loglik(const MhState& s, int64_t i, int lane)
+// The block's proposals' softplus partials, gathered for the MH tests (one warp per particle,
+// WARPS particles per block): thread t adds the chunks q = t / WARPS, t / WARPS + 32, ... of
+// particle WARPS blockIdx.x + t % WARPS, so the WARPS threads of a group read one 32-byte
+// sector per chunk, where a warp per particle touches one sector per lane. Slice s of a
+// particle is exactly the compensated partial sum that lane s of a warp-per-particle loop
+// over q = s, s + 32, ... forms, so the warp's tree over the slices gives the same bits.
+struct PartSlices {
+    float2 v[32][WARPS];
+};
+__device__ __forceinline__ void gather_partials(const MhState& s, int64_t N, PartSlices& sh)
+{
+    const int k = threadIdx.x % WARPS, slice = threadIdx.x / WARPS;
+    const int64_t i = (int64_t)blockIdx.x * WARPS + k;
+    FSum L;
+    if (i < N)
+        for (int q = slice; q < s.n_parts; q += 32) L.add(s.partial[(int64_t)q * s.ld_part + i]);
+    sh.v[slice][k] = make_float2(L.s, L.c);
+}
+
+// The proposal's log-likelihood pair: the warp sums the slices, then adds y . eta.
+__device__ __forceinline__ FSum proposal_loglik(const MhState& s, const PartSlices& sh, int64_t i, int lane)
 {
     FSum L;
-    for (int q = lane; q < s.n_parts; q += 32) L.add(s.partial[(int64_t)q * s.ld_part + i]);
+    const float2 v = sh.v[lane][threadIdx.x >> 5];
+    L.s = v.x;
+    L.c = v.y;
     L = warp_sum(L);
     const float2 yd = s.ydq[i];
     L.add(yd.x);
@@ -137,10 +176,10 @@ __device__ __forceinline__ void draw_accept_logu(const MhState& s, int64_t N, in
 // q-correction. Lane 0 decides with the accept uniform of move m_prev (drawn by the kernel
 // that proposed it) and, on acceptance, moves the proposal's log-likelihood and log-prior
 // into the current state. Returns the decision on every lane.
-__device__ __forceinline__ bool mh_decide(const MhState& s, int64_t i, int lane, float coef, float extra,
-                                          uint32_t m_prev, uint32_t* err)
+__device__ __forceinline__ bool mh_decide(const MhState& s, const PartSlices& sh, int64_t i, int lane, float coef,
+                                          float extra, uint32_t m_prev, uint32_t* err)
 {
-    const FSum L = proposal_loglik(s, i, lane);
+    const FSum L = proposal_loglik(s, sh, i, lane);
     int accept = 0;
     if (lane == 0) {
         const float2 L0 = s.llq[i];
@@ -192,11 +231,14 @@ __device__ __forceinline__ void rw_group(const MoveArgs& a, int p, int g, bool l
                                : b0;
         st4(dst + j0, b);
         const float4 v = ld4(a.vy + j0);
+        if (de) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            lt.add(prior_term(comp(b, k), inv_ac, de));
-            yd = fmaf(comp(b, k), comp(v, k), yd);
+            for (int k = 0; k < 4; ++k) lt.add(fabsf(comp(b, k)));
+        } else {
+            lt.add(prior_terms4(b, inv_ac));
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) yd = fmaf(comp(b, k), comp(v, k), yd);
         if (Arow) off += pack_coord4(Arow, a.Kp, j0, b, ld4(a.l2e_over_s + j0), ld4(a.mean_f + j0));
     } else {
 #pragma unroll
@@ -264,15 +306,20 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
                                                   const uint64_t* __restrict__ seedp, int noise, uint32_t* err)
 {
     __shared__ int accw[BLOCK / 32];
+    __shared__ PartSlices parts;
     grid_dependency_wait();  // the previous kernel (the likelihood GEMM) has finished
     grid_launch_dependents();
+    if (DECIDE) {
+        gather_partials(a.mh, N, parts);
+        __syncthreads();
+    }
     const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
     bool acc = false;
     if (i < N) {
         const uint64_t seed = (noise || DECIDE) ? *seedp : 0ull;
-        if (DECIDE) acc = mh_decide(a.mh, i, lane, sk.y, 0.0f, m_prev, err);
+        if (DECIDE) acc = mh_decide(a.mh, parts, i, lane, sk.y, 0.0f, m_prev, err);
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         float* dst = a.beta_p + i * p;
         float* cur = a.beta + i * p;
@@ -318,6 +365,11 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                                                     uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
 {
     __shared__ int accw[BLOCK / 32];
+    __shared__ PartSlices parts;
+    if (DECIDE) {
+        gather_partials(a.mh, N, parts);
+        __syncthreads();
+    }
     const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
@@ -340,7 +392,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
             bwd = warp_sum(bwd);
             const float2 fw = a.fwd[i];
             const float extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
-            acc = mh_decide(a.mh, i, lane, sk.y, extra, m_prev, err);
+            acc = mh_decide(a.mh, parts, i, lane, sk.y, extra, m_prev, err);
         }
         const float* src = (acc ? a.beta_p : a.beta) + i * p;
         const float* gsrc = (acc ? a.gl_p : a.gl) + i * p;
@@ -351,8 +403,10 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
         FSum lt, fw;
         float yd = 0.0f, off = 0.0f;
         const int groups = (p + 3) >> 2;
+        const bool grouped = (p & 3) == 0 && !pr.de;  // the four-coordinate prior term
         for (int g = lane; g < groups; g += 32) {
             const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
+            float bq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int j = 4 * g + k;
@@ -368,11 +422,13 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
                     dst[j] = b;
                     const float d = (b - b0) - drift;
                     fw.add(d * d * a.inv_D[j]);
-                    lt.add(prior_term(b, sk.w, pr.de));
+                    bq[k] = b;
+                    if (!grouped) lt.add(prior_term(b, sk.w, pr.de));
                     yd = fmaf(b, a.vy[j], yd);
                     if (Arow) off += pack_coord(Arow, a.Kp, j, b, a.l2e_over_s, a.mean_f);
                 }
             }
+            if (grouped) lt.add(prior_terms4(make_float4(bq[0], bq[1], bq[2], bq[3]), sk.w));
         }
         lt = warp_sum(lt);
         fw = warp_sum(fw);
@@ -517,7 +573,10 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
                                                       const uint64_t* __restrict__ seedp, uint32_t* err)
 {
     __shared__ int accw[BLOCK / 32];
+    __shared__ PartSlices parts;
     grid_dependency_wait();
+    gather_partials(a.mh, N, parts);
+    __syncthreads();
     const float4 sk = stepk[t];
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
@@ -540,7 +599,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
             const float2 fw = a.fwd[i];
             extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
         }
-        acc = mh_decide(a.mh, i, lane, sk.y, extra, m_prev, err);
+        acc = mh_decide(a.mh, parts, i, lane, sk.y, extra, m_prev, err);
         if (acc) {
             const float* src = a.beta_p + i * p;
             float* dst = a.beta + i * p;
@@ -565,10 +624,13 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
 __global__ void __launch_bounds__(BLOCK) k_finish_loglik(MhState s, int64_t N, double* __restrict__ logw,
                                                         double* __restrict__ ll_out, uint32_t* __restrict__ err)
 {
+    __shared__ PartSlices parts;
+    gather_partials(s, N, parts);
+    __syncthreads();
     const int64_t i = warp_global_id();
     const int lane = threadIdx.x & 31;
     if (i >= N) return;
-    const FSum L = proposal_loglik(s, i, lane);
+    const FSum L = proposal_loglik(s, parts, i, lane);
     if (lane != 0) return;
     if (!isfinite(L.s)) atomicOr(err, DERR_NONFINITE);
     s.llq[i] = make_float2(L.s, L.c);
@@ -602,11 +664,15 @@ __global__ void __launch_bounds__(RW_THREADS) k_reweight(const float* __restrict
         const int64_t i = base + q;
         FSum sdiff, snew;
         if (i < N) {
+            const bool grouped = (p & 3) == 0 && !pr.de;  // the moves' four-coordinate prior term
             for (int j = lane; j < p; j += 32) {
                 const float x = fabsf(beta[i * p + j]);
                 sdiff.add(pr.de ? x : log1pf(x * k1 / (kc * (kac + x))));
-                snew.add(prior_term(x, inv_ac, pr.de));
+                if (!grouped) snew.add(prior_term(x, inv_ac, pr.de));
             }
+            if (grouped)
+                for (int g = lane; 4 * g < p; g += 32)
+                    snew.add(prior_terms4(*reinterpret_cast<const float4*>(beta + i * p + 4 * g), inv_ac));
         }
         sdiff = warp_sum(sdiff);
         snew = warp_sum(snew);
