@@ -374,6 +374,28 @@ def test_every_tile_configuration_gives_the_same_bits(spa, monkeypatch, n, p, N)
         assert np.array_equal(grads[0].view(np.uint32), grads[cfg].view(np.uint32)), cfg
 
 
+@pytest.mark.parametrize("move", ["rw", "mala"])
+def test_sweep_is_the_same_for_every_tile_configuration(spa, monkeypatch, move):
+    """The partials do not depend on the tile, so neither does anything downstream: whole
+    sweeps (summaries, evidence, ESS, acceptance) are bit-identical across every valid
+    configuration, shared-memory and tensor-memory residence and the 224-wide n-tiles
+    included, with a ragged n and N."""
+    monkeypatch.delenv("SPA_TILE_CONFIG", raising=False)
+    monkeypatch.delenv("SPA_LOGLIK_BN", raising=False)
+    reg = synth.make_region(700, 44, 0.9, (0.5, -0.4), seed=57)
+    sched = synth.geometric_schedule(6)
+    outs = {}
+    with spa.Region(reg.G, reg.y, 2.0, config=spa.make_config(move=move)) as r:
+        for cfg in range(7):
+            r.set_tile_config(cfg)
+            outs[cfg] = r.run(sched, N=700, moves_per_step=2, seed=11)
+            assert r.tile_config() == (cfg, 0)  # p + 1 = 45: every configuration is valid
+    for cfg in range(1, 7):
+        for key in ("mean", "quantile", "conc", "ess", "log_z_inc", "accept_rate"):
+            a, b = np.asarray(outs[0][key]), np.asarray(outs[cfg][key])
+            assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), (cfg, key)
+
+
 def test_tile_table_entry_is_used(tmp_path):
     """A tile-table entry for a nearby shape decides the configuration without timing."""
     import json
