@@ -166,6 +166,10 @@ struct spa_ctx {
     double nu = 1.0;
     PriorArgs pr{1.0f, 0};
     int device = 0, num_sms = 0;
+    // SMs the tensor-core launches are sized for (0: all of them). A batch sets it while it
+    // captures its regions' sweeps side by side (see batch_plan_sms); buffers are always
+    // sized for all SMs, which is the largest any plan needs.
+    int plan_sms = 0;
     cudaStream_t own_stream = nullptr;
     // the key transpose and the summaries of step t run on side_stream beside step t + 1
     // (fork after the step's moves; the next step waits for the transpose before it
@@ -628,7 +632,9 @@ struct Enq {
 // gradient of the log-likelihood at the packed particles (beta_p / A) into out, on the
 // tensor cores: residual likelihood pass, C = R G, finish. Also leaves the softplus
 // partials of those particles in w.partial.
-TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, c->num_sms, c->ws.cfg); }
+int plan_sm_count(const spa_ctx* c) { return c->plan_sms > 0 ? c->plan_sms : c->num_sms; }
+
+TcPlan plan_of(const spa_ctx* c) { return tc_plan(c->n, (int)c->p, c->ws.N_pad, plan_sm_count(c), c->ws.cfg); }
 
 TcMaps maps_of(const spa_ctx* c)
 {
@@ -647,6 +653,8 @@ void enq_grad_tail(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     spa_ctx* c = q.c;
     Workspace& w = c->ws;
     const TcPlan plan = plan_of(c);
+    // the K-split from all SMs whatever plan_sm_count says: it sets how the FP32 partial sums
+    // over individuals are grouped, so a batch's gradients stay those of a single run
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st, c->wait_ns));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
@@ -1114,6 +1122,18 @@ void batch_free(spa_batch* b)
 // burn-in, all on the tensor cores. By default the batch is one graph branch per region: on
 // the 64-region batched workload that measured 2.74 s per batch against 3.30 s in lock step,
 // whose joins at every evaluation stop the regions' other kernels from overlapping.
+// The SMs each region's likelihood launches are sized for when a batch runs its regions as
+// graph branches side by side: an eighth of the GPU once 8 or more regions share it, else
+// an equal share. Smaller grids give each CTA more units (the per-CTA set-up and last
+// epilogue are paid fewer times over the batch's work), while the other regions' branches
+// keep the SMs busy. The likelihood partials are per 32 individuals whatever the grid, so
+// the batch's results stay bit-identical to single runs.
+int batch_plan_sms(int num_sms, int32_t R)
+{
+    const int share = R > 0 ? num_sms / (R < 8 ? R : 8) : num_sms;
+    return share > 0 ? share : 1;
+}
+
 bool batch_lockstep(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args)
 {
     const char* env = std::getenv("SPA_BATCH_MODE");
@@ -1341,7 +1361,9 @@ int batch_build(spa_batch* b, spa_ctx* const* ctxs, int32_t R, const spa_batch_a
             spa_ctx* c = b->ctxs[r];
             ee = cudaStreamWaitEvent(c->stream(), b->fork, 0);
             if (ee != cudaSuccess) break;
+            c->plan_sms = batch_plan_sms(c->num_sms, R);  // only while this batch's graph is captured
             const int64_t n = enqueue_sweep(c, b->T[r], args->moves_per_step[r], &ee);
+            c->plan_sms = 0;
             b->per_ctx_launches.push_back(n);
             b->launches += n;
             if (ee == cudaSuccess) ee = cudaEventRecord(b->joins[r], c->stream());
