@@ -694,10 +694,14 @@ __global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
 
 // ----------------------------------------------------------------------- adjoint
 // C[k, j] = sum_i r_ki g_ij for 128 particles x BN2 markers, contracting over the
-// individuals of this CTA's k-range: A = [R_hi | R_lo] (N_pad x 2 n_r), B = G^T
-// (markers x n_r, exact BF16), both K-major with the 128-byte swizzle. One output tile per
-// CTA; warps 2..5 copy the FP32 accumulator to gpart[ks][particle][marker]. The final
-// gradient (C - m_j sum_i r_ki) / s_j is formed by k_grad_finish.
+// individuals of one K-split range: A = [R_hi | R_lo] (N_pad x 2 n_r), B = G^T (markers x
+// n_r, exact BF16), both K-major with the 128-byte swizzle. A unit is one output tile (mt,
+// pt) of one K-split ks; a CTA takes units blockIdx.x, blockIdx.x + gridDim.x, ... (one unit
+// each when the grid covers them all), with a double-buffered accumulator in TMEM so that a
+// unit's MMAs overlap the previous unit's copy-out. Warps 2..5 copy the FP32 accumulator to
+// gpart[ks][particle][marker]. Every unit runs the same MMAs whichever CTA takes it, so
+// the partials do not depend on the grid. The final gradient (C - m_j sum_i r_ki) / s_j is
+// formed by k_grad_finish.
 constexpr int ADJ_THREADS = 64 + 32 * 4;
 
 template <int BN2, int STAGES>
@@ -706,10 +710,11 @@ struct AdjCfg {
     static constexpr int B_TILE = BN2 * BK * 2;
     static constexpr int STAGE = 2 * A_TILE + B_TILE;
     static constexpr int BAR_OFF = STAGES * STAGE;
-    static constexpr int NBARS = 2 * STAGES + 2;  // full, empty, acc_full, drain
+    static constexpr int NBARS = 2 * STAGES + 5;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
     static constexpr int SMEM = SLOT_OFF + 16 + 1024;
-    static constexpr uint32_t TMEM_COLS = 256;
+    static constexpr uint32_t ACC_STRIDE = 256;  // TMEM columns between the two accumulator buffers
+    static constexpr uint32_t TMEM_COLS = 512;
     static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
     static_assert(SMEM <= 232448, "shared memory budget");
     static_assert(BN2 % 16 == 0 && BN2 <= 256, "MMA N");
@@ -727,24 +732,31 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = sbase + C::BAR_OFF;
-    const uint32_t accf_bar = bar0 + 8u * (uint32_t)(2 * STAGES);
-    const uint32_t drain_bar = accf_bar + 8u;
+    const uint32_t drain_bar = bar0 + 8u * (uint32_t)(2 * STAGES + 4);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
 #define FULL_BAR(s) (bar0 + 8u * (uint32_t)(s))
 #define EMPTY_BAR(s) (bar0 + 8u * (uint32_t)(STAGES + (s)))
-    // unit = (mt, pt, ks)
-    const int u = blockIdx.x;
-    const int ks = u % ksplit;
-    const int pt = (u / ksplit) % p_tiles;
-    const int mt = u / (ksplit * p_tiles);
-    const int kb0 = (int)((int64_t)kblocks * ks / ksplit), kb1 = (int)((int64_t)kblocks * (ks + 1) / ksplit);
+#define ACCF_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + (b)))
+#define ACCE_BAR(b) (bar0 + 8u * (uint32_t)(2 * STAGES + 2 + (b)))
+    const int units = m_tiles * p_tiles * ksplit;
+    // unit u = (mt, pt, ks), ks fastest; its K range [kb0, kb1) of k-blocks
+    auto decode = [&](int u, int& mt, int& pt, int& kb0, int& kb1, int& ks) {
+        ks = u % ksplit;
+        pt = (u / ksplit) % p_tiles;
+        mt = u / (ksplit * p_tiles);
+        kb0 = (int)((int64_t)kblocks * ks / ksplit);
+        kb1 = (int)((int64_t)kblocks * (ks + 1) / ksplit);
+    };
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < STAGES; ++q) {
             mbar_init(FULL_BAR(q), 1);
             mbar_init(EMPTY_BAR(q), 1);
         }
-        mbar_init(accf_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(ACCF_BAR(b), 1);
+            mbar_init(ACCE_BAR(b), 4);  // the four epilogue warps
+        }
         mbar_init(drain_bar, 1);
         mbar_fence_init();
     }
@@ -764,15 +776,23 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
-            for (int kb = kb0; kb < kb1; ++kb) {
-                const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
-                if (!mbar_wait_bounded(EMPTY_BAR(q), ph ^ 1u, err, wait_ns)) break;
-                const uint32_t st = sbase + q * C::STAGE;
-                mbar_arrive_expect_tx(FULL_BAR(q), (uint32_t)C::STAGE);
-                tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
-                tma_load_2d(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM);
-                tma_load_2d(st + 2 * C::A_TILE, &mapGT, FULL_BAR(q), kb * BK, pt * BN2);
-                ++it;
+            bool ok = true;
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                int mt, pt, kb0, kb1, ks;
+                decode(u, mt, pt, kb0, kb1, ks);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
+                    if (!mbar_wait_bounded(EMPTY_BAR(q), ph ^ 1u, err, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + q * C::STAGE;
+                    mbar_arrive_expect_tx(FULL_BAR(q), (uint32_t)C::STAGE);
+                    tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
+                    tma_load_2d(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM);
+                    tma_load_2d(st + 2 * C::A_TILE, &mapGT, FULL_BAR(q), kb * BK, pt * BN2);
+                    ++it;
+                }
             }
             const uint32_t last = it < (uint32_t)STAGES ? it : (uint32_t)STAGES;
             for (uint32_t k = 1; k <= last; ++k) {
@@ -784,50 +804,77 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
         if (lane == 0) {
             constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN2);
             uint32_t it = 0;
+            int lt = 0;  // units with a non-empty K range, which use an accumulator buffer
             bool ok = true;
-            for (int kb = kb0; kb < kb1; ++kb) {
-                const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
-                if (!mbar_wait_bounded(FULL_BAR(q), ph, err, wait_ns)) {
+            for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+                int mt, pt, kb0, kb1, ks;
+                decode(u, mt, pt, kb0, kb1, ks);
+                if (kb1 <= kb0) continue;
+                const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+                if (!mbar_wait_bounded(ACCE_BAR(b), aph ^ 1u, err, wait_ns)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t st = sbase + q * C::STAGE;
-                const uint64_t ahi = sdesc_sw128(st), alo = sdesc_sw128(st + C::A_TILE);
-                const uint64_t bg = sdesc_sw128(st + 2 * C::A_TILE);
+                const uint32_t d = tmem_base + b * C::ACC_STRIDE;
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const uint32_t q = it % STAGES, ph = (it / STAGES) & 1u;
+                    if (!mbar_wait_bounded(FULL_BAR(q), ph, err, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + q * C::STAGE;
+                    const uint64_t ahi = sdesc_sw128(st), alo = sdesc_sw128(st + C::A_TILE);
+                    const uint64_t bg = sdesc_sw128(st + 2 * C::A_TILE);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) umma_bf16(tmem_base, ahi + 2u * k, bg + 2u * k, IDESC, (kb > kb0 || k) ? 1u : 0u);
+                    for (int k = 0; k < 4; ++k) umma_bf16(d, ahi + 2u * k, bg + 2u * k, IDESC, (kb > kb0 || k) ? 1u : 0u);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) umma_bf16(tmem_base, alo + 2u * k, bg + 2u * k, IDESC, 1u);
-                umma_commit(EMPTY_BAR(q));
-                ++it;
+                    for (int k = 0; k < 4; ++k) umma_bf16(d, alo + 2u * k, bg + 2u * k, IDESC, 1u);
+                    umma_commit(EMPTY_BAR(q));
+                    ++it;
+                }
+                if (!ok) break;
+                umma_commit(ACCF_BAR(b));
+                ++lt;
             }
-            if (ok) umma_commit(accf_bar);
             umma_commit(drain_bar);
             mbar_drain(drain_bar, 0u, err);
         }
     } else {
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        const int cols = (p - pt * BN2) < BN2 ? (p - pt * BN2) : BN2;
-        if (kb1 > kb0 && mbar_wait_bounded(accf_bar, 0u, err, wait_ns)) {
-            tc_fence_after();
+        int lt = 0;
+        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+            int mt, pt, kb0, kb1, ks;
+            decode(u, mt, pt, kb0, kb1, ks);
+            const int cols = (p - pt * BN2) < BN2 ? (p - pt * BN2) : BN2;
             float* out = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + row) * p + (int64_t)pt * BN2;
+            if (kb1 <= kb0) {
+                for (int c = 0; c < cols; ++c) out[c] = 0.0f;
+                continue;
+            }
+            const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+            if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
+            tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < cols; c += 32) {
                 float v[32];
-                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
+                tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + b * C::ACC_STRIDE + (uint32_t)c, v);
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
                     if (c + k < cols) out[c + k] = v[k];
             }
-        } else if (kb1 <= kb0) {
-            float* out = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + row) * p + (int64_t)pt * BN2;
-            for (int c = 0; c < cols; ++c) out[c] = 0.0f;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ACCE_BAR(b));
+            ++lt;
         }
     }
 #undef FULL_BAR
 #undef EMPTY_BAR
+#undef ACCF_BAR
+#undef ACCE_BAR
     __syncwarp();
     tc_fence_before();
     __syncthreads();
@@ -1160,16 +1207,17 @@ bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n
 }
 
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p,
-                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns)
+                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns, int max_ctas)
 {
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
+    const unsigned grid = (unsigned)((max_ctas > 0 && max_ctas < a.grid) ? max_ctas : a.grid);
     if (a.BN2 == ADJ_BN_SMALL) {
-        k_adjoint_tc<ADJ_BN_SMALL, 3><<<a.grid, ADJ_THREADS, AdjCfg<ADJ_BN_SMALL, 3>::SMEM, st>>>(
+        k_adjoint_tc<ADJ_BN_SMALL, 3><<<grid, ADJ_THREADS, AdjCfg<ADJ_BN_SMALL, 3>::SMEM, st>>>(
             mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns);
     } else {
-        k_adjoint_tc<256, 3><<<a.grid, ADJ_THREADS, AdjCfg<256, 3>::SMEM, st>>>(mapR, mapGT, a.m_tiles, a.p_tiles,
-                                                                               a.kblocks, a.ksplit, (int)a.n_r, p, gpart,
-                                                                               N_pad, err, wait_ns);
+        k_adjoint_tc<256, 3><<<grid, ADJ_THREADS, AdjCfg<256, 3>::SMEM, st>>>(mapR, mapGT, a.m_tiles, a.p_tiles,
+                                                                             a.kblocks, a.ksplit, (int)a.n_r, p, gpart,
+                                                                             N_pad, err, wait_ns);
     }
     return cudaGetLastError();
 }
