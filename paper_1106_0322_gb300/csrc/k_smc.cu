@@ -116,6 +116,8 @@ __device__ __forceinline__ void pack_offset(__nv_bfloat16* __restrict__ Arow, in
 }
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+// read-only path: per-coordinate constants no thread writes while the kernel runs
+__device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float comp(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w)); }
 
@@ -349,6 +351,39 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
 }
 
 // ------------------------------------------------------------ MALA move kernel
+// The reverse move's residual sum of particle i's pending proposal (lane partial, before the
+// warp sum): sum_j (beta_j - beta'_j - (h^2/2) D_j g'_j)^2 / D_j, g' = grad l' + the prior
+// gradient at beta'. VEC (p % 4 == 0): lane l takes the 4-coordinate groups l, l + 32, ...
+// with float4 loads; else coordinates l, l + 32, ...
+template <bool VEC>
+__device__ __forceinline__ FSum mala_reverse(const MoveArgs& a, int64_t i, int p, int lane, float h2, float a1, float ac,
+                                             float inv_c, int de)
+{
+    FSum bwd;
+    const float* b0 = a.beta + i * p;
+    const float* b1 = a.beta_p + i * p;
+    const float* g1 = a.gl_p + i * p;
+    if (VEC) {
+        for (int j0 = 4 * lane; j0 < p; j0 += 128) {
+            const float4 x0 = ld4(b0 + j0), x1 = ld4(b1 + j0), gg = ld4(g1 + j0);
+            const float4 Dv = ldg4(a.sigma + j0), iD = ldg4(a.inv_D + j0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float drift = h2 * comp(Dv, k) * (comp(gg, k) + dlogprior(comp(x1, k), a1, ac, inv_c, de));
+                const float d = (comp(x0, k) - comp(x1, k)) - drift;
+                bwd.add(d * d * comp(iD, k));
+            }
+        }
+    } else {
+        for (int j = lane; j < p; j += 32) {
+            const float drift = h2 * a.sigma[j] * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, de));
+            const float d = (b0[j] - b1[j]) - drift;
+            bwd.add(d * d * a.inv_D[j]);
+        }
+    }
+    return bwd;
+}
+
 // beta' = beta + (h^2/2) D grad log pi_t(beta) + h D^{1/2} xi with D = diag(D_j) and
 // h = lambda p^{-1/6} (written by the column-statistics kernel); grad log pi_t = grad l
 // (stored per particle) + the prior gradient -(a+1) sgn(beta)/(a c + |beta|) (double
@@ -359,7 +394,7 @@ __global__ void __launch_bounds__(BLOCK, 5) k_move_rw(MoveArgs a, int64_t N, int
 // bwd = sum_j (beta_j - beta'_j - (h^2/2) D_j g'_j)^2 / D_j, and runs its MH test with
 // log alpha = l' + lp' - l - lp - (bwd - fwd)/(2h^2); an accepted proposal and its gradient
 // are written back as the state while being read.
-template <bool DECIDE>
+template <bool DECIDE, bool VEC>
 __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
                                                     const float4* __restrict__ stepk, int t, uint32_t m,
                                                     uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
@@ -380,16 +415,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
         const float h = *a.h, h2 = 0.5f * h * h;
         const float* D = a.sigma;
         if (DECIDE) {
-            FSum bwd;
-            const float* b0 = a.beta + i * p;
-            const float* b1 = a.beta_p + i * p;
-            const float* g1 = a.gl_p + i * p;
-            for (int j = lane; j < p; j += 32) {
-                const float drift = h2 * D[j] * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
-                const float d = (b0[j] - b1[j]) - drift;
-                bwd.add(d * d * a.inv_D[j]);
-            }
-            bwd = warp_sum(bwd);
+            const FSum bwd = warp_sum(mala_reverse<VEC>(a, i, p, lane, h2, a1, ac, inv_c, pr.de));
             const float2 fw = a.fwd[i];
             const float extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
             acc = mh_decide(a.mh, parts, i, lane, sk.y, extra, m_prev, err);
@@ -404,7 +430,42 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
         float yd = 0.0f, off = 0.0f;
         const int groups = (p + 3) >> 2;
         const bool grouped = (p & 3) == 0 && !pr.de;  // the four-coordinate prior term
-        for (int g = lane; g < groups; g += 32) {
+        if (VEC) {
+            // p % 4 == 0: the same per-coordinate arithmetic on float4 groups, the state's and
+            // the gradient's rows read and written 16 bytes at a time, the GEMM row 8
+            for (int g = lane; g < groups; g += 32) {
+                const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
+                const int j0 = 4 * g;
+                const float4 x0 = ld4(src + j0), g0 = ld4(gsrc + j0);
+                if (acc) {
+                    st4(cur + j0, x0);
+                    st4(gcur + j0, g0);
+                }
+                const float4 Dv = ldg4(D + j0), sD = ldg4(a.sqrt_D + j0), iD = ldg4(a.inv_D + j0);
+                const float4 v = ldg4(a.vy + j0);
+                float bq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float b0 = comp(x0, k);
+                    const float drift = h2 * comp(Dv, k) * (comp(g0, k) + dlogprior(b0, a1, ac, inv_c, pr.de));
+                    const float b = (b0 + drift) + h * comp(sD, k) * comp(z4, k);
+                    const float d = (b - b0) - drift;
+                    fw.add(d * d * comp(iD, k));
+                    bq[k] = b;
+                    yd = fmaf(b, comp(v, k), yd);
+                }
+                const float4 b4 = make_float4(bq[0], bq[1], bq[2], bq[3]);
+                st4(dst + j0, b4);
+                if (grouped) {
+                    lt.add(prior_terms4(b4, sk.w));
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) lt.add(prior_term(bq[k], sk.w, pr.de));
+                }
+                if (Arow) off += pack_coord4(Arow, a.Kp, j0, b4, ldg4(a.l2e_over_s + j0), ldg4(a.mean_f + j0));
+            }
+        }
+        for (int g = VEC ? groups : lane; g < groups; g += 32) {
             const float4 z4 = normals4(seed, (uint32_t)g, (uint32_t)i, (uint32_t)t, m);
             float bq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -586,16 +647,7 @@ __global__ void __launch_bounds__(BLOCK) k_move_commit(MoveArgs a, int64_t N, in
         if (MALA) {
             const float ac = sk.x, a1 = pr.a + 1.0f, inv_c = sk.z;
             const float h = *a.h, h2 = 0.5f * h * h;
-            FSum bwd;
-            const float* b0 = a.beta + i * p;
-            const float* b1 = a.beta_p + i * p;
-            const float* g1 = a.gl_p + i * p;
-            for (int j = lane; j < p; j += 32) {
-                const float drift = h2 * a.sigma[j] * (g1[j] + dlogprior(b1[j], a1, ac, inv_c, pr.de));
-                const float d = (b0[j] - b1[j]) - drift;
-                bwd.add(d * d * a.inv_D[j]);
-            }
-            bwd = warp_sum(bwd);
+            const FSum bwd = warp_sum(mala_reverse<VEC>(a, i, p, lane, h2, a1, ac, inv_c, pr.de));
             const float2 fw = a.fwd[i];
             extra = -((bwd.s - fw.x) + (bwd.c - fw.y)) / (2.0f * h * h);
         }
@@ -1553,10 +1605,18 @@ cudaError_t launch_move_rw(const MoveArgs& a, bool decide, int64_t N, int p, Pri
 cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
                              uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
-    if (decide)
-        k_move_mala<true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
-    else
-        k_move_mala<false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+    const bool vec = (p & 3) == 0;
+    if (decide) {
+        if (vec)
+            k_move_mala<true, true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+        else
+            k_move_mala<true, false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+    } else {
+        if (vec)
+            k_move_mala<false, true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+        else
+            k_move_mala<false, false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+    }
     return cudaGetLastError();
 }
 
