@@ -167,14 +167,17 @@ int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, s
 /* A reusable batch: the R sweeps are captured into ONE CUDA graph whose R branches (one
  * per context, on the context's stream) run concurrently on the GPU, and every
  * spa_batch_run is a single graph launch on the batch's own stream. Each region's
- * likelihood tile shape comes from the library's tuner (timed once per shape).
+ * likelihood tile configuration comes from the tile table or the tuner. In this branch form
+ * each region's likelihood and adjoint launches are sized for an eighth of the SMs (an
+ * equal share when fewer than 8 regions), so that the regions share the GPU; the partials,
+ * and so the results, do not depend on the grid.
  * With the environment variable SPA_BATCH_MODE=lockstep at creation, a batch whose regions
  * share T, N, moves_per_step, the move kind (RW or MALA), the start and the burn-in, on the
  * tensor cores, is captured in lock step instead: at every likelihood evaluation all regions
  * wait for each other and one persistent grouped launch per tile class evaluates every
  * region's particles (a device table of all regions' particle-tile x n-tile units). The
  * results are the same bit for bit; on the 64-region MALA workload the branch form is faster
- * (2.74 s against 3.30 s per batch), so it is the default.
+ * (2.44 s against 3.12 s per batch), so it is the default.
  * Contexts must be distinct and outlive the batch; their schedules (args->schedules,
  * copied here), T, N and moves_per_step are fixed at creation. Results are bit-identical
  * to spa_run of each context with the same seed.
