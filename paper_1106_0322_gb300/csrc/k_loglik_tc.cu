@@ -110,6 +110,34 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
+// A 4 x 4 transpose of 16-byte chunks across each aligned group of four lanes: on entry lane
+// 4g + s holds chunks 0..3 of its own row s; on exit slot s of lane 4g + c holds chunk c of
+// row s of the group. Two butterfly exchanges, across lane bit 0 and then bit 1: in each, a
+// lane trades the two slots whose index bit differs from its own lane bit with its partner.
+__device__ __forceinline__ void xpose4_u4(uint4 (&v)[4], int lane)
+{
+#pragma unroll
+    for (int bit = 0; bit < 2; ++bit) {
+        const int m = 1 << bit;
+        const bool lb = (lane >> bit) & 1;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int q0 = bit == 0 ? 2 * k : k;  // the pair's slot with index bit `bit` clear
+            const int q1 = q0 | m;                // and set
+            const uint4 send = lb ? v[q0] : v[q1];
+            uint4 recv;
+            recv.x = __shfl_xor_sync(0xffffffffu, send.x, m);
+            recv.y = __shfl_xor_sync(0xffffffffu, send.y, m);
+            recv.z = __shfl_xor_sync(0xffffffffu, send.z, m);
+            recv.w = __shfl_xor_sync(0xffffffffu, send.w, m);
+            if (lb)
+                v[q0] = recv;
+            else
+                v[q1] = recv;
+        }
+    }
+}
+
 // Residual mode: besides the softplus sum, r = y - logit^{-1}(eta) for the 32 columns of
 // this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into rsum.
 // eta2 = eta log2(e): with e = 2^-|eta2|, softplus2 = max(eta2, 0) + log2(1 + e) and
@@ -135,15 +163,24 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
         rs[k] = r;
         split_bf16(r, hi[k], lo[k]);
     }
-    // 16-byte stores of the 32 hi and 32 lo values (rrow is 64-byte aligned)
-    uint4* dh = reinterpret_cast<uint4*>(rrow);
-    uint4* dl = reinterpret_cast<uint4*>(rrow + n_r);
-    const uint4* sh = reinterpret_cast<const uint4*>(hi);
-    const uint4* sl = reinterpret_cast<const uint4*>(lo);
+    // 16-byte stores of the 32 hi and 32 lo values (rrow is 64-byte aligned), transposed in
+    // groups of four lanes first, so that each store instruction writes eight rows' whole
+    // 64-byte segments instead of one 16-byte piece of each of 32 rows
+    uint4 h4[4], l4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        dh[q] = sh[q];
-        dl[q] = sl[q];
+        h4[q] = reinterpret_cast<const uint4*>(hi)[q];
+        l4[q] = reinterpret_cast<const uint4*>(lo)[q];
+    }
+    const int lane = threadIdx.x & 31;
+    xpose4_u4(h4, lane);
+    xpose4_u4(l4, lane);
+    const int c4 = lane & 3;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        __nv_bfloat16* dst = rrow + (int64_t)(s - c4) * 2 * n_r + 8 * c4;
+        *reinterpret_cast<uint4*>(dst) = h4[s];
+        *reinterpret_cast<uint4*>(dst + n_r) = l4[s];
     }
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1)
@@ -699,8 +736,10 @@ __global__ void __launch_bounds__(Epi<EW>::THREADS, 1)
 // pt) of one K-split ks; a CTA takes units blockIdx.x, blockIdx.x + gridDim.x, ... (one unit
 // each when the grid covers them all), with a double-buffered accumulator in TMEM so that a
 // unit's MMAs overlap the previous unit's copy-out. Warps 2..5 copy the FP32 accumulator to
-// gpart[ks][particle][marker]. Every unit runs the same MMAs whichever CTA takes it, so
-// the partials do not depend on the grid. The final gradient (C - m_j sum_i r_ki) / s_j is
+// gpart[ks][particle][marker], 32 x 32 blocks at a time through a shared-memory transpose:
+// a lane holds one particle's row of a block after tcgen05.ld, and a warp's stores then write
+// whole 128-byte row segments instead of 32 rows' single words per instruction. Every unit
+// runs the same MMAs whichever CTA takes it, so the partials do not depend on the grid. The final gradient (C - m_j sum_i r_ki) / s_j is
 // formed by k_grad_finish.
 constexpr int ADJ_THREADS = 64 + 32 * 4;
 
@@ -712,7 +751,11 @@ struct AdjCfg {
     static constexpr int BAR_OFF = STAGES * STAGE;
     static constexpr int NBARS = 2 * STAGES + 5;  // full[S], empty[S], acc_full[2], acc_empty[2], drain
     static constexpr int SLOT_OFF = BAR_OFF + NBARS * 8;
-    static constexpr int SMEM = SLOT_OFF + 16 + 1024;
+    // one 32 x 33 FP32 transpose buffer per epilogue warp (the padding column keeps both the
+    // row writes and the column reads free of bank conflicts)
+    static constexpr int XPOSE_OFF = SLOT_OFF + 16;
+    static constexpr int XPOSE_FLOATS = 32 * 33;
+    static constexpr int SMEM = XPOSE_OFF + 4 * XPOSE_FLOATS * 4 + 1024;
     static constexpr uint32_t ACC_STRIDE = 256;  // TMEM columns between the two accumulator buffers
     static constexpr uint32_t TMEM_COLS = 512;
     static_assert(STAGE % 1024 == 0, "tiles must stay 1024-byte aligned");
@@ -844,6 +887,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     } else {
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
+        float* xp = reinterpret_cast<float*>(smem + C::XPOSE_OFF) + quad * C::XPOSE_FLOATS;
         int lt = 0;
         for (int u = blockIdx.x; u < units; u += gridDim.x) {
             int mt, pt, kb0, kb1, ks;
@@ -857,13 +901,20 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
             const uint32_t b = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
             if (!mbar_wait_bounded(ACCF_BAR(b), aph, err, wait_ns)) break;
             tc_fence_after();
+            // this warp's 32 rows, from row quad * 32 of the tile
+            float* out0 = gpart + ((int64_t)ks * N_pad + (int64_t)mt * BM + quad * 32) * p + (int64_t)pt * BN2;
 #pragma unroll 1
             for (int c = 0; c < cols; c += 32) {
                 float v[32];
                 tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + b * C::ACC_STRIDE + (uint32_t)c, v);
 #pragma unroll
-                for (int k = 0; k < 32; ++k)
-                    if (c + k < cols) out[c + k] = v[k];
+                for (int k = 0; k < 32; ++k) xp[lane * 33 + k] = v[k];
+                __syncwarp();
+                if (c + lane < cols) {
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) out0[(int64_t)r * p + c + lane] = xp[r * 33 + lane];
+                }
+                __syncwarp();
             }
             tc_fence_before();
             __syncwarp();
@@ -891,9 +942,16 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 // warp per particle would, each load touches its own sector), and the 32 compensated partial
 // sums of a particle are combined in slice order. Then each warp finishes its particle's row
 // (lane j reads marker j of every K-split partial), C - m_j sum r by one fused multiply-add.
+// The row is taken GF_U markers per lane at a time with the K-split count KS fixed at compile
+// time, so that all KS x GF_U partial loads and the GF_U state loads of a batch are in flight
+// together: the loads are L2 hits, and issued one dependent batch at a time their latency,
+// not bandwidth, set the kernel's duration. Each marker's partials are still added in K-split
+// order, so the gradient is the same bit for bit.
 constexpr int GF_PARTICLES = 8;
+constexpr int GF_U = 4;
 
-__global__ void __launch_bounds__(256) k_grad_finish(const float* __restrict__ gpart, int ksplit,
+template <int KS>
+__global__ void __launch_bounds__(256) k_grad_finish(const float* __restrict__ gpart,
                                                      const float* __restrict__ rsum_part, int n_parts, int64_t N_pad,
                                                      int64_t N, int p, const float* __restrict__ mean_f,
                                                      const float* __restrict__ inv_sd, const float* __restrict__ B,
@@ -926,16 +984,31 @@ __global__ void __launch_bounds__(256) k_grad_finish(const float* __restrict__ g
     if (k >= N) return;
     const float rs = rsum[w];
     const float a1 = pr.a + 1.0f, ac = (float)((double)pr.a * c), inv_c = c > 0.0 ? (float)(1.0 / c) : 0.0f;
-    for (int j = lane; j < p; j += 32) {
-        FSum g;
-        for (int q = 0; q < ksplit; ++q) g.add(gpart[((int64_t)q * N_pad + k) * p + j]);
-        float gv = fmaf(-mean_f[j], rs, g.value()) * inv_sd[j];
-        if (c > 0.0) {
-            const float b = B[k * p + j];
-            const float sg = (b > 0.0f) ? 1.0f : ((b < 0.0f) ? -1.0f : 0.0f);
-            gv += pr.de ? -sg * inv_c : -a1 * sg / (ac + fabsf(b));
+    for (int j0 = lane; j0 < p; j0 += 32 * GF_U) {
+        float x[KS][GF_U], b[GF_U];
+#pragma unroll
+        for (int u = 0; u < GF_U; ++u) {
+            const int j = j0 + 32 * u;
+            const bool in = j < p;
+#pragma unroll
+            for (int q = 0; q < KS; ++q) x[q][u] = in ? gpart[((int64_t)q * N_pad + k) * p + j] : 0.0f;
+            b[u] = (in && c > 0.0) ? B[k * p + j] : 0.0f;
         }
-        grad[k * p + j] = gv;
+#pragma unroll
+        for (int u = 0; u < GF_U; ++u) {
+            const int j = j0 + 32 * u;
+            if (j >= p) break;
+            FSum g;
+#pragma unroll
+            for (int q = 0; q < KS; ++q) g.add(x[q][u]);
+            float gv = fmaf(-mean_f[j], rs, g.value()) * inv_sd[j];
+            if (c > 0.0) {
+                const float bj = b[u];
+                const float sg = (bj > 0.0f) ? 1.0f : ((bj < 0.0f) ? -1.0f : 0.0f);
+                gv += pr.de ? -sg * inv_c : -a1 * sg / (ac + fabsf(bj));
+            }
+            grad[k * p + j] = gv;
+        }
     }
 }
 
@@ -1226,8 +1299,25 @@ cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum
                                int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st)
 {
-    k_grad_finish<<<(unsigned)((N + GF_PARTICLES - 1) / GF_PARTICLES), 256, 0, st>>>(
-        gpart, ksplit, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd, B, pr, c, grad);
+    const unsigned grid = (unsigned)((N + GF_PARTICLES - 1) / GF_PARTICLES);
+#define GF_CASE(KS_)                                                                                            \
+    case KS_:                                                                                                   \
+        k_grad_finish<KS_><<<grid, 256, 0, st>>>(gpart, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd, B, pr, c, \
+                                                 grad);                                                         \
+        break
+    switch (ksplit) {
+        GF_CASE(1);
+        GF_CASE(2);
+        GF_CASE(3);
+        GF_CASE(4);
+        GF_CASE(5);
+        GF_CASE(6);
+        GF_CASE(7);
+        GF_CASE(8);
+    default:
+        return cudaErrorInvalidValue;  // adj_plan keeps the K-split in 1..8
+    }
+#undef GF_CASE
     return cudaGetLastError();
 }
 
