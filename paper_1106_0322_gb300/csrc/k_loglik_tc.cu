@@ -815,6 +815,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // launched as a programmatic dependent of the residual pass: the prologue above overlaps
+    // its tail, and R is read only after it has finished
+    grid_dependency_wait();
+    grid_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -959,6 +963,8 @@ __global__ void __launch_bounds__(256) k_grad_finish(const float* __restrict__ g
 {
     __shared__ float2 part[32][GF_PARTICLES];
     __shared__ float rsum[GF_PARTICLES];
+    grid_dependency_wait();  // the adjoint GEMM has finished
+    grid_launch_dependents();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t k0 = (int64_t)blockIdx.x * GF_PARTICLES;
     {
@@ -1284,27 +1290,41 @@ cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT,
 {
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     const unsigned grid = (unsigned)((max_ctas > 0 && max_ctas < a.grid) ? max_ctas : a.grid);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(ADJ_THREADS);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (a.BN2 == ADJ_BN_SMALL) {
-        k_adjoint_tc<ADJ_BN_SMALL, 3><<<grid, ADJ_THREADS, AdjCfg<ADJ_BN_SMALL, 3>::SMEM, st>>>(
-            mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns);
-    } else {
-        k_adjoint_tc<256, 3><<<grid, ADJ_THREADS, AdjCfg<256, 3>::SMEM, st>>>(mapR, mapGT, a.m_tiles, a.p_tiles,
-                                                                             a.kblocks, a.ksplit, (int)a.n_r, p, gpart,
-                                                                             N_pad, err, wait_ns);
+        cfg.dynamicSmemBytes = AdjCfg<ADJ_BN_SMALL, 3>::SMEM;
+        return cudaLaunchKernelEx(&cfg, k_adjoint_tc<ADJ_BN_SMALL, 3>, mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks,
+                                  a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns);
     }
-    return cudaGetLastError();
+    cfg.dynamicSmemBytes = AdjCfg<256, 3>::SMEM;
+    return cudaLaunchKernelEx(&cfg, k_adjoint_tc<256, 3>, mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit,
+                              (int)a.n_r, p, gpart, N_pad, err, wait_ns);
 }
 
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
                                int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st)
 {
-    const unsigned grid = (unsigned)((N + GF_PARTICLES - 1) / GF_PARTICLES);
-#define GF_CASE(KS_)                                                                                            \
-    case KS_:                                                                                                   \
-        k_grad_finish<KS_><<<grid, 256, 0, st>>>(gpart, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd, B, pr, c, \
-                                                 grad);                                                         \
-        break
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((N + GF_PARTICLES - 1) / GF_PARTICLES));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+#define GF_CASE(KS_) \
+    case KS_:        \
+        return cudaLaunchKernelEx(&cfg, k_grad_finish<KS_>, gpart, rsum_part, n_parts, N_pad, N, p, mean_f, inv_sd, B, pr, c, grad)
     switch (ksplit) {
         GF_CASE(1);
         GF_CASE(2);
@@ -1318,7 +1338,6 @@ cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum
         return cudaErrorInvalidValue;  // adj_plan keeps the K-split in 1..8
     }
 #undef GF_CASE
-    return cudaGetLastError();
 }
 
 }  // namespace spa

@@ -401,6 +401,8 @@ __global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int 
 {
     __shared__ int accw[BLOCK / 32];
     __shared__ PartSlices parts;
+    grid_dependency_wait();  // the previous kernel (the gradient finish) has finished
+    grid_launch_dependents();
     if (DECIDE) {
         gather_partials(a.mh, N, parts);
         __syncthreads();
@@ -1606,18 +1608,15 @@ cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, P
                              uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
     const bool vec = (p & 3) == 0;
+    cudaLaunchConfig_t cfg = pdl_config(warps_grid(N), BLOCK, st);  // follows the gradient finish
+    cudaLaunchAttribute attr[1];
+    pdl_attr(cfg, attr);
     if (decide) {
-        if (vec)
-            k_move_mala<true, true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
-        else
-            k_move_mala<true, false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
-    } else {
-        if (vec)
-            k_move_mala<false, true><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
-        else
-            k_move_mala<false, false><<<warps_grid(N), BLOCK, 0, st>>>(a, N, p, pr, stepk, t, m, m_prev, seed, err);
+        if (vec) return cudaLaunchKernelEx(&cfg, k_move_mala<true, true>, a, N, p, pr, stepk, t, m, m_prev, seed, err);
+        return cudaLaunchKernelEx(&cfg, k_move_mala<true, false>, a, N, p, pr, stepk, t, m, m_prev, seed, err);
     }
-    return cudaGetLastError();
+    if (vec) return cudaLaunchKernelEx(&cfg, k_move_mala<false, true>, a, N, p, pr, stepk, t, m, m_prev, seed, err);
+    return cudaLaunchKernelEx(&cfg, k_move_mala<false, false>, a, N, p, pr, stepk, t, m, m_prev, seed, err);
 }
 
 cudaError_t launch_move_commit(const MoveArgs& a, bool mala, int64_t N, int p, PriorArgs pr, const float4* stepk, int t,
