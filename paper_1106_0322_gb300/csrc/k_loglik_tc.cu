@@ -142,26 +142,39 @@ __device__ __forceinline__ void xpose4_u4(uint4 (&v)[4], int lane)
 // this chunk is stored as BF16 hi (row of R) and lo (row + n_r) and summed into rsum.
 // eta2 = eta log2(e): with e = 2^-|eta2|, softplus2 = max(eta2, 0) + log2(1 + e) and
 // logit^{-1}(eta) = 1/(1 + e) for eta >= 0, e/(1 + e) otherwise (one ex2 shared).
+// FULL: all 32 columns are individuals (every chunk but the last of a region's row), so no
+// column needs the valid-count test. The hi | lo split is taken two columns at a time (one
+// paired conversion each for hi and lo), with the same round-to-nearest values as one at a time.
+template <bool FULL>
 __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, uint32_t ybits,
                                              __nv_bfloat16* __restrict__ rrow, int64_t n_r, float& rsum)
 {
     float sp[32];
-    __align__(16) __nv_bfloat16 hi[32];
-    __align__(16) __nv_bfloat16 lo[32];
+    uint32_t hi2[16], lo2[16];  // BF16 pairs, column 2q in the low half
     float rs[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const float x = v[k];
-        const bool ok = k < valid;
-        const float e = ex2_approx(-fabsf(x));
-        const float onepe = 1.0f + e;
-        const float inv = rcp_approx(onepe);
-        const float sig = (x >= 0.0f) ? inv : e * inv;
-        const bool yk = (ybits >> k) & 1u;
-        sp[k] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
-        const float r = ok ? (yk ? 1.0f : 0.0f) - sig : 0.0f;
-        rs[k] = r;
-        split_bf16(r, hi[k], lo[k]);
+    for (int k = 0; k < 32; k += 2) {
+        float r2[2];
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+            const int kk = k + d;
+            const float x = v[kk];
+            const bool ok = FULL || kk < valid;
+            const float e = ex2_approx(-fabsf(x));
+            const float onepe = 1.0f + e;
+            const float inv = rcp_approx(onepe);
+            const float sig = (x >= 0.0f) ? inv : e * inv;
+            const bool yk = (ybits >> kk) & 1u;
+            sp[kk] = ok ? fmaxf(x, 0.0f) + lg2_approx(onepe) : 0.0f;
+            const float r = ok ? (yk ? 1.0f : 0.0f) - sig : 0.0f;
+            rs[kk] = r;
+            r2[d] = r;
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(r2[0], r2[1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r2[0] - hf.x, r2[1] - hf.y);
+        hi2[k >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+        lo2[k >> 1] = *reinterpret_cast<const uint32_t*>(&l);
     }
     // 16-byte stores of the 32 hi and 32 lo values (rrow is 64-byte aligned), transposed in
     // groups of four lanes first, so that each store instruction writes eight rows' whole
@@ -169,8 +182,8 @@ __device__ __forceinline__ float resid_chunk(const float (&v)[32], int valid, ui
     uint4 h4[4], l4[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        h4[q] = reinterpret_cast<const uint4*>(hi)[q];
-        l4[q] = reinterpret_cast<const uint4*>(lo)[q];
+        h4[q] = make_uint4(hi2[4 * q], hi2[4 * q + 1], hi2[4 * q + 2], hi2[4 * q + 3]);
+        l4[q] = make_uint4(lo2[4 * q], lo2[4 * q + 1], lo2[4 * q + 2], lo2[4 * q + 3]);
     }
     const int lane = threadIdx.x & 31;
     xpose4_u4(h4, lane);
@@ -678,8 +691,10 @@ __device__ __forceinline__ void loglik_tc_body(const Src& src, uint32_t* __restr
                     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
                     const int64_t i0 = (int64_t)t.nt * BN + col0 + 32 * ch;
                     float rs;
-                    const float sp =
-                        resid_chunk(v, valid, __ldg(t.ybits + (i0 >> 5)), t.R + prow * 2 * t.n_r + i0, t.n_r, rs);
+                    const uint32_t yb = __ldg(t.ybits + (i0 >> 5));
+                    __nv_bfloat16* rrow = t.R + prow * 2 * t.n_r + i0;
+                    const float sp = valid >= 32 ? resid_chunk<true>(v, valid, yb, rrow, t.n_r, rs)
+                                                 : resid_chunk<false>(v, valid, yb, rrow, t.n_r, rs);
                     partial[(gc0 + ch) * t.N_pad + prow] = -sp;
                     t.rsum_part[(gc0 + ch) * t.N_pad + prow] = rs;
                 }
