@@ -782,7 +782,7 @@ template <int BN2, int STAGES>
 __global__ void __launch_bounds__(ADJ_THREADS, 1)
     k_adjoint_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapGT, int m_tiles,
                  int p_tiles, int kblocks, int ksplit, int n_r, int p, float* __restrict__ gpart, int64_t N_pad,
-                 uint32_t* __restrict__ err, uint64_t wait_ns)
+                 uint32_t* __restrict__ err, uint64_t wait_ns, int r_hint)
 {
     using C = AdjCfg<BN2, STAGES>;
     extern __shared__ uint8_t smem_raw[];
@@ -837,6 +837,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
 
     if (warp == 0) {
         if (lane == 0) {
+            // R is read once, here: with r_hint its lines go first when L2 needs room, ahead
+            // of the particle state that the move kernel reads next
+            const uint64_t r_pol = r_hint ? l2_policy_evict_first() : 0;
             uint32_t it = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -850,8 +853,13 @@ __global__ void __launch_bounds__(ADJ_THREADS, 1)
                     }
                     const uint32_t st = sbase + q * C::STAGE;
                     mbar_arrive_expect_tx(FULL_BAR(q), (uint32_t)C::STAGE);
-                    tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
-                    tma_load_2d(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM);
+                    if (r_hint) {
+                        tma_load_2d_hint(st, &mapR, FULL_BAR(q), kb * BK, mt * BM, r_pol);
+                        tma_load_2d_hint(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM, r_pol);
+                    } else {
+                        tma_load_2d(st, &mapR, FULL_BAR(q), kb * BK, mt * BM);
+                        tma_load_2d(st + C::A_TILE, &mapR, FULL_BAR(q), n_r + kb * BK, mt * BM);
+                    }
                     tma_load_2d(st + 2 * C::A_TILE, &mapGT, FULL_BAR(q), kb * BK, pt * BN2);
                     ++it;
                 }
@@ -1301,8 +1309,10 @@ bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n
 }
 
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p,
-                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns, int max_ctas)
+                              float* gpart, int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns, int max_ctas,
+                              bool r_last_use_hint)
 {
+    const int r_hint = r_last_use_hint ? 1 : 0;
     if (wait_ns == 0) wait_ns = WAIT_LIMIT_DEFAULT_NS;
     const unsigned grid = (unsigned)((max_ctas > 0 && max_ctas < a.grid) ? max_ctas : a.grid);
     cudaLaunchConfig_t cfg = {};
@@ -1317,11 +1327,11 @@ cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT,
     if (a.BN2 == ADJ_BN_SMALL) {
         cfg.dynamicSmemBytes = AdjCfg<ADJ_BN_SMALL, 3>::SMEM;
         return cudaLaunchKernelEx(&cfg, k_adjoint_tc<ADJ_BN_SMALL, 3>, mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks,
-                                  a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns);
+                                  a.ksplit, (int)a.n_r, p, gpart, N_pad, err, wait_ns, r_hint);
     }
     cfg.dynamicSmemBytes = AdjCfg<256, 3>::SMEM;
     return cudaLaunchKernelEx(&cfg, k_adjoint_tc<256, 3>, mapR, mapGT, a.m_tiles, a.p_tiles, a.kblocks, a.ksplit,
-                              (int)a.n_r, p, gpart, N_pad, err, wait_ns);
+                              (int)a.n_r, p, gpart, N_pad, err, wait_ns, r_hint);
 }
 
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,

@@ -395,7 +395,7 @@ __device__ __forceinline__ FSum mala_reverse(const MoveArgs& a, int64_t i, int p
 // log alpha = l' + lp' - l - lp - (bwd - fwd)/(2h^2); an accepted proposal and its gradient
 // are written back as the state while being read.
 template <bool DECIDE, bool VEC>
-__global__ void __launch_bounds__(BLOCK) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
+__global__ void __launch_bounds__(BLOCK, 4) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
                                                     const float4* __restrict__ stepk, int t, uint32_t m,
                                                     uint32_t m_prev, const uint64_t* __restrict__ seedp, uint32_t* err)
 {

@@ -657,7 +657,7 @@ void enq_grad_tail(Enq& q, float* out, const float* Bsrc, double cs, int64_t N)
     // over individuals are grouped, so a batch's gradients stay those of a single run
     const AdjPlan a = adj_plan((int)c->p, c->n, w.N_pad, c->num_sms);
     q.ck(launch_adjoint_tc(w.mapR, c->mapGT, a, (int)c->p, w.gpart, w.N_pad, c->d_err, q.st, c->wait_ns,
-                           c->plan_sms > 0 ? c->plan_sms : 0));
+                           c->plan_sms > 0 ? c->plan_sms : 0, /*r_last_use_hint=*/c->plan_sms == 0));
     q.ck(launch_grad_finish(w.gpart, a.ksplit, w.rsum, plan.n_parts, w.N_pad, N, (int)c->p, c->mean_f, c->colf, Bsrc,
                             c->pr, cs, out, q.st));
 }

@@ -365,9 +365,12 @@ AdjPlan adj_plan(int p, int64_t n, int64_t N_pad, int num_sms);
 bool adj_make_map_R(CUtensorMap* map, const __nv_bfloat16* R, int64_t N_pad, int64_t n_r);
 bool adj_make_map_GT(CUtensorMap* map, const __nv_bfloat16* GT, int p, int64_t n_r, int BN2);
 // max_ctas > 0 caps the grid (the CTAs then loop over the output tiles; the partials do not
-// change), else one CTA per output tile and K-split.
+// change), else one CTA per output tile and K-split. r_last_use_hint reads R under an L2
+// evict-first policy (R is dead after this kernel): measured faster for a region that has
+// the GPU to itself, slower for a batch's regions side by side.
 cudaError_t launch_adjoint_tc(const CUtensorMap& mapR, const CUtensorMap& mapGT, const AdjPlan& a, int p, float* gpart,
-                              int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns = 0, int max_ctas = 0);
+                              int64_t N_pad, uint32_t* err, cudaStream_t st, uint64_t wait_ns = 0, int max_ctas = 0,
+                              bool r_last_use_hint = false);
 cudaError_t launch_grad_finish(const float* gpart, int ksplit, const float* rsum_part, int n_parts, int64_t N_pad,
                                int64_t N, int p, const float* mean_f, const float* inv_sd, const float* B, PriorArgs pr,
                                double c, float* grad, cudaStream_t st);
