@@ -299,8 +299,13 @@ def grad_split_bound(G, B):
 
 # The last three are the batched workload's extreme region shapes (n up to 5000, p from 20 to
 # 500) at its N = 4096 particles, so the adjoint runs with the K-split those sweeps use.
+# The adjoint's K-split count is floor(SMs / output tiles), at most 8 and at most the
+# k-blocks. On a 152-SM GB300 these shapes give K-splits 1, 5, 8, 8, 8, 2, 4, 2, and the last
+# three 3 (40 particle tiles), 6 (24) and 7 (21), so the gradient finish runs with every
+# K-split count it is compiled for.
 @pytest.mark.parametrize("n,p,N", [(7, 3, 5), (300, 37, 70), (600, 130, 300), (2000, 200, 256), (1000, 300, 129),
-                                   (5000, 500, 4096), (5000, 20, 4096), (1000, 500, 4096)])
+                                   (5000, 500, 4096), (5000, 20, 4096), (1000, 500, 4096),
+                                   (400, 20, 5120), (400, 20, 3000), (400, 20, 2600)])
 def test_gradient_tensor_core_bound(spa, n, p, N):
     reg = synth.make_region(n, p, 0.9, (0.5, -0.4), seed=n + 3 * p)
     B = synth.random_particles(N, p, 0.2, seed=N + 1)
