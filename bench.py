@@ -126,12 +126,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_sha() -> str:
-    path = os.path.join(ROOT, "paper_1106_0322_gb300", "csrc", "k_loglik_tc.cu")
+def code_digest(sources) -> str:
+    """Hash of C++/CUDA source texts with comments and blank lines left out and each line's
+    whitespace runs collapsed to one space."""
+    import re
+
     h = hashlib.sha256()
-    for f in (path, os.path.join(ROOT, "paper_1106_0322_gb300", "csrc", "spa_device.cuh")):
-        h.update(open(f, "rb").read())
+    for src in sources:
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("\n".join(" ".join(line.split()) for line in src.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
+
+
+def kernel_source_sha() -> str:
+    """code_digest of the likelihood kernel's source (its file and the device header): the
+    recorded DRAM counters belong to the code, so a comment edit keeps them while any code
+    change drops them."""
+    csrc = os.path.join(ROOT, "paper_1106_0322_gb300", "csrc")
+    return code_digest(open(os.path.join(csrc, f), encoding="utf-8").read() for f in ("k_loglik_tc.cu", "spa_device.cuh"))
 
 
 def measured_peaks():

@@ -74,6 +74,14 @@ def test_recorded_traffic_is_tied_to_the_kernel_source():
     assert bench.profile_traffic("no-such-workload") is None
 
 
+def test_kernel_digest_ignores_comments_only():
+    a = "int f(int x) {\n    return x + 1;  // one more\n}\n"
+    b = "// the next integer\nint f(int x) {\n    /* plain */ return x + 1;\n\n}\n"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench.code_digest([a]) == bench.code_digest([b])
+    assert bench.code_digest([a]) != bench.code_digest([c])
+
+
 def test_cli_parses_without_a_gpu():
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--help"], capture_output=True, text=True,
                          timeout=300)
