@@ -393,7 +393,8 @@ __device__ __forceinline__ FSum mala_reverse(const MoveArgs& a, int64_t i, int p
 // DECIDE the warp first forms the reverse term of the pending proposal,
 // bwd = sum_j (beta_j - beta'_j - (h^2/2) D_j g'_j)^2 / D_j, and runs its MH test with
 // log alpha = l' + lp' - l - lp - (bwd - fwd)/(2h^2); an accepted proposal and its gradient
-// are written back as the state while being read.
+// are written back as the state while being read. At most 64 registers, so that 4 blocks
+// fit an SM (1.68 waves of 8192 particle warps; the test variant would take 74 and 3 blocks).
 template <bool DECIDE, bool VEC>
 __global__ void __launch_bounds__(BLOCK, 4) k_move_mala(MoveArgs a, int64_t N, int p, PriorArgs pr,
                                                     const float4* __restrict__ stepk, int t, uint32_t m,
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_move_mala(MoveArgs a, int64_t N, i
 {
     __shared__ int accw[BLOCK / 32];
     __shared__ PartSlices parts;
-    grid_dependency_wait();  // the previous kernel (the gradient finish) has finished
+    grid_dependency_wait();  // the previous kernel (the gradient finish, or the step's proposal scales) has finished
     grid_launch_dependents();
     if (DECIDE) {
         gather_partials(a.mh, N, parts);
@@ -1608,7 +1609,7 @@ cudaError_t launch_move_mala(const MoveArgs& a, bool decide, int64_t N, int p, P
                              uint32_t m, uint32_t m_prev, const uint64_t* seed, uint32_t* err, cudaStream_t st)
 {
     const bool vec = (p & 3) == 0;
-    cudaLaunchConfig_t cfg = pdl_config(warps_grid(N), BLOCK, st);  // follows the gradient finish
+    cudaLaunchConfig_t cfg = pdl_config(warps_grid(N), BLOCK, st);  // follows the gradient finish or the scales
     cudaLaunchAttribute attr[1];
     pdl_attr(cfg, attr);
     if (decide) {
