@@ -177,7 +177,7 @@ int spa_run_batch(spa_ctx* const* ctxs, int32_t R, const spa_batch_args* args, s
  * wait for each other and one persistent grouped launch per tile class evaluates every
  * region's particles (a device table of all regions' particle-tile x n-tile units). The
  * results are the same bit for bit; on the 64-region MALA workload the branch form is faster
- * (2.44 s against 3.12 s per batch), so it is the default.
+ * (1.84 s against 2.26 s per batch), so it is the default.
  * Contexts must be distinct and outlive the batch; their schedules (args->schedules,
  * copied here), T, N and moves_per_step are fixed at creation. Results are bit-identical
  * to spa_run of each context with the same seed.
